@@ -1,0 +1,161 @@
+/*
+ * wd.h -- C ABI of the GB300 Wilson-Dirac conjugate-gradient library.
+ *
+ * The library solves D psi = eta for the Wilson-Dirac operator D of Eq. (1) of arXiv 2111.14958
+ * ("Implementation of the conjugate gradient algorithm for heterogeneous systems", Sec. 1), using
+ * conjugate gradient on the normal equations (Sec. 2: the gamma_5-hermiticity gamma_5 D gamma_5 =
+ * D^dagger turns the problem into a Hermitian one). The operator, in the hopping form with Wilson
+ * parameter r = 1, is
+ *
+ *   (D psi)(n) = psi(n) - kappa sum_mu [ (1 - gamma_mu) U_mu(n) b psi(n + mu)
+ *                                       + (1 + gamma_mu) U_mu(n - mu)^dagger b psi(n - mu) ]
+ *
+ * with mu = 0,1,2,3 = x,y,z,t, the chiral gamma basis (gamma_k = [[0,-i sigma_k],[i sigma_k,0]],
+ * gamma_t = [[0,1],[1,0]]), and b = boundary[mu] for a hop that wraps around the lattice in
+ * direction mu (else 1). D^dagger swaps the two projectors.
+ *
+ * Canonical (caller-visible) layouts, site index n = x + Lx*(y + Ly*(z + Lz*t)):
+ *   spinor field : complex [Lt][Lz][Ly][Lx][4 spin][3 colour], interleaved (re, im)
+ *                  -- complex128 (double pairs) unless a function says otherwise;
+ *   gauge field  : complex128 [Lt][Lz][Ly][Lx][4 mu][3][3], U[n][mu] = U_mu(n), the link
+ *                  n -> n + mu, row-major (row = first colour index).
+ * Internally every field is converted to a site-blocked structure-of-arrays layout; callers never
+ * see it.
+ *
+ * Conventions for every call:
+ *   - Pointers to fields are DEVICE pointers (memory of the context's device) unless a parameter
+ *     says otherwise. The library borrows them for the duration of the call and never frees them.
+ *   - All work is enqueued on the stream given to wd_create; calls return after the work they
+ *     enqueued has finished unless stated otherwise.
+ *   - Every call returns a wd_status. On failure, wd_last_error() returns a message (per thread).
+ *   - A context is not thread-safe: one thread at a time per context.
+ */
+#ifndef WD_H
+#define WD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_ctx wd_ctx; /* opaque: device gauge copies, Krylov workspace, CUDA graphs */
+
+typedef enum {
+  WD_OK = 0,
+  WD_NOT_CONVERGED = 1,  /* maxit reached; outputs are filled with the last iterate       */
+  WD_EINVAL = -1,        /* bad argument (null pointer, bad dims, bad precision, ...)    */
+  WD_ENOMEM = -2,        /* device allocation failed                                      */
+  WD_ECUDA = -3,         /* a CUDA runtime call failed                                    */
+  WD_ENOTUNITARY = -4,   /* loaded links deviate from SU(3) beyond the stated bound       */
+  WD_BREAKDOWN = -5,     /* non-finite or non-positive CG scalar (e.g. NaN in the source) */
+  WD_ENOGAUGE = -6       /* an operator call before wd_load_gauge                          */
+} wd_status;
+
+/* Precision of the dslash and Krylov vectors (the `precision` argument of wd_create). */
+enum {
+  WD_PREC_F64 = 64,        /* plain FP64 CG: FP64 spinors, FP64 links, FP64 arithmetic             */
+  WD_PREC_F32 = 32,        /* plain FP32 CG: FP32 spinors and links, FP64 reductions               */
+  WD_PREC_MIXED_F32 = 6432,/* FP32 inner CG with FP64 reliable updates (FP64 solution, residual)   */
+  WD_PREC_MIXED_F16 = 6416 /* FP16 spinors with per-site FP32 norm inside, FP64 reliable updates   */
+};
+
+/* Options for wd_set_option. */
+enum {
+  WD_OPT_RELIABLE_DELTA = 1, /* mixed precision: reliable update when |r| drops by this factor
+                                (default 0.1), in (0, 1)                                          */
+  WD_OPT_USE_GRAPH = 2,      /* 1 (default): run the CG loop as a CUDA graph with a device-side
+                                while node; 0: plain stream launches with a host poll           */
+  WD_OPT_BLOCK_DSLASH = 3,   /* threads per block of the dslash kernel (0 = tuned default)      */
+  WD_OPT_BLOCK_BLAS = 4,     /* threads per block of the BLAS-1 kernels (0 = default)            */
+  WD_OPT_MAX_RESTARTS = 5    /* max restarts from the true residual (default 5)                  */
+};
+
+/* Per-solve statistics, filled by wd_get_stats after cg_solve. */
+typedef struct {
+  int iterations;          /* CG iterations (each = 2 dslash applications)                    */
+  int restarts;            /* relaunches from the recomputed true residual                     */
+  int reliable_updates;    /* mixed precision: FP64 residual recomputations                    */
+  int dslash_calls;        /* dslash applications, all precisions                              */
+  int dslash_calls_f64;    /* of which in FP64                                                  */
+  int status;              /* wd_status of the solve                                            */
+  double true_rel_residual;/* ||eta - D x|| / ||eta||, recomputed in the outer precision         */
+  double solve_ms;         /* host wall time of cg_solve                                          */
+} wd_stats;
+
+/*
+ * Create a context for a lattice.
+ *   dims[4]     : Lx, Ly, Lz, Lt; each >= 2 (for L = 2 the two hops land on the same site and
+ *                 both terms of Eq. (1) are added), V = Lx*Ly*Lz*Lt <= 2^27.
+ *   kappa       : hopping parameter (finite, |kappa| < 1).
+ *   boundary[4] : +1 periodic or -1 antiperiodic per direction; NULL means (1, 1, 1, -1).
+ *   precision   : one of WD_PREC_*.
+ *   cuda_stream : cudaStream_t to enqueue on (NULL = the legacy default stream).
+ *   out         : receives the context. Allocates the device workspace (about 8 spinor fields
+ *                 of the working precision plus the gauge copies).
+ * Errors: WD_EINVAL, WD_ENOMEM, WD_ECUDA.
+ */
+wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int precision,
+                    void* cuda_stream, wd_ctx** out);
+
+/* Free every device resource of the context. Null is ignored. */
+void wd_destroy(wd_ctx* ctx);
+
+/*
+ * Load the gauge field U (links of Eq. (1); canonical complex128 layout above).
+ *   U          : host pointer if on_device == 0, else device pointer; V*4*9 complex128.
+ *   compress12 : 1 stores FP32 links of the inner solver (or of a WD_PREC_F32 context) as
+ *                12 reals (rows 0 and 1; row 2 = conj(row0 x row1) rebuilt in the kernel);
+ *                FP64 links are always stored as 18 reals.
+ *   max_unitarity_dev : optional out (host pointer): max over links of max(|U^dag U - 1|_max,
+ *                 |det U - 1|). Returns WD_ENOTUNITARY (data still loaded) if it exceeds 1e-6
+ *                 and compress12 == 1, since the 12-real reconstruction assumes SU(3).
+ */
+wd_status wd_load_gauge(wd_ctx* ctx, const double* U, int on_device, int compress12,
+                        double* max_unitarity_dev);
+
+/*
+ * out = D in (dagger == 0) or D^dagger in (dagger != 0), Eq. (1).
+ *   in, out : device spinor fields in the canonical layout; complex128 for WD_PREC_F64 and the
+ *             mixed modes (FP64 operator), complex64 for WD_PREC_F32. in != out.
+ * Errors: WD_EINVAL, WD_ENOGAUGE, WD_ECUDA.
+ */
+wd_status wd_apply(wd_ctx* ctx, const void* in, void* out, int dagger);
+
+/*
+ * Solve D x = src by CG on D^dagger D x = D^dagger src (CGLS arrangement: two dslash per
+ * iteration, Sec. 2), stopping when the recursive ||r|| / ||src|| <= tol, then recomputing the
+ * true residual ||src - D x|| / ||src|| and restarting from it while it exceeds tol (up to
+ * WD_OPT_MAX_RESTARTS times, within maxit total iterations).
+ *   src       : device, complex128 canonical.
+ *   x         : device, complex128 canonical; initial guess on input, solution on output.
+ *   tol       : > 0 relative tolerance; maxit: >= 0, <= 10^7.
+ *   iters, true_rel_res : optional host outs.
+ * Returns WD_OK, WD_NOT_CONVERGED (x holds the last iterate), WD_BREAKDOWN (non-finite source or
+ * scalar; x holds the last finite iterate), WD_EINVAL, WD_ENOGAUGE, WD_ECUDA.
+ */
+wd_status cg_solve(wd_ctx* ctx, const void* src, void* x, double tol, int maxit, int* iters,
+                   double* true_rel_res);
+
+/* Set an option (WD_OPT_*). Returns WD_EINVAL for an unknown key or a value out of range. */
+wd_status wd_set_option(wd_ctx* ctx, int key, double value);
+
+/* Statistics of the last cg_solve on this context. */
+wd_status wd_get_stats(const wd_ctx* ctx, wd_stats* out);
+
+/*
+ * Time the dslash kernel as the CG launches it: `launches` back-to-back launches on the
+ * context's internal vectors (dagger as given), bracketed by CUDA events on the context's
+ * stream. *avg_ms receives the mean duration of one launch. Requires a loaded gauge field.
+ */
+wd_status wd_time_dslash(wd_ctx* ctx, int dagger, int launches, double* avg_ms);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* wd_last_error(void);
+
+/* Library version string. */
+const char* wd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WD_H */

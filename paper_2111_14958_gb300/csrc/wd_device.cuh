@@ -1,0 +1,411 @@
+// Device-side building blocks of the Wilson-Dirac library: field layouts, complex arithmetic,
+// spin projection/reconstruction for the chiral basis, SU(3) products and deterministic grid
+// reductions. Included by the kernel translation units only.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wdk {
+
+// Storage precisions of spinor fields.
+enum { P64 = 0, P32 = 1, P16 = 2 };
+
+// Lattice geometry. Site index s = x + Lx*(y + Ly*(z + Lz*t)); stride[mu] = step of s along mu.
+struct Geom {
+  int L[4];
+  int stride[4];
+  int V;
+  int bc[4];  // +1 periodic, -1 antiperiodic
+};
+
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cx(R a, R b) {
+  Cx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+
+// ---------------------------------------------------------------- spinor field views
+//
+// Device layout: structure of arrays over sites, so that consecutive threads (sites) touch
+// consecutive addresses for every component.
+//   P64: double2 [12][V]           component c = 3*spin + colour
+//   P32: float4  [6][V]            pair j holds components 2j and 2j+1
+//   P16: uint4   [3][V] + float[V] each uint4 holds 4 components as half2 (re, im), scaled by
+//                                   the per-site norm (max |re|, |im| over the site's 24 reals)
+
+template <int P>
+struct SpinorRef;
+
+template <>
+struct SpinorRef<P64> {
+  double2* p;
+  typedef double real;
+};
+
+template <>
+struct SpinorRef<P32> {
+  float4* p;
+  typedef float real;
+};
+
+template <>
+struct SpinorRef<P16> {
+  uint4* p;
+  float* norm;
+  typedef float real;
+};
+
+__device__ __forceinline__ void load_spinor(const SpinorRef<P64>& f, int s, int V, Cx<double> (&v)[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const double2 d = __ldg(f.p + (size_t)c * V + s);
+    v[c] = cx(d.x, d.y);
+  }
+}
+
+__device__ __forceinline__ void load_spinor(const SpinorRef<P32>& f, int s, int V, Cx<float> (&v)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float4 d = __ldg(f.p + (size_t)j * V + s);
+    v[2 * j] = cx(d.x, d.y);
+    v[2 * j + 1] = cx(d.z, d.w);
+  }
+}
+
+__device__ __forceinline__ void load_spinor(const SpinorRef<P16>& f, int s, int V, Cx<float> (&v)[12]) {
+  const float nrm = __ldg(f.norm + s);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const uint4 d = __ldg(f.p + (size_t)j * V + s);
+    const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 h = *reinterpret_cast<const __half2*>(&w[k]);
+      const float2 fl = __half22float2(h);
+      v[4 * j + k] = cx(fl.x * nrm, fl.y * nrm);
+    }
+  }
+}
+
+__device__ __forceinline__ void store_spinor(const SpinorRef<P64>& f, int s, int V, const Cx<double> (&v)[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) f.p[(size_t)c * V + s] = make_double2(v[c].re, v[c].im);
+}
+
+__device__ __forceinline__ void store_spinor(const SpinorRef<P32>& f, int s, int V, const Cx<float> (&v)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    f.p[(size_t)j * V + s] = make_float4(v[2 * j].re, v[2 * j].im, v[2 * j + 1].re, v[2 * j + 1].im);
+}
+
+__device__ __forceinline__ void store_spinor(const SpinorRef<P16>& f, int s, int V, const Cx<float> (&v)[12]) {
+  float m = 0.f;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf(v[c].re), fabsf(v[c].im)));
+  const float inv = m > 0.f ? 1.0f / m : 0.f;
+  f.norm[s] = m;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 h = __floats2half2_rn(v[4 * j + k].re * inv, v[4 * j + k].im * inv);
+      w[k] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    f.p[(size_t)j * V + s] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// ---------------------------------------------------------------- gauge field views
+//
+//   FP64, 18 reals: double2 [4][9][V]  (component k = 3*row + col)
+//   FP32, 18 reals: float2  [4][9][V]
+//   FP32, 12 reals: float4  [4][3][V]  (rows 0 and 1; pair j holds components 2j, 2j+1)
+
+template <typename R, bool C12>
+struct GaugeRef;
+
+template <>
+struct GaugeRef<double, false> {
+  const double2* p;
+};
+
+template <>
+struct GaugeRef<float, false> {
+  const float2* p;
+};
+
+template <>
+struct GaugeRef<float, true> {
+  const float4* p;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return cx<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> conj_(Cx<R> a) {
+  return cx<R>(a.re, -a.im);
+}
+
+// row 2 of an SU(3) matrix from rows 0 and 1: conj(row0 x row1)
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(Cx<R> (&u)[9]) {
+  const Cx<R> a = cmul(u[1], u[5]), b = cmul(u[2], u[4]);
+  const Cx<R> c = cmul(u[2], u[3]), d = cmul(u[0], u[5]);
+  const Cx<R> e = cmul(u[0], u[4]), f = cmul(u[1], u[3]);
+  u[6] = cx<R>(a.re - b.re, -(a.im - b.im));
+  u[7] = cx<R>(c.re - d.re, -(c.im - d.im));
+  u[8] = cx<R>(e.re - f.re, -(e.im - f.im));
+}
+
+__device__ __forceinline__ void load_link(const GaugeRef<double, false>& g, int mu, int s, int V,
+                                          Cx<double> (&u)[9]) {
+  const double2* base = g.p + (size_t)mu * 9 * V + s;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double2 d = __ldg(base + (size_t)k * V);
+    u[k] = cx(d.x, d.y);
+  }
+}
+
+__device__ __forceinline__ void load_link(const GaugeRef<float, false>& g, int mu, int s, int V,
+                                          Cx<float> (&u)[9]) {
+  const float2* base = g.p + (size_t)mu * 9 * V + s;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float2 d = __ldg(base + (size_t)k * V);
+    u[k] = cx(d.x, d.y);
+  }
+}
+
+__device__ __forceinline__ void load_link(const GaugeRef<float, true>& g, int mu, int s, int V,
+                                          Cx<float> (&u)[9]) {
+  const float4* base = g.p + (size_t)mu * 3 * V + s;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float4 d = __ldg(base + (size_t)j * V);
+    u[2 * j] = cx(d.x, d.y);
+    u[2 * j + 1] = cx(d.z, d.w);
+  }
+  reconstruct_row2(u);
+}
+
+// ---------------------------------------------------------------- spin algebra (chiral basis)
+//
+// gamma_mu = [[0, B_mu], [B_mu^dag, 0]] in 2x2 spin blocks, with
+//   B_x = -i sigma_1 = [[0,-i],[-i,0]],  B_y = -i sigma_2 = [[0,-1],[1,0]],
+//   B_z = -i sigma_3 = diag(-i, i),      B_t = 1.
+// For a hop with spin factor (1 + S gamma_mu), S = +1 or -1:
+//   upper = psi_u + S B psi_l =: h,   lower = psi_l + S B^dag psi_u = S B^dag h,
+// so only the two-spin half-spinor h is multiplied by the link (spin projection).
+
+template <int S, typename R>
+__device__ __forceinline__ R sg(R x) {
+  return S > 0 ? x : -x;
+}
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void spin_project(const Cx<R> (&psi)[12], Cx<R> (&h)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cx<R> p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
+    if (MU == 0) {  // B psi_l = (-i p3, -i p2); -i z = (z.im, -z.re)
+      h[c] = cx<R>(p0.re + sg<S>(p3.im), p0.im - sg<S>(p3.re));
+      h[3 + c] = cx<R>(p1.re + sg<S>(p2.im), p1.im - sg<S>(p2.re));
+    } else if (MU == 1) {  // B psi_l = (-p3, p2)
+      h[c] = cx<R>(p0.re - sg<S>(p3.re), p0.im - sg<S>(p3.im));
+      h[3 + c] = cx<R>(p1.re + sg<S>(p2.re), p1.im + sg<S>(p2.im));
+    } else if (MU == 2) {  // B psi_l = (-i p2, i p3); i z = (-z.im, z.re)
+      h[c] = cx<R>(p0.re + sg<S>(p2.im), p0.im - sg<S>(p2.re));
+      h[3 + c] = cx<R>(p1.re - sg<S>(p3.im), p1.im + sg<S>(p3.re));
+    } else {  // B psi_l = (p2, p3)
+      h[c] = cx<R>(p0.re + sg<S>(p2.re), p0.im + sg<S>(p2.im));
+      h[3 + c] = cx<R>(p1.re + sg<S>(p3.re), p1.im + sg<S>(p3.im));
+    }
+  }
+}
+
+// acc += k * [chi ; S B^dag chi]  (chi = link x h, two spins x three colours)
+template <int MU, int S, typename R>
+__device__ __forceinline__ void spin_reconstruct(Cx<R> (&acc)[12], const Cx<R> (&chi)[6], R k) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cx<R> c0 = chi[c], c1 = chi[3 + c];
+    acc[c].re = fma(k, c0.re, acc[c].re);
+    acc[c].im = fma(k, c0.im, acc[c].im);
+    acc[3 + c].re = fma(k, c1.re, acc[3 + c].re);
+    acc[3 + c].im = fma(k, c1.im, acc[3 + c].im);
+    Cx<R> l0, l1;
+    if (MU == 0) {  // B^dag chi = (i c1, i c0)
+      l0 = cx<R>(-c1.im, c1.re);
+      l1 = cx<R>(-c0.im, c0.re);
+    } else if (MU == 1) {  // (c1, -c0)
+      l0 = c1;
+      l1 = cx<R>(-c0.re, -c0.im);
+    } else if (MU == 2) {  // (i c0, -i c1)
+      l0 = cx<R>(-c0.im, c0.re);
+      l1 = cx<R>(c1.im, -c1.re);
+    } else {  // (c0, c1)
+      l0 = c0;
+      l1 = c1;
+    }
+    acc[6 + c].re = fma(k, sg<S>(l0.re), acc[6 + c].re);
+    acc[6 + c].im = fma(k, sg<S>(l0.im), acc[6 + c].im);
+    acc[9 + c].re = fma(k, sg<S>(l1.re), acc[9 + c].re);
+    acc[9 + c].im = fma(k, sg<S>(l1.im), acc[9 + c].im);
+  }
+}
+
+// chi = U h (per spin), U row-major 3x3
+template <typename R>
+__device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6], Cx<R> (&chi)[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const Cx<R> u0 = u[3 * a], u1 = u[3 * a + 1], u2 = u[3 * a + 2];
+      const Cx<R> h0 = h[3 * sp], h1 = h[3 * sp + 1], h2 = h[3 * sp + 2];
+      R re = u0.re * h0.re;
+      re = fma(-u0.im, h0.im, re);
+      re = fma(u1.re, h1.re, re);
+      re = fma(-u1.im, h1.im, re);
+      re = fma(u2.re, h2.re, re);
+      re = fma(-u2.im, h2.im, re);
+      R im = u0.re * h0.im;
+      im = fma(u0.im, h0.re, im);
+      im = fma(u1.re, h1.im, im);
+      im = fma(u1.im, h1.re, im);
+      im = fma(u2.re, h2.im, im);
+      im = fma(u2.im, h2.re, im);
+      chi[3 * sp + a] = cx<R>(re, im);
+    }
+  }
+}
+
+// chi = U^dag h: chi_a = sum_b conj(U_ba) h_b
+template <typename R>
+__device__ __forceinline__ void su3_dag_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6], Cx<R> (&chi)[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const Cx<R> u0 = u[a], u1 = u[3 + a], u2 = u[6 + a];
+      const Cx<R> h0 = h[3 * sp], h1 = h[3 * sp + 1], h2 = h[3 * sp + 2];
+      R re = u0.re * h0.re;
+      re = fma(u0.im, h0.im, re);
+      re = fma(u1.re, h1.re, re);
+      re = fma(u1.im, h1.im, re);
+      re = fma(u2.re, h2.re, re);
+      re = fma(u2.im, h2.im, re);
+      R im = u0.re * h0.im;
+      im = fma(-u0.im, h0.re, im);
+      im = fma(u1.re, h1.im, im);
+      im = fma(-u1.im, h1.re, im);
+      im = fma(u2.re, h2.im, im);
+      im = fma(-u2.im, h2.re, im);
+      chi[3 * sp + a] = cx<R>(re, im);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- deterministic grid reductions
+//
+// Every block reduces its threads' values with a fixed shuffle tree, stores one partial per block,
+// and takes a ticket. The block that draws the last ticket (ticket % gridDim == gridDim - 1) sums
+// the partials in a fixed order and publishes the result: the same grid always gives the same
+// bits, whatever order the blocks ran in. No block waits for another, so nothing can hang.
+
+struct OpSum {
+  static __device__ __forceinline__ double identity() { return 0.0; }
+  static __device__ __forceinline__ double apply(double a, double b) { return a + b; }
+};
+
+struct OpMax {
+  static __device__ __forceinline__ double identity() { return 0.0; }  // used for non-negative values
+  static __device__ __forceinline__ double apply(double a, double b) { return fmax(a, b); }
+};
+
+template <typename Op, int N>
+__device__ __forceinline__ void block_reduce(double (&v)[N], double* smem /* [N][32] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] = Op::apply(v[i], __shfl_down_sync(0xffffffffu, v[i], off));
+  }
+  __syncthreads();  // smem may still be read by a previous reduction in this kernel
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) smem[i * 32 + wid] = v[i];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double t = lane < nw ? smem[i * 32 + lane] : Op::identity();
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t = Op::apply(t, __shfl_down_sync(0xffffffffu, t, off));
+      v[i] = t;  // valid in thread 0
+    }
+  }
+}
+
+// Reduce v over the whole grid. Must be reached by every thread of every block.
+// Returns true in every thread of the single block that finished last; in that block's thread 0,
+// total[] holds the grid-wide result. partials must hold N * gridDim.x doubles.
+template <typename Op, int N>
+__device__ __forceinline__ bool grid_reduce(double (&v)[N], double* partials, unsigned* ticket,
+                                            double (&total)[N]) {
+  __shared__ double smem[N * 32];
+  __shared__ int is_last;
+  block_reduce<Op, N>(v, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = v[i];
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    is_last = (t % gridDim.x) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double w[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    w[i] = Op::identity();
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      w[i] = Op::apply(w[i], __ldcg(partials + (size_t)i * gridDim.x + b));
+  }
+  block_reduce<Op, N>(w, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) total[i] = w[i];
+    atomicExch(ticket, 0u);
+  }
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ double norm2_site(const Cx<R> (&v)[12]) {
+  R a = 0;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    a = fma(v[c].re, v[c].re, a);
+    a = fma(v[c].im, v[c].im, a);
+  }
+  return (double)a;
+}
+
+}  // namespace wdk

@@ -1,0 +1,125 @@
+// Host-visible interface between the C ABI (wd_api.cu) and the kernel translation units.
+// Plain structs and launcher declarations only; no device code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wdk {
+
+struct Geom;  // defined in wd_device.cuh; mirrored by GeomH below
+
+// Same memory layout as wdk::Geom.
+struct GeomH {
+  int L[4];
+  int stride[4];
+  int V;
+  int bc[4];
+};
+
+enum { SP64 = 0, SP32 = 1, SP16 = 2 };  // spinor storage precisions (match wd_device.cuh)
+
+// A spinor field in the device layout.
+struct FieldPtr {
+  void* p;
+  float* norm;  // P16 only
+  int prec;
+};
+
+// A gauge field in the device layout.
+struct GaugePtr {
+  const void* p;
+  int prec;  // SP64 (18 reals) or SP32
+  int c12;   // SP32 only: 1 = 12 reals
+};
+
+// Device-resident solver scalars (one per context). Layout shared with the kernels.
+struct CgScalars {
+  double eta2;       // ||eta||^2
+  double rr;         // recursive ||r||^2
+  double qq;         // ||D p||^2
+  double gamma;      // ||D^dag r||^2 of the current direction
+  double gamma_new;  // ||D^dag r||^2 after the r update
+  double alpha;
+  double beta;
+  double tol2;       // tol^2 (relative, squared) of the current launch
+  double rr_true;    // ||eta - D x||^2 recomputed
+  double max_dev;    // gauge unitarity check
+  double rr_ref;     // mixed precision: ||r||^2 at the last reliable update
+  double delta2;     // mixed precision: reliable-update trigger factor, squared
+  double scratch[4];
+  int iter;          // cumulative iterations
+  int maxit;
+  int status;        // ST_* below
+  int updates;       // reliable updates done
+  int need_update;   // mixed precision: set when ||r|| dropped by delta since the last update
+  int no_update;     // = !need_update (skip flag of the FP64 dslash in the update)
+  int pad[2];
+  unsigned ticket[16];
+};
+
+enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_BREAKDOWN = 3 };
+
+// ticket slots (each kernel role uses its own counter)
+enum { TK_DSLASH_A = 0, TK_DSLASH_B = 1, TK_UPD_R = 2, TK_UPD_XP = 3, TK_PACK = 4, TK_GAUGE = 5,
+       TK_DSLASH_C = 6, TK_MISC = 7, TK_UPD_REL = 8 };
+
+enum { EPI_PLAIN = 0, EPI_RESID = 1 };
+
+// A reduction target: result == nullptr means no reduction.
+struct Red {
+  double* partials;  // >= N * gridDim doubles
+  unsigned* ticket;
+  double* result;
+};
+
+struct DslashCall {
+  GeomH g;
+  GaugePtr u;
+  FieldPtr in, out, b;  // b: EPI_RESID only (out = b - D in)
+  double kappa;
+  int dagger;
+  int epi;
+  const int* skip;  // optional: if *skip != 0 the launch does nothing
+  Red red;          // optional |out|^2
+  int block;
+};
+
+// Launchers. Each returns cudaGetLastError() after the launch.
+cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st);
+
+// canonical complex128 [V][12] -> field; optional |src|^2 into red
+cudaError_t launch_pack(const double* canon, FieldPtr out, int V, Red red, int block, cudaStream_t st);
+// canonical complex64 [V][12] -> P32 field
+cudaError_t launch_pack_c64(const float* canon, FieldPtr out, int V, int block, cudaStream_t st);
+// field -> canonical complex128
+cudaError_t launch_unpack(FieldPtr in, double* canon, int V, int block, cudaStream_t st);
+// P32 field -> canonical complex64
+cudaError_t launch_unpack_c64(FieldPtr in, float* canon, int V, int block, cudaStream_t st);
+// canonical complex128 links [V][4][9] -> gauge field; optional max deviation from SU(3) into red
+cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, Red red, int block, cudaStream_t st);
+
+// CG pieces (prec = storage precision of all vectors involved)
+cudaError_t launch_cg_init(CgScalars* sc, int reset_iter, cudaStream_t st);
+cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond, cudaStream_t st);
+cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int V, CgScalars* sc, double* partials,
+                               int block, cudaStream_t st);
+cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int V, CgScalars* sc,
+                                double* partials, int use_cond, unsigned long long cond, int block,
+                                cudaStream_t st);
+// Mixed precision (inner W = SP32 or SP16 spinors, x_lo in SP32, outer FP64)
+cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int V, CgScalars* sc,
+                                double* partials, int use_cond, unsigned long long upd, int block, cudaStream_t st);
+// skip: pointer to CgScalars::need_update; the kernel runs only when it is non-zero (nullptr = always)
+cudaError_t launch_mp_accumulate(FieldPtr xhi, FieldPtr xlo, int V, const int* skip, int block, cudaStream_t st);
+cudaError_t launch_mp_convert(FieldPtr rhi, FieldPtr rlo, int V, CgScalars* sc, double* partials, int count,
+                              const int* skip, int block, cudaStream_t st);
+cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int V, CgScalars* sc, double* partials,
+                               int use_cond, unsigned long long cond, int block, cudaStream_t st);
+// zero `bytes` (multiple of 16) of device memory with a kernel
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+// grid size used by a launcher for V sites at a block size
+inline int grid_for(int V, int block) { return (V + block - 1) / block; }
+
+}  // namespace wdk

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the C ABI in include/wd.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``libwdcg.so``; this module only converts torch
+tensors to pointers and status codes to exceptions. Importing it fails loudly if the library has
+not been built (``python -m paper_2111_14958_gb300.build``): there is no CPU fallback.
+
+Low-level functions carry the C names (``wd_create``, ``wd_load_gauge``, ``wd_apply``,
+``cg_solve``, ...); :class:`WilsonDirac` wraps them for torch users.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwdcg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_2111_14958_gb300.build); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes (include/wd.h)
+WD_OK = 0
+WD_NOT_CONVERGED = 1
+WD_EINVAL = -1
+WD_ENOMEM = -2
+WD_ECUDA = -3
+WD_ENOTUNITARY = -4
+WD_BREAKDOWN = -5
+WD_ENOGAUGE = -6
+STATUS_NAMES = {0: "WD_OK", 1: "WD_NOT_CONVERGED", -1: "WD_EINVAL", -2: "WD_ENOMEM", -3: "WD_ECUDA",
+                -4: "WD_ENOTUNITARY", -5: "WD_BREAKDOWN", -6: "WD_ENOGAUGE"}
+
+WD_PREC_F64 = 64
+WD_PREC_F32 = 32
+WD_PREC_MIXED_F32 = 6432
+WD_PREC_MIXED_F16 = 6416
+
+WD_OPT_RELIABLE_DELTA = 1
+WD_OPT_USE_GRAPH = 2
+WD_OPT_BLOCK_DSLASH = 3
+WD_OPT_BLOCK_BLAS = 4
+WD_OPT_MAX_RESTARTS = 5
+
+
+class WdStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
+                ("dslash_calls_f64", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_sig = {
+    "wd_create": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)]),
+    "wd_destroy": (None, [_P]),
+    "wd_load_gauge": (_I, [_P, _P, _I, _I, ctypes.POINTER(_D)]),
+    "wd_apply": (_I, [_P, _P, _P, _I]),
+    "cg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "wd_set_option": (_I, [_P, _I, _D]),
+    "wd_get_stats": (_I, [_P, ctypes.POINTER(WdStats)]),
+    "wd_time_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_D)]),
+    "wd_last_error": (ctypes.c_char_p, []),
+    "wd_version": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class WdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.wd_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _check(status: int, where: str, allow=(WD_OK,)) -> int:
+    if status not in allow:
+        raise WdError(status, where)
+    return status
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ------------------------------------------------------------------ C-named functions
+
+def wd_version() -> str:
+    return _lib.wd_version().decode()
+
+
+def wd_last_error() -> str:
+    return _lib.wd_last_error().decode(errors="replace")
+
+
+def wd_create(dims, kappa: float, boundary=(1, 1, 1, -1), precision: int = WD_PREC_F64, stream=None):
+    """Create a context; returns an opaque handle (int). Raises WdError on failure."""
+    d = (_I * 4)(*[int(v) for v in dims])
+    b = (_I * 4)(*[int(v) for v in boundary]) if boundary is not None else None
+    out = _P()
+    _check(_lib.wd_create(d, float(kappa), b, int(precision), _P(_stream_handle(stream)), ctypes.byref(out)),
+           "wd_create")
+    return out.value
+
+
+def wd_destroy(ctx) -> None:
+    _lib.wd_destroy(_P(ctx))
+
+
+def wd_load_gauge(ctx, U: torch.Tensor, compress12: bool = False, check: bool = True) -> float:
+    """Load links (complex128 [Lt,Lz,Ly,Lx,4,3,3], host or device). Returns the max SU(3) deviation."""
+    if U.dtype != torch.complex128 or not U.is_contiguous():
+        raise ValueError("U must be a contiguous complex128 tensor")
+    dev = _D(0.0)
+    st = _lib.wd_load_gauge(_P(ctx), _P(_ptr(U)), int(U.is_cuda), int(compress12), ctypes.byref(dev))
+    _check(st, "wd_load_gauge", allow=(WD_OK,) if check else (WD_OK, WD_ENOTUNITARY))
+    return dev.value
+
+
+def wd_apply(ctx, inp: torch.Tensor, out: torch.Tensor, dagger: bool = False) -> None:
+    _check(_lib.wd_apply(_P(ctx), _P(_ptr(inp)), _P(_ptr(out)), int(bool(dagger))), "wd_apply")
+
+
+def cg_solve(ctx, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
+    """Returns (status, iterations, true relative residual); x is updated in place."""
+    it = _I(0)
+    res = _D(0.0)
+    st = _lib.cg_solve(_P(ctx), _P(_ptr(src)), _P(_ptr(x)), float(tol), int(maxit), ctypes.byref(it),
+                       ctypes.byref(res))
+    _check(st, "cg_solve", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
+    return st, it.value, res.value
+
+
+def wd_set_option(ctx, key: int, value: float) -> None:
+    _check(_lib.wd_set_option(_P(ctx), int(key), float(value)), "wd_set_option")
+
+
+def wd_get_stats(ctx) -> dict:
+    s = WdStats()
+    _check(_lib.wd_get_stats(_P(ctx), ctypes.byref(s)), "wd_get_stats")
+    return {name: getattr(s, name) for name, _ in WdStats._fields_}
+
+
+def wd_time_dslash(ctx, dagger: bool = False, launches: int = 20) -> float:
+    ms = _D(0.0)
+    _check(_lib.wd_time_dslash(_P(ctx), int(bool(dagger)), int(launches), ctypes.byref(ms)), "wd_time_dslash")
+    return ms.value
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class WilsonDirac:
+    """A Wilson-Dirac operator on one lattice, bound to a CUDA stream.
+
+    Fields are torch tensors in the canonical layout ``[Lt, Lz, Ly, Lx, 4, 3]`` (spinors) and
+    ``[Lt, Lz, Ly, Lx, 4, 3, 3]`` (links), complex128 (complex64 for ``apply`` at precision 32).
+    """
+
+    def __init__(self, dims, kappa, boundary=(1, 1, 1, -1), precision=WD_PREC_F64, stream=None,
+                 device="cuda"):
+        self.dims = tuple(int(d) for d in dims)
+        self.kappa = float(kappa)
+        self.boundary = tuple(boundary)
+        self.precision = int(precision)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = wd_create(self.dims, self.kappa, self.boundary, self.precision, self.stream)
+        lx, ly, lz, lt = self.dims
+        self.spinor_shape = (lt, lz, ly, lx, 4, 3)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            wd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_gauge(self, U, compress12=False, check=True) -> float:
+        return wd_load_gauge(self.ctx, U.contiguous(), compress12, check)
+
+    def apply(self, psi, dagger=False, out=None):
+        if out is None:
+            out = torch.empty_like(psi)
+        wd_apply(self.ctx, psi.contiguous(), out, dagger)
+        return out
+
+    def solve(self, src, x0=None, tol=1e-10, maxit=2000):
+        x = torch.zeros_like(src) if x0 is None else x0.clone()
+        status, iters, res = cg_solve(self.ctx, src.contiguous(), x, tol, maxit)
+        return x, iters, res, status
+
+    def set_option(self, key, value):
+        wd_set_option(self.ctx, key, value)
+
+    def stats(self):
+        return wd_get_stats(self.ctx)
+
+    def time_dslash(self, dagger=False, launches=20) -> float:
+        return wd_time_dslash(self.ctx, dagger, launches)

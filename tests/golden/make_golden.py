@@ -42,6 +42,11 @@ def main():
     }
     with open(os.path.join(HERE, "cgls_oracle.json"), "w") as f:
         json.dump(out, f, indent=1)
+    # the benchmark workload: 14^4, kappa 0.12, eps 0.4, seeds 1/2, tol 1e-10
+    rec = cgls_record((14, 14, 14, 14), 0.12, 0.4, 1, 2, 1e-10, 4000)
+    rec["what"] = "oracle CGLS solve of the benchmark workload (iteration count for extrapolation)"
+    with open(os.path.join(HERE, "bench_workload.json"), "w") as f:
+        json.dump(rec, f, indent=1)
 
 
 if __name__ == "__main__":

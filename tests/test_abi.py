@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every function include/wd.h declares (no GPU needed)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fname in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fname.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fname)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            if m.group(1) not in ("defined",):
+                names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2111_14958_gb300 import build
+    build.build()
+    import ctypes
+    return ctypes.CDLL(os.path.join(ROOT, "paper_2111_14958_gb300", "libwdcg.so"))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("wd_create", "wd_load_gauge", "wd_apply", "cg_solve", "wd_destroy", "wd_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header(lib):
+    from paper_2111_14958_gb300 import wd
+    assert set(_declared()) == set(wd.EXPORTED)
+
+
+def test_version_and_no_device_error(lib):
+    import torch
+    from paper_2111_14958_gb300 import wd
+    assert "sm_103a" in wd.wd_version()
+    if not torch.cuda.is_available():
+        with pytest.raises(wd.WdError) as e:
+            wd.wd_create((4, 4, 4, 4), 0.12, stream=0)
+        assert e.value.status == wd.WD_ECUDA
+
+
+def test_argument_validation_without_device(lib):
+    import ctypes
+    from paper_2111_14958_gb300 import wd
+    out = ctypes.c_void_p()
+    bad = (ctypes.c_int * 4)(4, 4, 1, 4)
+    assert lib.wd_create(bad, ctypes.c_double(0.12), None, 64, None, ctypes.byref(out)) == wd.WD_EINVAL
+    good = (ctypes.c_int * 4)(4, 4, 4, 4)
+    assert lib.wd_create(good, ctypes.c_double(0.12), None, 7, None, ctypes.byref(out)) == wd.WD_EINVAL
+    assert lib.wd_create(good, ctypes.c_double(1.5), None, 64, None, ctypes.byref(out)) == wd.WD_EINVAL
+    bc = (ctypes.c_int * 4)(1, 1, 1, 0)
+    assert lib.wd_create(good, ctypes.c_double(0.12), bc, 64, None, ctypes.byref(out)) == wd.WD_EINVAL
+    assert lib.wd_create(good, ctypes.c_double(0.12), None, 64, None, None) == wd.WD_EINVAL

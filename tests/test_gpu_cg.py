@@ -1,0 +1,179 @@
+"""CG solves through the C ABI, checked against the FP64 CPU oracle.
+
+Every solve's true relative residual is recomputed by the oracle in FP64 from the returned x and
+must meet the tolerance; solutions are compared with the oracle's CGLS and, at 4^4, with a dense
+direct solve.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import cg as ocg
+from oracle import freefield, wilson
+from tests.gpu_util import fields, rel, require_gpu, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+BC = (1, 1, 1, -1)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cgls_oracle.json")
+
+
+def _solve(wd, dims, kappa, prec, tol, maxit=4000, U=None, eta=None, graph=True, **opts):
+    if U is None:
+        U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, kappa, BC, prec)
+    op.load_gauge(to_dev(U), compress12=opts.pop("c12", False))
+    if not graph:
+        op.set_option(wd.WD_OPT_USE_GRAPH, 0)
+    for k, v in opts.items():
+        op.set_option(k, v)
+    x, iters, res, status = op.solve(to_dev(eta), tol=tol, maxit=maxit)
+    stats = op.stats()
+    op.close()
+    return to_np(x), iters, res, status, stats, U, eta
+
+
+def test_c1_fp64_matches_oracle_and_direct_solve():
+    wd = require_gpu()
+    with open(GOLDEN) as f:
+        golden = json.load(f)["solves"][0]
+    dims = tuple(golden["dims"])
+    x, iters, res, status, stats, U, eta = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10)
+    assert status == wd.WD_OK
+    assert ocg.true_residual(U, eta, x, 0.12) <= 1e-10
+    assert abs(res - ocg.true_residual(U, eta, x, 0.12)) < 1e-12
+    assert abs(iters - golden["iterations"]) <= 2
+    dense = wilson.dense_D(U, 0.12, BC)
+    x_direct = np.linalg.solve(dense, eta.reshape(-1))
+    assert rel(x, x_direct) < 1e-8
+
+
+@pytest.mark.parametrize("idx", [1, 2])
+def test_golden_cases_fp64(idx):
+    wd = require_gpu()
+    with open(GOLDEN) as f:
+        g = json.load(f)["solves"][idx]
+    dims = tuple(g["dims"])
+    U = synthetic.gauge_field(dims, g["eps"], g["gauge_seed"])
+    eta = synthetic.gaussian_source(dims, g["source_seed"])
+    x, iters, res, status, _, _, _ = _solve(wd, dims, g["kappa"], wd.WD_PREC_F64, g["tol"], U=U, eta=eta)
+    assert status == wd.WD_OK
+    assert ocg.true_residual(U, eta, x, g["kappa"]) <= g["tol"]
+    assert abs(iters - g["iterations"]) <= 2
+
+
+def test_c2_fp64_and_fp32_14x4():
+    wd = require_gpu()
+    dims = (14, 14, 14, 14)
+    U, eta = fields(dims)
+    x64, it64, res64, st64, _, _, _ = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta)
+    assert st64 == wd.WD_OK
+    assert ocg.true_residual(U, eta, x64, 0.12) <= 1e-10
+    x32, it32, res32, st32, _, _, _ = _solve(wd, dims, 0.12, wd.WD_PREC_F32, 1e-6, U=U, eta=eta, c12=True)
+    assert st32 == wd.WD_OK
+    assert ocg.true_residual(U, eta, x32, 0.12) <= 1.05e-6
+    assert rel(x32, x64) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["mixed32", "mixed16"])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (14, 14, 14, 14)])
+def test_mixed_precision_reaches_fp64_accuracy(prec, dims):
+    wd = require_gpu()
+    p = wd.WD_PREC_MIXED_F32 if prec == "mixed32" else wd.WD_PREC_MIXED_F16
+    U, eta = fields(dims)
+    x, iters, res, status, stats, _, _ = _solve(wd, dims, 0.12, p, 1e-10, U=U, eta=eta, c12=True)
+    assert status == wd.WD_OK, stats
+    assert ocg.true_residual(U, eta, x, 0.12) <= 1e-10
+    assert stats["reliable_updates"] >= 1
+
+
+def test_graph_and_host_loop_agree_bitwise():
+    wd = require_gpu()
+    dims = (6, 4, 4, 8)
+    U, eta = fields(dims)
+    xa, ia, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=True)
+    xb, ib, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=False)
+    xc, ic, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=True)
+    assert ia == ib == ic
+    assert np.array_equal(xa, xb) and np.array_equal(xa, xc)
+
+
+def test_mixed_graph_and_host_loop_agree():
+    wd = require_gpu()
+    dims = (6, 4, 4, 8)
+    U, eta = fields(dims)
+    xa, ia, _, _, sa, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_MIXED_F32, 1e-10, U=U, eta=eta, graph=True)
+    xb, ib, _, _, sb, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_MIXED_F32, 1e-10, U=U, eta=eta, graph=False)
+    assert ia == ib and sa["reliable_updates"] == sb["reliable_updates"]
+    assert np.array_equal(xa, xb)
+
+
+def test_free_field_solve_matches_fft():
+    wd = require_gpu()
+    dims = (8, 8, 8, 8)
+    U = synthetic.unit_gauge(dims)
+    eta = synthetic.gaussian_source(dims, 4)
+    x, _, _, status, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-12, U=U, eta=eta)
+    assert status == wd.WD_OK
+    assert rel(x, freefield.solve(eta, 0.124, BC)) < 1e-10
+
+
+def test_kappa_zero_is_one_iteration():
+    wd = require_gpu()
+    dims = (4, 2, 2, 4)
+    U, eta = fields(dims)
+    x, iters, res, status, _, _, _ = _solve(wd, dims, 0.0, wd.WD_PREC_F64, 1e-12, U=U, eta=eta)
+    assert status == wd.WD_OK and iters == 1
+    assert rel(x, eta) < 1e-15
+
+
+def test_maxit_returns_not_converged_with_iterate():
+    wd = require_gpu()
+    dims = (4, 4, 4, 4)
+    U, eta = fields(dims)
+    x, iters, res, status, _, _, _ = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, maxit=10, U=U, eta=eta)
+    assert status == wd.WD_NOT_CONVERGED and iters == 10
+    xo, _, ro, _ = ocg.cgls(U, eta, 0.12, 0.0, 10)
+    assert rel(x, xo) < 1e-10 and abs(res - ro) < 1e-10
+
+
+def test_zero_source_and_exact_guess():
+    wd = require_gpu()
+    dims = (4, 4, 2, 2)
+    U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_F64)
+    op.load_gauge(to_dev(U))
+    zero = torch.zeros(op.spinor_shape, dtype=torch.complex128, device="cuda")
+    x, iters, res, status = op.solve(zero, tol=1e-10)
+    assert status == wd.WD_OK and iters == 0 and float(x.abs().max()) == 0.0
+    # an exact initial guess needs no iteration
+    xs = to_dev(np.linalg.solve(wilson.dense_D(U, 0.12, BC), eta.reshape(-1)).reshape(eta.shape))
+    x, iters, res, status = op.solve(to_dev(eta), x0=xs, tol=1e-10)
+    assert status == wd.WD_OK and iters == 0
+    op.close()
+
+
+def test_nan_source_is_breakdown():
+    wd = require_gpu()
+    dims = (4, 4, 2, 2)
+    U, eta = fields(dims)
+    eta = eta.copy()
+    eta[0, 0, 0, 1, 2, 1] = np.nan
+    x, iters, res, status, _, _, _ = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta)
+    assert status == wd.WD_BREAKDOWN
+
+
+def test_repeated_solves_are_bitwise_identical():
+    wd = require_gpu()
+    dims = (8, 8, 8, 8)
+    U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_MIXED_F32)
+    op.load_gauge(to_dev(U), compress12=True)
+    a = op.solve(to_dev(eta), tol=1e-10)[0]
+    b = op.solve(to_dev(eta), tol=1e-10)[0]
+    assert torch.equal(a, b)
+    op.close()
