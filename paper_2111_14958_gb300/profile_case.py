@@ -1,0 +1,60 @@
+"""Small, self-contained workloads for profiling one kernel under ncu.
+
+Examples:
+  python -m paper_2111_14958_gb300.profile_case --prec 64 --dims 14,14,14,14 --launches 5
+  python -m paper_2111_14958_gb300.profile_case --prec 32 --c12 --dims 32,32,32,32 --launches 3
+  python -m paper_2111_14958_gb300.profile_case --prec 64 --dims 14,14,14,14 --solve
+
+Fields come from the seeded generators (links exp(i 0.4 H), Gaussian source); the program prints
+the timing of the dslash as the solver launches it (CUDA events) and, with --solve, one CG solve.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--prec", type=int, default=64, help="64, 32, 6432 or 6416")
+    ap.add_argument("--dims", default="14,14,14,14")
+    ap.add_argument("--c12", action="store_true")
+    ap.add_argument("--launches", type=int, default=5)
+    ap.add_argument("--dagger", action="store_true")
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--kappa", type=float, default=0.12)
+    ap.add_argument("--block", type=int, default=0)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import synthetic
+    from paper_2111_14958_gb300 import wd
+
+    dims = tuple(int(v) for v in args.dims.split(","))
+    U = torch.from_numpy(synthetic.gauge_field(dims, 0.4, 1)).cuda()
+    op = wd.WilsonDirac(dims, args.kappa, (1, 1, 1, -1), args.prec)
+    op.load_gauge(U, compress12=args.c12)
+    if args.block:
+        op.set_option(wd.WD_OPT_BLOCK_DSLASH, args.block)
+    if args.launches:
+        ms = op.time_dslash(args.dagger, args.launches)
+        print(f"dslash dims={dims} prec={args.prec} c12={args.c12}: {ms * 1e3:.2f} us per launch")
+    if args.solve:
+        eta = torch.from_numpy(synthetic.gaussian_source(dims, 2)).cuda()
+        x, iters, res, status = op.solve(eta, tol=args.tol, maxit=4000)
+        s = op.stats()
+        print(f"solve: status {status} iterations {iters} true residual {res:.3e} "
+              f"reliable updates {s['reliable_updates']} host ms {s['solve_ms']:.3f}")
+    op.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
