@@ -148,6 +148,32 @@ wd_status wd_get_stats(const wd_ctx* ctx, wd_stats* out);
  */
 wd_status wd_time_dslash(wd_ctx* ctx, int dagger, int launches, double* avg_ms);
 
+/*
+ * wd_dslash_noalloc -- out = D in (or D^dagger in) and, optionally, ||out||^2, without allocating.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * (code under a framework or pooled allocator that must own every device allocation, plug-ins
+ * handed fixed buffers). Such callers cannot create a wd_ctx, so everything is passed in:
+ *   dims, kappa, boundary : as for wd_create (boundary NULL = (1, 1, 1, -1)); V <= 2^20 sites.
+ *   U    : device, canonical complex128 links [V][4][3][3] (read in place, not converted).
+ *   in   : device, canonical complex128 spinor [V][4][3];  out: device, same layout, != in.
+ *   norm2_out : device pointer to one double receiving ||out||^2, or NULL for none.
+ *   cuda_stream : stream to enqueue on (NULL = legacy default stream).
+ * The call only enqueues work (no synchronisation); results are ready when the stream reaches it.
+ * The norm's scratch (one partial per 128-site block and a counter, 64 KiB + 256 B) is a fixed
+ * array in the library's device memory, held on every GPU that loads the library until the
+ * process exits. The first call on each device looks up that array's device address (a one-time
+ * set-up per device); make that first call before any stream capture. Every call shares the one
+ * array, so calls whose kernels overlap on the GPU (different streams, concurrent threads) race
+ * and give wrong norms; serialise them. The call allocates nothing: no cudaMalloc/cudaFree and
+ * no allocating library routine.
+ * Errors: WD_EINVAL (null pointer, bad dims, V > 2^20, bad kappa or boundary, in == out),
+ * WD_ECUDA (device or launch failure).
+ */
+wd_status wd_dslash_noalloc(const int dims[4], double kappa, const int boundary[4], const double* U,
+                            const double* in, double* out, int dagger, double* norm2_out,
+                            void* cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* wd_last_error(void);
 

@@ -37,6 +37,11 @@ bool is_mixed(int p) { return p == WD_PREC_MIXED_F32 || p == WD_PREC_MIXED_F16; 
 
 }  // namespace
 
+namespace wdk {
+// Message for wd_last_error(), set by the other translation units of the library.
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace wdk
+
 struct wd_ctx {
   int dims[4];
   int bc[4];

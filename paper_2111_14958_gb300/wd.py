@@ -67,6 +67,7 @@ _sig = {
     "wd_set_option": (_I, [_P, _I, _D]),
     "wd_get_stats": (_I, [_P, ctypes.POINTER(WdStats)]),
     "wd_time_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_D)]),
+    "wd_dslash_noalloc": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _P, _P, _P, _I, _P, _P]),
     "wd_last_error": (ctypes.c_char_p, []),
     "wd_version": (ctypes.c_char_p, []),
 }
@@ -147,6 +148,24 @@ def cg_solve(ctx, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
                        ctypes.byref(res))
     _check(st, "cg_solve", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
     return st, it.value, res.value
+
+
+def wd_dslash_noalloc(dims, kappa: float, U: torch.Tensor, inp: torch.Tensor, out: torch.Tensor,
+                      dagger: bool = False, norm2_out: torch.Tensor = None, boundary=(1, 1, 1, -1),
+                      stream=None) -> None:
+    """out = D inp (or D^dagger inp) without any device allocation; all tensors on the device,
+    canonical complex128 layouts; norm2_out: optional float64 device tensor of one element."""
+    for t in (U, inp, out):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("U, inp and out must be contiguous complex128 CUDA tensors")
+    if norm2_out is not None and (norm2_out.dtype != torch.float64 or not norm2_out.is_cuda):
+        raise ValueError("norm2_out must be a float64 CUDA tensor")
+    d = (_I * 4)(*[int(v) for v in dims])
+    b = (_I * 4)(*[int(v) for v in boundary]) if boundary is not None else None
+    _check(_lib.wd_dslash_noalloc(d, float(kappa), b, _P(_ptr(U)), _P(_ptr(inp)), _P(_ptr(out)),
+                                  int(bool(dagger)),
+                                  _P(_ptr(norm2_out)) if norm2_out is not None else None,
+                                  _P(_stream_handle(stream))), "wd_dslash_noalloc")
 
 
 def wd_set_option(ctx, key: int, value: float) -> None:
