@@ -70,7 +70,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -107,7 +107,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": "warm-up start to timed-region end, 100 ms period"}
 
 
 def make_inputs(dims, eps=EPS, gseed=GAUGE_SEED, sseed=SOURCE_SEED):
@@ -191,20 +191,23 @@ def run_native(args, rank, world):
 
     op = wd.WilsonDirac(DIMS, KAPPA, BC, wd.WD_PREC_F64, stream=stream)
     op.load_gauge(Ud)
+    if args.no_graph:
+        op.set_option(wd.WD_OPT_USE_GRAPH, 0)
 
     def step():
         op.load_gauge(Ud)
         x.zero_()
         return wd.cg_solve(op.ctx, etad, x, TOL, MAXIT)
 
-    for _ in range(max(args.warmup, 3)):
-        res = step()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     iters_seen, res_seen = [], []
+    # clocks are sampled from the start of the warm-up to the end of the timed region
     with ClockSampler(local) as clk:
+        for _ in range(max(args.warmup, 3)):
+            step()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             ev[i][0].record(stream)
@@ -267,13 +270,17 @@ def run_native(args, rank, world):
 
 
 def _profile_traffic(name):
-    """DRAM bytes per launch from a committed ncu summary, if one matches the current kernel."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel, read from
+    its ncu summary in profiles/ (the `traffic_bytes_per_launch:` line), or None."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
     try:
         with open(path) as f:
-            return json.load(f).get(name)
+            for line in f:
+                if line.startswith("traffic_bytes_per_launch:"):
+                    return int(line.split(":", 1)[1])
     except (OSError, ValueError):
         return None
+    return None
 
 
 def _e2e(args, op, U, eta, dev, stream):
@@ -370,6 +377,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--quick", action="store_true", help="only the headline step (for profiling)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the solver's kernels one by one instead of as a CUDA graph (for "
+                         "ncu launch lists, which do not list kernels inside conditional graph nodes)")
     ap.add_argument("--sweep", default="8,12,14,16,24,32")
     args = ap.parse_args()
     args.sweep = [int(v) for v in args.sweep.split(",") if v]

@@ -64,9 +64,12 @@ enum {
                                 (default 0.1), in (0, 1)                                          */
   WD_OPT_USE_GRAPH = 2,      /* 1 (default): run the CG loop as a CUDA graph with a device-side
                                 while node; 0: plain stream launches with a host poll           */
-  WD_OPT_BLOCK_DSLASH = 3,   /* threads per block of the dslash kernel (0 = tuned default)      */
+  WD_OPT_BLOCK_DSLASH = 3,   /* threads per block of the dslash kernel, 32..256 (0 = 256)       */
   WD_OPT_BLOCK_BLAS = 4,     /* threads per block of the BLAS-1 kernels (0 = default)            */
-  WD_OPT_MAX_RESTARTS = 5    /* max restarts from the true residual (default 5)                  */
+  WD_OPT_MAX_RESTARTS = 5,   /* max restarts from the true residual (default 5)                  */
+  WD_OPT_MULTI_GROUP = 6,    /* multi-RHS: right-hand sides sharing one link load (K, divides
+                                nrhs); 0 (default) = chosen by the autotuner                     */
+  WD_OPT_MULTI_SITES = 7     /* multi-RHS: sites per thread block (K * sites <= 256); 0 = tuned   */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */
@@ -80,6 +83,19 @@ typedef struct {
   double true_rel_residual;/* ||eta - D x|| / ||eta||, recomputed in the outer precision         */
   double solve_ms;         /* host wall time of cg_solve                                          */
 } wd_stats;
+
+/* Statistics of the last cg_solve_multi / wd_apply_multi, filled by wd_get_multi_stats. */
+typedef struct {
+  int nrhs;
+  int iterations;          /* loop iterations until every right-hand side stopped               */
+  int restarts;
+  int reliable_updates;    /* mixed precision: FP64 residual recomputations (all RHS at once)   */
+  int group;               /* K: right-hand sides per thread group sharing one link load         */
+  int sites_per_block;
+  int status;
+  double solve_ms;         /* host wall time of the solve                                       */
+  double dslash_ms;        /* one multi-RHS dslash launch at the tuned shape (working precision) */
+} wd_multi_stats;
 
 /*
  * Create a context for a lattice.
@@ -134,6 +150,29 @@ wd_status wd_apply(wd_ctx* ctx, const void* in, void* out, int dagger);
  */
 wd_status cg_solve(wd_ctx* ctx, const void* src, void* x, double tol, int maxit, int* iters,
                    double* true_rel_res);
+
+/*
+ * Multiple right-hand sides sharing the operator (a propagator's 12 spin-colour sources, say).
+ * Fields are nrhs canonical complex128 spinor fields back to back ([nrhs][Lt][Lz][Ly][Lx][4][3]),
+ * 1 <= nrhs <= 16. The multi-RHS dslash maps the K right-hand sides of a group to consecutive
+ * threads that read each link once; K and the block shape are autotuned on first use for a given
+ * nrhs (timed with CUDA events on the context stream) unless fixed with WD_OPT_MULTI_*.
+ *
+ * wd_apply_multi: out_r = D in_r (or D^dagger), in the context's operator precision (FP64 for
+ *   WD_PREC_F64 and the mixed modes, FP32 arithmetic on rounded inputs for WD_PREC_F32).
+ * cg_solve_multi: solves D x_r = src_r for every r with the context's solver (plain FP64, plain
+ *   FP32, or mixed precision with FP64 reliable updates applied to all right-hand sides at once
+ *   whenever one of them has dropped by delta), each right-hand side stopping on its own
+ *   tolerance; iters[r] and true_rel_res[r] (optional host arrays of nrhs) receive the iterations
+ *   each took and its true residual ||src_r - D x_r|| / ||src_r||.
+ * Returns WD_OK when every right-hand side converged, WD_NOT_CONVERGED if any reached maxit,
+ * WD_BREAKDOWN if any broke down (the others are still solved), WD_EINVAL, WD_ENOGAUGE,
+ * WD_ENOMEM (workspace: about 8 fields of nrhs right-hand sides), WD_ECUDA.
+ */
+wd_status wd_apply_multi(wd_ctx* ctx, const double* in, double* out, int nrhs, int dagger);
+wd_status cg_solve_multi(wd_ctx* ctx, const double* src, double* x, int nrhs, double tol, int maxit, int* iters,
+                         double* true_rel_res);
+wd_status wd_get_multi_stats(const wd_ctx* ctx, wd_multi_stats* out);
 
 /* Set an option (WD_OPT_*). Returns WD_EINVAL for an unknown key or a value out of range. */
 wd_status wd_set_option(wd_ctx* ctx, int key, double value);

@@ -85,6 +85,23 @@ struct wd_ctx {
   wd_stats stats;
   cudaEvent_t ev0, ev1;
   void* staging;  // host gauge uploads (kept for reuse)
+
+  // multiple right-hand sides (allocated on first use for mN right-hand sides)
+  int mN;
+  FieldPtr mx, mr, mp, mq, ms, meta;  // working precision (mixed: mx = x_lo in FP32, meta unused)
+  FieldPtr mx64, mr64, meta64;        // FP64 (F64 context: unused; mixed: outer solution/residual)
+  MCgScalars* msc;
+  MCgScalars* msc_host;
+  double* mpartials;
+  size_t mpartials_len;
+  int mK, mspb, mgrid;        // tuned launch shape of the working-precision multi-RHS dslash
+  int mK64, mspb64, mgrid64;  // ... of the FP64 one (mixed modes)
+  cudaGraph_t mgraph;
+  cudaGraphExec_t mexec;
+  bool mgraph_ready;
+  int force_mK, force_mspb;   // launch shape fixed by options (0 = autotuned)
+  int tuned_block[3];         // autotuned single-RHS dslash block size per storage precision
+  wd_multi_stats mstats;
 };
 
 namespace {
@@ -144,7 +161,8 @@ Red no_red() {
 
 int dslash_block(const wd_ctx* c, int prec) {
   if (c->block_dslash > 0) return c->block_dslash;
-  return prec == SP64 ? 128 : 256;
+  if (prec >= 0 && prec < 3 && c->tuned_block[prec] > 0) return c->tuned_block[prec];
+  return 256;
 }
 
 GaugePtr gauge_for(const wd_ctx* c, int prec) {
@@ -209,13 +227,13 @@ cudaError_t plain_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long l
   if ((e = dslash(c, c->p, c->q, 0, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
     return e;
   // alpha; r -= alpha q; |r|^2
-  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->V, sc, c->partials, bb, st)) != cudaSuccess) return e;
+  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->V, sc, c->partials, bb, c->sms, st)) != cudaSuccess) return e;
   // s = D^dag r, gamma' = |s|^2
   if ((e = dslash(c, c->r, c->s, 1, EPI_PLAIN, none_field(), &sc->gamma_new, TK_DSLASH_B, &sc->status, st)) !=
       cudaSuccess)
     return e;
   // x += alpha p; p = s + beta p; loop condition
-  return launch_cg_update_xp(c->wprec, c->x, c->p, c->s, c->V, sc, c->partials, use_cond, cond, bb, st);
+  return launch_cg_update_xp(c->wprec, c->x, c->p, c->s, c->V, sc, c->partials, use_cond, cond, bb, c->sms, st);
 }
 
 cudaError_t plain_epilogue(wd_ctx* c, cudaStream_t st) {
@@ -437,6 +455,372 @@ __global__ void set_params_kernel(CgScalars* sc, double tol2, double delta2, int
   }
 }
 
+// The paper tunes the SYCL workgroup size per device (Sec. 3.1, Fig. 1); here the dslash block
+// size is timed per context and precision on first use (CUDA events, the context's own fields).
+wd_status autotune_single(wd_ctx* c) {
+  if (c->block_dslash > 0) return WD_OK;
+  const int precs[2] = {c->wprec, (is_mixed(c->precision) ? SP64 : -1)};
+  for (int prec : precs) {
+    if (prec < 0 || c->tuned_block[prec] > 0) continue;
+    FieldPtr in = prec == c->wprec ? c->p : c->x64;
+    FieldPtr out = prec == c->wprec ? c->q : c->r64;
+    const int cands[] = {64, 128, 256};
+    float best = 1e30f;
+    int best_b = 256;
+    const int reps = prec == SP64 ? 2 : 4;
+    for (int b : cands) {
+      c->tuned_block[prec] = b;
+      WD_CUDA(dslash(c, in, out, 0, EPI_PLAIN, none_field(), &c->sc->scratch[1], TK_MISC, nullptr, c->stream));
+      WD_CUDA(cudaEventRecord(c->ev0, c->stream));
+      for (int i = 0; i < reps; ++i)
+        WD_CUDA(dslash(c, in, out, 0, EPI_PLAIN, none_field(), &c->sc->scratch[1], TK_MISC, nullptr, c->stream));
+      WD_CUDA(cudaEventRecord(c->ev1, c->stream));
+      WD_CUDA(cudaEventSynchronize(c->ev1));
+      float ms = 0.f;
+      WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      if (ms < best) {
+        best = ms;
+        best_b = b;
+      }
+    }
+    c->tuned_block[prec] = best_b;
+  }
+  return WD_OK;
+}
+
+// ---------------------------------------------------------------- multiple right-hand sides
+
+void free_multi(wd_ctx* c) {
+  if (c->mexec) cudaGraphExecDestroy(c->mexec);
+  if (c->mgraph) cudaGraphDestroy(c->mgraph);
+  c->mexec = nullptr;
+  c->mgraph = nullptr;
+  c->mgraph_ready = false;
+  FieldPtr* fs[] = {&c->mx, &c->mr, &c->mp, &c->mq, &c->ms, &c->meta, &c->mx64, &c->mr64, &c->meta64};
+  for (FieldPtr* f : fs) free_field(f);
+  if (c->mpartials) cudaFree(c->mpartials);
+  if (c->msc) cudaFree(c->msc);
+  if (c->msc_host) cudaFreeHost(c->msc_host);
+  c->mpartials = nullptr;
+  c->msc = nullptr;
+  c->msc_host = nullptr;
+  c->mN = 0;
+  c->mK = c->mK64 = 0;
+}
+
+wd_status alloc_mfield(wd_ctx* c, FieldPtr* f, int prec, int N) {
+  f->prec = prec;
+  f->norm = nullptr;
+  f->p = nullptr;
+  const size_t bytes = spinor_bytes(prec, c->V) * (size_t)N;
+  if (cudaMalloc(&f->p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WD_ENOMEM, "cudaMalloc of a multi-RHS field failed");
+  }
+  if (cudaMemsetAsync(f->p, 0, bytes, c->stream) != cudaSuccess) return fail(WD_ECUDA, "cudaMemsetAsync failed");
+  if (prec == SP16) {
+    if (cudaMalloc(&f->norm, sizeof(float) * (size_t)c->V * N) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(WD_ENOMEM, "cudaMalloc of a multi-RHS norm field failed");
+    }
+    if (cudaMemsetAsync(f->norm, 0, sizeof(float) * (size_t)c->V * N, c->stream) != cudaSuccess)
+      return fail(WD_ECUDA, "cudaMemsetAsync failed");
+  }
+  return WD_OK;
+}
+
+int mgrid_for(const wd_ctx* c, int spb) {
+  const long long need = ((long long)c->V + spb - 1) / spb;
+  const long long cap = (long long)c->sms * 16;
+  return (int)(need < cap ? need : cap);
+}
+
+wd_status ensure_multi(wd_ctx* c, int N) {
+  if (c->mN == N) return WD_OK;
+  free_multi(c);
+  const bool mixed = is_mixed(c->precision);
+  const int w = c->wprec;
+  wd_status st;
+  if ((st = alloc_mfield(c, &c->mx, mixed ? SP32 : w, N)) != WD_OK) return st;
+  if ((st = alloc_mfield(c, &c->mr, w, N)) != WD_OK) return st;
+  if ((st = alloc_mfield(c, &c->mp, w, N)) != WD_OK) return st;
+  if ((st = alloc_mfield(c, &c->mq, w, N)) != WD_OK) return st;
+  if ((st = alloc_mfield(c, &c->ms, w, N)) != WD_OK) return st;
+  if (!mixed) {
+    if ((st = alloc_mfield(c, &c->meta, w, N)) != WD_OK) return st;
+  } else {
+    if ((st = alloc_mfield(c, &c->mx64, SP64, N)) != WD_OK) return st;
+    if ((st = alloc_mfield(c, &c->mr64, SP64, N)) != WD_OK) return st;
+    if ((st = alloc_mfield(c, &c->meta64, SP64, N)) != WD_OK) return st;
+  }
+  // partials: N per block for grids up to sms * 16 blocks
+  c->mpartials_len = (size_t)N * (size_t)c->sms * 16 + 64;
+  if (cudaMalloc(&c->mpartials, sizeof(double) * c->mpartials_len) != cudaSuccess ||
+      cudaMalloc(&c->msc, sizeof(MCgScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WD_ENOMEM, "cudaMalloc of the multi-RHS reduction workspace failed");
+  }
+  if (cudaMallocHost(&c->msc_host, sizeof(MCgScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WD_ENOMEM, "pinned host allocation failed");
+  }
+  memset(c->msc_host, 0, sizeof(MCgScalars));
+  c->msc_host->nrhs = N;
+  WD_CUDA(cudaMemcpyAsync(c->msc, c->msc_host, sizeof(MCgScalars), cudaMemcpyHostToDevice, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  c->mN = N;
+  return WD_OK;
+}
+
+MDslashCall mcall(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, FieldPtr b, double* result, int slot,
+                  const int* status) {
+  MDslashCall d;
+  d.g = c->geom;
+  d.u = gauge_for(c, in.prec);
+  d.in = in;
+  d.out = out;
+  d.b = b;
+  d.kappa = c->kappa;
+  d.dagger = dagger;
+  d.epi = epi;
+  d.nrhs = c->mN;
+  const bool f64 = in.prec == SP64 && c->wprec != SP64;
+  d.group = f64 ? c->mK64 : c->mK;
+  d.sites_per_block = f64 ? c->mspb64 : c->mspb;
+  d.grid_x = f64 ? c->mgrid64 : c->mgrid;
+  d.status = status;
+  d.partials = c->mpartials;
+  d.tickets = &c->msc->ticket[slot];
+  d.result = result;
+  return d;
+}
+
+cudaError_t mdslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, FieldPtr b, double* result, int slot,
+                    const int* status, cudaStream_t st) {
+  return launch_dslash_multi(mcall(c, in, out, dagger, epi, b, result, slot, status), st);
+}
+
+// Time candidate launch shapes of the multi-RHS dslash on the context's fields; keep the fastest.
+wd_status autotune_multi(wd_ctx* c, FieldPtr in, FieldPtr out, bool f64) {
+  const int N = c->mN;
+  int bestK = N, bestS = 256 / N;
+  float best = 1e30f;
+  const int fixK = c->force_mK, fixS = c->force_mspb;
+  for (int K = 1; K <= N; ++K) {
+    if (N % K) continue;
+    if (fixK && K != fixK) continue;
+    if (f64 && K != N && !fixK) continue;  // FP64 is ALU-bound: only the full group is tried
+    const int spbs[] = {4, 8, 16, 32, 64, 128};
+    for (int spb : spbs) {
+      if (fixS && spb != fixS) continue;
+      const int block = K * spb;
+      if (block > 256 || block < 64) continue;
+      MDslashCall d = mcall(c, in, out, 0, EPI_PLAIN, none_field(), nullptr, TKM_MISC, nullptr);
+      d.group = K;
+      d.sites_per_block = spb;
+      d.grid_x = mgrid_for(c, spb);
+      WD_CUDA(launch_dslash_multi(d, c->stream));  // warm-up
+      WD_CUDA(cudaEventRecord(c->ev0, c->stream));
+      const int reps = f64 ? 1 : 3;
+      for (int i = 0; i < reps; ++i) WD_CUDA(launch_dslash_multi(d, c->stream));
+      WD_CUDA(cudaEventRecord(c->ev1, c->stream));
+      WD_CUDA(cudaEventSynchronize(c->ev1));
+      float ms = 0.f;
+      WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      ms /= reps;
+      if (ms < best) {
+        best = ms;
+        bestK = K;
+        bestS = spb;
+      }
+    }
+  }
+  if (best >= 1e29f) return fail(WD_EINVAL, "no valid multi-RHS launch shape for this nrhs and options");
+  if (f64) {
+    c->mK64 = bestK;
+    c->mspb64 = bestS;
+    c->mgrid64 = mgrid_for(c, bestS);
+  } else {
+    c->mK = bestK;
+    c->mspb = bestS;
+    c->mgrid = mgrid_for(c, bestS);
+    c->mstats.dslash_ms = best;
+  }
+  return WD_OK;
+}
+
+wd_status ensure_multi_tuned(wd_ctx* c) {
+  wd_status st;
+  if (!c->mK) {
+    if ((st = autotune_multi(c, c->mp, c->mq, false)) != WD_OK) return st;
+  }
+  if (is_mixed(c->precision) && !c->mK64) {
+    if ((st = autotune_multi(c, c->mx64, c->mr64, true)) != WD_OK) return st;
+  }
+  c->mstats.group = c->mK;
+  c->mstats.sites_per_block = c->mspb;
+  return WD_OK;
+}
+
+cudaError_t mplain_prologue(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
+  cudaError_t e;
+  MCgScalars* sc = c->msc;
+  if ((e = launch_mcg_init(sc, st)) != cudaSuccess) return e;
+  if ((e = mdslash(c, c->mx, c->mr, 0, EPI_RESID, c->meta, sc->rr, TKM_DSLASH_A, nullptr, st)) != cudaSuccess) return e;
+  if ((e = mdslash(c, c->mr, c->mp, 1, EPI_PLAIN, none_field(), sc->gamma, TKM_DSLASH_B, nullptr, st)) != cudaSuccess)
+    return e;
+  return launch_mcg_check(sc, use_cond, cond, st);
+}
+
+cudaError_t mplain_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
+  cudaError_t e;
+  MCgScalars* sc = c->msc;
+  if ((e = mdslash(c, c->mp, c->mq, 0, EPI_PLAIN, none_field(), sc->qq, TKM_DSLASH_A, sc->status, st)) != cudaSuccess)
+    return e;
+  if ((e = launch_mcg_update_r(c->wprec, c->mr, c->mq, c->mp, c->mx, c->V, sc, c->mpartials, c->mN, c->mK, c->mspb,
+                               c->mgrid, 0, 0, 0, st)) != cudaSuccess)
+    return e;
+  if ((e = mdslash(c, c->mr, c->ms, 1, EPI_PLAIN, none_field(), sc->gamma_new, TKM_DSLASH_B, sc->status, st)) !=
+      cudaSuccess)
+    return e;
+  return launch_mcg_update_xp(c->wprec, c->mx, c->mp, c->ms, c->V, sc, c->mpartials, c->mN, c->mK, c->mspb, c->mgrid,
+                              0, use_cond, cond, st);
+}
+
+cudaError_t mplain_epilogue(wd_ctx* c, cudaStream_t st) {
+  return mdslash(c, c->mx, c->mq, 0, EPI_RESID, c->meta, c->msc->rr_true, TKM_DSLASH_C, nullptr, st);
+}
+
+cudaError_t mmixed_update(wd_ctx* c, cudaStream_t st) {
+  cudaError_t e;
+  MCgScalars* sc = c->msc;
+  if ((e = launch_macc(c->mx64, c->mx, c->V, c->mN, c->mgrid, st)) != cudaSuccess) return e;
+  if ((e = mdslash(c, c->mx64, c->mr64, 0, EPI_RESID, c->meta64, sc->rr_true, TKM_DSLASH_C, sc->status, st)) !=
+      cudaSuccess)
+    return e;
+  return launch_mconv(c->mr64, c->mr, c->V, c->mN, c->mgrid, sc, 1, st);
+}
+
+cudaError_t mmixed_prologue(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
+  cudaError_t e;
+  MCgScalars* sc = c->msc;
+  if ((e = launch_mcg_init(sc, st)) != cudaSuccess) return e;
+  if ((e = mdslash(c, c->mx64, c->mr64, 0, EPI_RESID, c->meta64, sc->rr_true, TKM_DSLASH_C, nullptr, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = launch_zero(c->mx.p, spinor_bytes(SP32, c->V) * (size_t)c->mN, st)) != cudaSuccess) return e;
+  if ((e = launch_mconv(c->mr64, c->mr, c->V, c->mN, c->mgrid, sc, 0, st)) != cudaSuccess) return e;
+  if ((e = mdslash(c, c->mr, c->mp, 1, EPI_PLAIN, none_field(), sc->gamma, TKM_DSLASH_B, nullptr, st)) != cudaSuccess)
+    return e;
+  return launch_mcg_check(sc, use_cond, cond, st);
+}
+
+cudaError_t mmixed_body_a(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long upd) {
+  cudaError_t e;
+  MCgScalars* sc = c->msc;
+  if ((e = mdslash(c, c->mp, c->mq, 0, EPI_PLAIN, none_field(), sc->qq, TKM_DSLASH_A, sc->status, st)) != cudaSuccess)
+    return e;
+  return launch_mcg_update_r(c->wprec, c->mr, c->mq, c->mp, c->mx, c->V, sc, c->mpartials, c->mN, c->mK, c->mspb,
+                             c->mgrid, 1, use_cond, upd, st);
+}
+
+cudaError_t mmixed_body_b(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
+  cudaError_t e;
+  MCgScalars* sc = c->msc;
+  if ((e = mdslash(c, c->mr, c->ms, 1, EPI_PLAIN, none_field(), sc->gamma_new, TKM_DSLASH_B, sc->status, st)) !=
+      cudaSuccess)
+    return e;
+  return launch_mcg_update_xp(c->wprec, c->mx, c->mp, c->ms, c->V, sc, c->mpartials, c->mN, c->mK, c->mspb, c->mgrid,
+                              1, use_cond, cond, st);
+}
+
+cudaError_t mmixed_epilogue(wd_ctx* c, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_macc(c->mx64, c->mx, c->V, c->mN, c->mgrid, st)) != cudaSuccess) return e;
+  return mdslash(c, c->mx64, c->mr64, 0, EPI_RESID, c->meta64, c->msc->rr_true, TKM_DSLASH_C, nullptr, st);
+}
+
+wd_status build_mgraph(wd_ctx* c) {
+  if (c->mgraph_ready) return WD_OK;
+  const bool mixed = is_mixed(c->precision);
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  WD_CUDA(cudaGraphCreate(&c->mgraph, 0));
+  cudaGraphConditionalHandle loop_h;
+  WD_CUDA(cudaGraphConditionalHandleCreate(&loop_h, c->mgraph, 0, cudaGraphCondAssignDefault));
+  cudaGraph_t loop_body = nullptr;
+  wd_status st;
+  WD_CUDA(cudaStreamBeginCaptureToGraph(c->cap, c->mgraph, nullptr, nullptr, 0, mode));
+  if ((st = cap_check(mixed ? mmixed_prologue(c, c->cap, 1, loop_h) : mplain_prologue(c, c->cap, 1, loop_h),
+                      "multi prologue")) != WD_OK)
+    return st;
+  if ((st = add_conditional(c->cap, loop_h, cudaGraphCondTypeWhile, &loop_body)) != WD_OK) return st;
+  if ((st = cap_check(mixed ? mmixed_epilogue(c, c->cap) : mplain_epilogue(c, c->cap), "multi epilogue")) != WD_OK)
+    return st;
+  WD_CUDA(cudaMemcpyAsync(c->msc_host, c->msc, sizeof(MCgScalars), cudaMemcpyDeviceToHost, c->cap));
+  cudaGraph_t g = nullptr;
+  WD_CUDA(cudaStreamEndCapture(c->cap, &g));
+  WD_CUDA(cudaStreamBeginCaptureToGraph(c->cap2, loop_body, nullptr, nullptr, 0, mode));
+  if (!mixed) {
+    if ((st = cap_check(mplain_body(c, c->cap2, 1, loop_h), "multi body")) != WD_OK) return st;
+  } else {
+    cudaGraphConditionalHandle upd_h;
+    WD_CUDA(cudaGraphConditionalHandleCreate(&upd_h, loop_body, 0, cudaGraphCondAssignDefault));
+    if ((st = cap_check(mmixed_body_a(c, c->cap2, 1, upd_h), "multi body a")) != WD_OK) return st;
+    cudaGraph_t upd_body = nullptr;
+    if ((st = add_conditional(c->cap2, upd_h, cudaGraphCondTypeIf, &upd_body)) != WD_OK) return st;
+    if ((st = cap_check(mmixed_body_b(c, c->cap2, 1, loop_h), "multi body b")) != WD_OK) return st;
+    cudaGraph_t lb = nullptr;
+    WD_CUDA(cudaStreamEndCapture(c->cap2, &lb));
+    WD_CUDA(cudaStreamBeginCaptureToGraph(c->cap2, upd_body, nullptr, nullptr, 0, mode));
+    if ((st = cap_check(mmixed_update(c, c->cap2), "multi update")) != WD_OK) return st;
+  }
+  cudaGraph_t bg = nullptr;
+  WD_CUDA(cudaStreamEndCapture(c->cap2, &bg));
+  WD_CUDA(cudaGraphInstantiate(&c->mexec, c->mgraph, 0));
+  c->mgraph_ready = true;
+  return WD_OK;
+}
+
+wd_status run_mhost_loop(wd_ctx* c) {
+  const bool mixed = is_mixed(c->precision);
+  MCgScalars* sc = c->msc;
+  WD_CUDA(mixed ? mmixed_prologue(c, c->stream, 0, 0) : mplain_prologue(c, c->stream, 0, 0));
+  for (;;) {
+    WD_CUDA(cudaMemcpyAsync(c->msc_host, sc, sizeof(MCgScalars), cudaMemcpyDeviceToHost, c->stream));
+    WD_CUDA(cudaStreamSynchronize(c->stream));
+    if (!c->msc_host->any_running) break;
+    if (!mixed) {
+      WD_CUDA(mplain_body(c, c->stream, 0, 0));
+      continue;
+    }
+    WD_CUDA(mmixed_body_a(c, c->stream, 0, 0));
+    WD_CUDA(cudaMemcpyAsync(c->msc_host, sc, sizeof(MCgScalars), cudaMemcpyDeviceToHost, c->stream));
+    WD_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->msc_host->need_update) WD_CUDA(mmixed_update(c, c->stream));
+    WD_CUDA(mmixed_body_b(c, c->stream, 0, 0));
+  }
+  WD_CUDA(mixed ? mmixed_epilogue(c, c->stream) : mplain_epilogue(c, c->stream));
+  WD_CUDA(cudaMemcpyAsync(c->msc_host, sc, sizeof(MCgScalars), cudaMemcpyDeviceToHost, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return WD_OK;
+}
+
+__global__ void mset_params_kernel(MCgScalars* sc, double tol2, double delta2, int maxit) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc->tol2 = tol2;
+    sc->delta2 = delta2;
+    sc->maxit = maxit;
+    sc->iter = 0;
+    sc->updates = 0;
+    sc->any_running = 0;
+    for (int i = 0; i < kMaxRhs; ++i) {
+      sc->iters[i] = 0;
+      sc->status[i] = ST_RUNNING;
+    }
+    for (int i = 0; i < 128; ++i) sc->ticket[i] = 0u;
+  }
+}
+
 wd_status check_ctx(const wd_ctx* c) {
   if (!c) return fail(WD_EINVAL, "null context");
   return WD_OK;
@@ -532,7 +916,8 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
     if ((st = alloc_field(c, &c->r64, SP64)) != WD_OK) return bail(st);
     if ((st = alloc_field(c, &c->eta64, SP64)) != WD_OK) return bail(st);
   }
-  c->partials_len = (size_t)4 * (size_t)(4 * V / 32 + 64);
+  // the largest grid of any reduction: 12 V words at 32 threads per block, or 4 V links
+  c->partials_len = (size_t)(12 * V / 32 + 64);
   if (cudaMalloc(&c->partials, sizeof(double) * c->partials_len) != cudaSuccess ||
       cudaMalloc(&c->sc, sizeof(CgScalars)) != cudaSuccess) {
     cudaGetLastError();
@@ -554,6 +939,7 @@ void wd_destroy(wd_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   destroy_graph(c);
+  free_multi(c);
   free_field(&c->x);
   free_field(&c->r);
   free_field(&c->p);
@@ -590,12 +976,31 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
     case WD_OPT_BLOCK_DSLASH:
     case WD_OPT_BLOCK_BLAS: {
       const int b = (int)value;
-      if (value != (double)b || (b != 0 && (b < 32 || b > 1024 || b % 32))) return fail(WD_EINVAL, "block size must be 0 or a multiple of 32 in [32, 1024]");
-      if (key == WD_OPT_BLOCK_DSLASH)
+      const int bmax = key == WD_OPT_BLOCK_DSLASH ? 256 : 1024;
+      if (value != (double)b || (b != 0 && (b < 32 || b > bmax || b % 32)))
+        return fail(WD_EINVAL, "block size must be 0 or a multiple of 32 in [32, 256] (dslash) / [32, 1024] (BLAS)");
+      if (key == WD_OPT_BLOCK_DSLASH) {
         c->block_dslash = b;
-      else
+        c->tuned_block[0] = c->tuned_block[1] = c->tuned_block[2] = 0;
+      } else
         c->block_blas = b ? b : 256;
       destroy_graph(c);  // launch shapes are baked into the graph
+      return WD_OK;
+    }
+    case WD_OPT_MULTI_GROUP:
+    case WD_OPT_MULTI_SITES: {
+      const int v = (int)value;
+      if (value != (double)v || v < 0 || v > 256) return fail(WD_EINVAL, "multi-RHS shape option out of range");
+      if (key == WD_OPT_MULTI_GROUP)
+        c->force_mK = v;
+      else
+        c->force_mspb = v;
+      c->mK = c->mK64 = 0;  // re-tune (or apply the forced shape) on next use
+      if (c->mexec) cudaGraphExecDestroy(c->mexec);
+      if (c->mgraph) cudaGraphDestroy(c->mgraph);
+      c->mexec = nullptr;
+      c->mgraph = nullptr;
+      c->mgraph_ready = false;
       return WD_OK;
     }
     case WD_OPT_MAX_RESTARTS:
@@ -686,6 +1091,7 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
   if (!in || !out) return fail(WD_EINVAL, "null field pointer");
   if (in == out) return fail(WD_EINVAL, "in and out must differ");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
+  if ((st = autotune_single(c)) != WD_OK) return st;
   const int bb = c->block_blas;
   if (c->precision == WD_PREC_F32) {
     WD_CUDA(launch_pack_c64((const float*)in, c->q, c->V, bb, c->stream));
@@ -720,6 +1126,7 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
   WD_CUDA(cudaGetLastError());
   WD_CUDA(launch_pack((const double*)src, eta, c->V, red_to(c, TK_PACK, &sc->eta2), bb, c->stream));
   WD_CUDA(launch_pack((const double*)x, xs, c->V, no_red(), bb, c->stream));
+  if ((st = autotune_single(c)) != WD_OK) return st;
   if (c->use_graph) {
     if ((st = build_graph(c)) != WD_OK) return st;
   }
@@ -782,6 +1189,7 @@ wd_status wd_time_dslash(wd_ctx* c, int dagger, int launches, double* avg_ms) {
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!avg_ms || launches <= 0) return fail(WD_EINVAL, "bad arguments");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
+  if ((st = autotune_single(c)) != WD_OK) return st;
   // the solver's dominant dslash: the working precision one, with its fused norm
   FieldPtr in = c->p, out = c->q;
   WD_CUDA(dslash(c, in, out, dagger, EPI_PLAIN, none_field(), &c->sc->scratch[0], TK_MISC, nullptr, c->stream));
@@ -794,6 +1202,115 @@ wd_status wd_time_dslash(wd_ctx* c, int dagger, int launches, double* avg_ms) {
   WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   *avg_ms = (double)ms / launches;
   return WD_OK;
+}
+
+wd_status wd_get_multi_stats(const wd_ctx* c, wd_multi_stats* out) {
+  if (!c || !out) return fail(WD_EINVAL, "null argument");
+  *out = c->mstats;
+  return WD_OK;
+}
+
+wd_status wd_apply_multi(wd_ctx* c, const double* in, double* out, int nrhs, int dagger) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!in || !out || in == out) return fail(WD_EINVAL, "null or aliased field pointer");
+  if (nrhs < 1 || nrhs > kMaxRhs) return fail(WD_EINVAL, "nrhs must be in [1, 16]");
+  if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
+  if ((st = ensure_multi(c, nrhs)) != WD_OK) return st;
+  if ((st = ensure_multi_tuned(c)) != WD_OK) return st;
+  const bool mixed = is_mixed(c->precision);
+  FieldPtr a = mixed ? c->mx64 : c->mq;
+  FieldPtr b = mixed ? c->mr64 : c->ms;
+  const int grid = mixed ? c->mgrid64 : c->mgrid;
+  WD_CUDA(launch_mpack(in, a, c->V, nrhs, grid, nullptr, nullptr, nullptr, c->stream));
+  WD_CUDA(mdslash(c, a, b, dagger ? 1 : 0, EPI_PLAIN, none_field(), nullptr, TKM_MISC, nullptr, c->stream));
+  WD_CUDA(launch_munpack(b, out, c->V, nrhs, grid, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  c->mstats.nrhs = nrhs;
+  return WD_OK;
+}
+
+wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, double tol, int maxit, int* iters,
+                         double* true_rel_res) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!src || !x) return fail(WD_EINVAL, "null field pointer");
+  if (nrhs < 1 || nrhs > kMaxRhs) return fail(WD_EINVAL, "nrhs must be in [1, 16]");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(WD_EINVAL, "tol must be a positive finite number");
+  if (maxit < 0 || maxit > 10000000) return fail(WD_EINVAL, "maxit must be in [0, 10^7]");
+  if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
+  const auto t0 = std::chrono::steady_clock::now();
+  if ((st = ensure_multi(c, nrhs)) != WD_OK) return st;
+  if ((st = ensure_multi_tuned(c)) != WD_OK) return st;
+  const bool mixed = is_mixed(c->precision);
+  MCgScalars* sc = c->msc;
+  FieldPtr eta = mixed ? c->meta64 : c->meta;
+  FieldPtr xs = mixed ? c->mx64 : c->mx;
+  mset_params_kernel<<<1, 32, 0, c->stream>>>(sc, tol * tol, c->delta * c->delta, maxit);
+  WD_CUDA(cudaGetLastError());
+  WD_CUDA(launch_mpack(src, eta, c->V, nrhs, c->mgrid, c->mpartials, &sc->ticket[TKM_PACK], sc->eta2, c->stream));
+  WD_CUDA(launch_mpack(x, xs, c->V, nrhs, c->mgrid, nullptr, nullptr, nullptr, c->stream));
+  if (c->use_graph) {
+    if ((st = build_mgraph(c)) != WD_OK) {
+      abort_capture(c->cap);
+      abort_capture(c->cap2);
+      if (c->mexec) cudaGraphExecDestroy(c->mexec);
+      if (c->mgraph) cudaGraphDestroy(c->mgraph);
+      c->mexec = nullptr;
+      c->mgraph = nullptr;
+      return st;
+    }
+  }
+  int restarts = 0;
+  bool any_break = false, any_maxit = false, all_conv = false;
+  for (;;) {
+    if (c->use_graph) {
+      WD_CUDA(cudaGraphLaunch(c->mexec, c->stream));
+      WD_CUDA(cudaStreamSynchronize(c->stream));
+    } else {
+      if ((st = run_mhost_loop(c)) != WD_OK) return st;
+    }
+    const MCgScalars& h = *c->msc_host;
+    any_break = any_maxit = false;
+    all_conv = true;
+    for (int r = 0; r < nrhs; ++r) {
+      const double rel = h.eta2[r] > 0.0 ? std::sqrt(h.rr_true[r] / h.eta2[r]) : std::sqrt(h.rr_true[r]);
+      if (h.status[r] == ST_BREAKDOWN || !std::isfinite(rel) || !std::isfinite(h.eta2[r])) {
+        any_break = true;
+        all_conv = false;
+      } else if (rel > tol) {
+        all_conv = false;
+        if (h.status[r] == ST_MAXIT) any_maxit = true;
+      }
+    }
+    if (all_conv || any_break || any_maxit) break;
+    if (h.iter >= maxit || restarts >= c->max_restarts) {
+      any_maxit = true;
+      break;
+    }
+    ++restarts;
+  }
+  WD_CUDA(launch_munpack(xs, x, c->V, nrhs, c->mgrid, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  const MCgScalars& h = *c->msc_host;
+  for (int r = 0; r < nrhs; ++r) {
+    const double rel = h.eta2[r] > 0.0 ? std::sqrt(h.rr_true[r] / h.eta2[r]) : std::sqrt(h.rr_true[r]);
+    if (iters) iters[r] = h.iters[r];
+    if (true_rel_res) true_rel_res[r] = rel;
+  }
+  const auto t1 = std::chrono::steady_clock::now();
+  c->mstats.nrhs = nrhs;
+  c->mstats.iterations = h.iter;
+  c->mstats.restarts = restarts;
+  c->mstats.reliable_updates = h.updates;
+  c->mstats.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  wd_status ret = WD_OK;
+  if (any_break)
+    ret = fail(WD_BREAKDOWN, "CG breakdown in at least one right-hand side (NaN/Inf in a source?)");
+  else if (!all_conv)
+    ret = fail(WD_NOT_CONVERGED, "maximum iterations reached before every right-hand side met tol");
+  c->mstats.status = ret;
+  return ret;
 }
 
 }  // extern "C"

@@ -361,8 +361,9 @@ cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond
 }
 
 cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int V, CgScalars* sc, double* partials, int block,
-                               cudaStream_t st) {
+                               int sms, cudaStream_t st) {
   const int grid = grid_for(V, block);
+  (void)sms;
   switch (prec) {
     case SP64: cg_update_r_kernel<P64><<<grid, block, 0, st>>>(view<P64>(r), view<P64>(q), V, sc, partials); break;
     case SP32: cg_update_r_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), V, sc, partials); break;
@@ -373,10 +374,11 @@ cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int V, CgScalar
 }
 
 cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int V, CgScalars* sc,
-                                double* partials, int use_cond, unsigned long long cond, int block,
+                                double* partials, int use_cond, unsigned long long cond, int block, int sms,
                                 cudaStream_t st) {
   const int grid = grid_for(V, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
+  (void)sms;
   switch (prec) {
     case SP64:
       cg_update_xp_kernel<P64><<<grid, block, 0, st>>>(view<P64>(x), view<P64>(p), view<P64>(s), V, sc, partials,

@@ -72,8 +72,18 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, int s, co
   }
 }
 
+// Occupancy: the kernel is latency-bound at large volumes (memory-level parallelism comes from
+// resident warps), so registers are capped for 3 blocks of 256 threads per SM in FP32/FP16
+// (24 warps) and 2 in FP64 (whose FP64 pipe saturates with few warps).
+constexpr int kDslashMaxThreads = 256;
+template <int SP>
+struct DslashMinBlocks {
+  static constexpr int value = SP == P64 ? 2 : 3;
+};
+
 template <int SP, bool C12, bool DAG, int EPI, bool NORM>
-__global__ void dslash_kernel(const DslashArgs<SP, C12> a) {
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
+    dslash_kernel(const DslashArgs<SP, C12> a) {
   typedef typename RealOf<SP>::type R;
   if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
   const int V = a.g.V;
@@ -149,6 +159,7 @@ static cudaError_t launch_p(const DslashCall& c, cudaStream_t st) {
 }
 
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32) return cudaErrorInvalidValue;
   if (c.in.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;
     return launch_p<P64, false>(c, st);

@@ -58,7 +58,7 @@ struct CgScalars {
   unsigned ticket[16];
 };
 
-enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_BREAKDOWN = 3 };
+enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_BREAKDOWN = 3, ST_PENDING = 4 };
 
 // ticket slots (each kernel role uses its own counter)
 enum { TK_DSLASH_A = 0, TK_DSLASH_B = 1, TK_UPD_R = 2, TK_UPD_XP = 3, TK_PACK = 4, TK_GAUGE = 5,
@@ -102,10 +102,11 @@ cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, Red red,
 // CG pieces (prec = storage precision of all vectors involved)
 cudaError_t launch_cg_init(CgScalars* sc, int reset_iter, cudaStream_t st);
 cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond, cudaStream_t st);
+// sms: SM count of the device (sizes the grid of the element-wise FP64/FP32 kernels)
 cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int V, CgScalars* sc, double* partials,
-                               int block, cudaStream_t st);
+                               int block, int sms, cudaStream_t st);
 cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int V, CgScalars* sc,
-                                double* partials, int use_cond, unsigned long long cond, int block,
+                                double* partials, int use_cond, unsigned long long cond, int block, int sms,
                                 cudaStream_t st);
 // Mixed precision (inner W = SP32 or SP16 spinors, x_lo in SP32, outer FP64)
 cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int V, CgScalars* sc,
@@ -118,6 +119,59 @@ cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int V, CgScala
                                int use_cond, unsigned long long cond, int block, cudaStream_t st);
 // zero `bytes` (multiple of 16) of device memory with a kernel
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+// ---------------------------------------------------------------- multiple right-hand sides
+
+constexpr int kMaxRhs = 16;
+
+// Per-RHS solver scalars for the multi-RHS CG (one per context).
+struct MCgScalars {
+  double eta2[kMaxRhs], rr[kMaxRhs], qq[kMaxRhs], gamma[kMaxRhs], gamma_new[kMaxRhs];
+  double alpha[kMaxRhs], rr_true[kMaxRhs], rr_ref[kMaxRhs];
+  double tol2, delta2;
+  int status[kMaxRhs];  // ST_* per right-hand side
+  int iters[kMaxRhs];   // iterations in which the right-hand side was updated
+  int need[kMaxRhs];    // mixed precision: reliable update requested
+  int nrhs, iter, maxit, any_running, need_update, no_update, updates, pad;
+  unsigned ticket[128];
+};
+
+// ticket slots: the per-group slots take kMaxRhs entries each
+enum { TKM_DSLASH_A = 0, TKM_DSLASH_B = 16, TKM_DSLASH_C = 32, TKM_UPD_R = 48, TKM_UPD_XP = 64, TKM_PACK = 80,
+       TKM_GROUPS = 96, TKM_GROUPS2 = 97, TKM_MISC = 112 };
+
+struct MDslashCall {
+  GeomH g;
+  GaugePtr u;
+  FieldPtr in, out, b;  // layout [unit][V][nrhs]
+  double kappa;
+  int dagger, epi;
+  int nrhs;             // right-hand sides in the fields
+  int group;            // K: right-hand sides per thread group (divides nrhs)
+  int sites_per_block;  // block = group * sites_per_block <= 256
+  int grid_x;           // blocks per group (grid-stride over sites)
+  const int* status;    // optional per-RHS status mask (only ST_RUNNING computed)
+  double* partials;     // >= nrhs * grid_x
+  unsigned* tickets;    // >= nrhs / group counters
+  double* result;       // optional per-RHS |out|^2
+};
+
+cudaError_t launch_dslash_multi(const MDslashCall& c, cudaStream_t st);
+// canonical N fields back to back (complex128 [N][V][12]) <-> [unit][V][N]; block = N * (256 / N)
+cudaError_t launch_mpack(const double* canon, FieldPtr out, int V, int N, int grid_x, double* partials,
+                         unsigned* tickets, double* result, cudaStream_t st);
+cudaError_t launch_munpack(FieldPtr in, double* canon, int V, int N, int grid_x, cudaStream_t st);
+cudaError_t launch_mcg_init(MCgScalars* sc, cudaStream_t st);
+cudaError_t launch_mcg_check(MCgScalars* sc, int use_cond, unsigned long long cond, cudaStream_t st);
+cudaError_t launch_mcg_update_r(int prec, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int V, MCgScalars* sc,
+                                double* partials, int N, int K, int spb, int grid_x, int mixed, int use_cond,
+                                unsigned long long upd, cudaStream_t st);
+cudaError_t launch_mcg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int V, MCgScalars* sc, double* partials,
+                                 int N, int K, int spb, int grid_x, int mixed, int use_cond, unsigned long long cond,
+                                 cudaStream_t st);
+cudaError_t launch_macc(FieldPtr xhi, FieldPtr xlo, int V, int N, int grid_x, cudaStream_t st);
+cudaError_t launch_mconv(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x, MCgScalars* sc, int count,
+                         cudaStream_t st);
 
 // grid size used by a launcher for V sites at a block size
 inline int grid_for(int V, int block) { return (V + block - 1) / block; }

@@ -48,6 +48,16 @@ WD_OPT_BLOCK_BLAS = 4
 WD_OPT_MAX_RESTARTS = 5
 
 
+WD_OPT_MULTI_GROUP = 6
+WD_OPT_MULTI_SITES = 7
+
+
+class WdMultiStats(ctypes.Structure):
+    _fields_ = [("nrhs", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("group", ctypes.c_int), ("sites_per_block", ctypes.c_int),
+                ("status", ctypes.c_int), ("solve_ms", ctypes.c_double), ("dslash_ms", ctypes.c_double)]
+
+
 class WdStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
@@ -67,6 +77,9 @@ _sig = {
     "wd_set_option": (_I, [_P, _I, _D]),
     "wd_get_stats": (_I, [_P, ctypes.POINTER(WdStats)]),
     "wd_time_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_D)]),
+    "wd_apply_multi": (_I, [_P, _P, _P, _I, _I]),
+    "cg_solve_multi": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "wd_get_multi_stats": (_I, [_P, ctypes.POINTER(WdMultiStats)]),
     "wd_dslash_noalloc": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _P, _P, _P, _I, _P, _P]),
     "wd_last_error": (ctypes.c_char_p, []),
     "wd_version": (ctypes.c_char_p, []),
@@ -148,6 +161,35 @@ def cg_solve(ctx, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
                        ctypes.byref(res))
     _check(st, "cg_solve", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
     return st, it.value, res.value
+
+
+def _check_multi(t: torch.Tensor, name: str) -> int:
+    if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.dim() != 7:
+        raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor [nrhs, Lt, Lz, Ly, Lx, 4, 3]")
+    return t.shape[0]
+
+
+def wd_apply_multi(ctx, inp: torch.Tensor, out: torch.Tensor, dagger: bool = False) -> None:
+    n = _check_multi(inp, "inp")
+    _check_multi(out, "out")
+    _check(_lib.wd_apply_multi(_P(ctx), _P(_ptr(inp)), _P(_ptr(out)), n, int(bool(dagger))), "wd_apply_multi")
+
+
+def cg_solve_multi(ctx, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
+    """Returns (status, iterations per RHS, true relative residual per RHS); x updated in place."""
+    n = _check_multi(src, "src")
+    _check_multi(x, "x")
+    it = (_I * n)()
+    res = (_D * n)()
+    st = _lib.cg_solve_multi(_P(ctx), _P(_ptr(src)), _P(_ptr(x)), n, float(tol), int(maxit), it, res)
+    _check(st, "cg_solve_multi", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
+    return st, list(it), list(res)
+
+
+def wd_get_multi_stats(ctx) -> dict:
+    s = WdMultiStats()
+    _check(_lib.wd_get_multi_stats(_P(ctx), ctypes.byref(s)), "wd_get_multi_stats")
+    return {name: getattr(s, name) for name, _ in WdMultiStats._fields_}
 
 
 def wd_dslash_noalloc(dims, kappa: float, U: torch.Tensor, inp: torch.Tensor, out: torch.Tensor,
@@ -238,3 +280,17 @@ class WilsonDirac:
 
     def time_dslash(self, dagger=False, launches=20) -> float:
         return wd_time_dslash(self.ctx, dagger, launches)
+
+    def apply_multi(self, psi, dagger=False, out=None):
+        if out is None:
+            out = torch.empty_like(psi)
+        wd_apply_multi(self.ctx, psi.contiguous(), out, dagger)
+        return out
+
+    def solve_multi(self, src, x0=None, tol=1e-10, maxit=2000):
+        x = torch.zeros_like(src) if x0 is None else x0.clone()
+        status, iters, res = cg_solve_multi(self.ctx, src.contiguous(), x, tol, maxit)
+        return x, iters, res, status
+
+    def multi_stats(self):
+        return wd_get_multi_stats(self.ctx)

@@ -22,14 +22,14 @@ BC = (1, 1, 1, -1)
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cgls_oracle.json")
 
 
-def _solve(wd, dims, kappa, prec, tol, maxit=4000, U=None, eta=None, graph=True, **opts):
+def _solve(wd, dims, kappa, prec, tol, maxit=4000, U=None, eta=None, graph=True, c12=False, options=None):
     if U is None:
         U, eta = fields(dims)
     op = wd.WilsonDirac(dims, kappa, BC, prec)
-    op.load_gauge(to_dev(U), compress12=opts.pop("c12", False))
+    op.load_gauge(to_dev(U), compress12=c12)
     if not graph:
         op.set_option(wd.WD_OPT_USE_GRAPH, 0)
-    for k, v in opts.items():
+    for k, v in (options or {}).items():
         op.set_option(k, v)
     x, iters, res, status = op.solve(to_dev(eta), tol=tol, maxit=maxit)
     stats = op.stats()
@@ -95,9 +95,11 @@ def test_graph_and_host_loop_agree_bitwise():
     wd = require_gpu()
     dims = (6, 4, 4, 8)
     U, eta = fields(dims)
-    xa, ia, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=True)
-    xb, ib, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=False)
-    xc, ic, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=True)
+    # a fixed block size: the reduction tree (hence the last bits of every scalar) depends on it
+    fix = {wd.WD_OPT_BLOCK_DSLASH: 128}
+    xa, ia, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=True, options=fix)
+    xb, ib, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=False, options=fix)
+    xc, ic, _, _, _, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=True, options=fix)
     assert ia == ib == ic
     assert np.array_equal(xa, xb) and np.array_equal(xa, xc)
 
@@ -106,8 +108,9 @@ def test_mixed_graph_and_host_loop_agree():
     wd = require_gpu()
     dims = (6, 4, 4, 8)
     U, eta = fields(dims)
-    xa, ia, _, _, sa, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_MIXED_F32, 1e-10, U=U, eta=eta, graph=True)
-    xb, ib, _, _, sb, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_MIXED_F32, 1e-10, U=U, eta=eta, graph=False)
+    fix = {wd.WD_OPT_BLOCK_DSLASH: 128}
+    xa, ia, _, _, sa, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_MIXED_F32, 1e-10, U=U, eta=eta, graph=True, options=fix)
+    xb, ib, _, _, sb, _, _ = _solve(wd, dims, 0.124, wd.WD_PREC_MIXED_F32, 1e-10, U=U, eta=eta, graph=False, options=fix)
     assert ia == ib and sa["reliable_updates"] == sb["reliable_updates"]
     assert np.array_equal(xa, xb)
 
