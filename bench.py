@@ -262,6 +262,8 @@ def run_native(args, rank, world):
         out["mixed_f32"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_MIXED_F32, TOL, c12=True)
         out["mixed_f16"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_MIXED_F16, TOL, c12=True)
         out["dslash_sweep"] = _sweep(wd, dev, stream, args.sweep)
+        out["mixed_32x64"] = _mixed_32x64(wd, dev, stream)
+        out["multi_rhs_24x48"] = _multi_24x48(wd, dev, stream)
         out["cpu_baseline"] = _cpu_baseline(iters)
     op.close()
     if rank == 0:
@@ -335,24 +337,105 @@ def _variant(wd, U, eta, dev, stream, prec, tol, c12):
 
 
 def _sweep(wd, dev, stream, sizes):
-    import torch
+    """Stand-alone dslash bandwidth sweep (links generated on the device, same recipe)."""
     out = []
     for L in sizes:
         dims = (L, L, L, L)
-        U, psi = make_inputs(dims)
-        Ud = torch.from_numpy(U).to(dev)
         V = L ** 4
         row = {"L": L, "V": V}
         for name, prec, c12, bps in (("f64_18r", wd.WD_PREC_F64, False, 960), ("f32_18r", wd.WD_PREC_F32, False, 480),
-                                     ("f32_12r", wd.WD_PREC_F32, True, 384)):
+                                     ("f32_12r", wd.WD_PREC_F32, True, 384), ("f16_12r", wd.WD_PREC_MIXED_F16, True, 296)):
             op = wd.WilsonDirac(dims, KAPPA, BC, prec, stream=stream)
-            op.load_gauge(Ud, compress12=c12)
+            op.generate_gauge(EPS, GAUGE_SEED, compress12=c12)
             ms = op.time_dslash(False, 50 if L >= 24 else 200)
             op.close()
             row[name] = {"ms": ms, "gbs": bps * V / (ms * 1e-3) / 1e9,
                          "gflops": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e9}
         out.append(row)
-        del Ud
+    return out
+
+
+def _timed_solve(op, wd, eta, tol, repeats=1):
+    import torch
+    x = torch.zeros_like(eta)
+    best = None
+    for _ in range(repeats):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, res = wd.cg_solve(op.ctx, eta, x, tol, 20000)
+        t1 = time.perf_counter()
+        best = min(best, t1 - t0) if best is not None else t1 - t0
+    return x, {"ms": 1e3 * best, "iterations": it, "true_rel_residual": res, "status": st,
+               "reliable_updates": op.stats()["reliable_updates"]}
+
+
+def _mixed_32x64(wd, dev, stream):
+    """Mixed precision at 32^3 x 64 (kappa 0.124) against plain FP64 CG on the same GPU."""
+    import torch
+    dims, kappa = (32, 32, 32, 64), 0.124
+    out = {"workload": "32^3x64, kappa 0.124, eps 0.4, tol 1e-10, 1 RHS, FP32 12-real inner links",
+           "reliable_delta": 0.1}
+    ref = wd.WilsonDirac(dims, kappa, BC, wd.WD_PREC_F64, stream=stream)
+    ref.generate_gauge(EPS, GAUGE_SEED)
+    eta = ref.generate_source(SOURCE_SEED)
+    x64, out["plain_f64"] = _timed_solve(ref, wd, eta, TOL)
+    for name, prec in (("mixed_f32", wd.WD_PREC_MIXED_F32), ("mixed_f16", wd.WD_PREC_MIXED_F16)):
+        op = wd.WilsonDirac(dims, kappa, BC, prec, stream=stream)
+        op.generate_gauge(EPS, GAUGE_SEED, compress12=True)
+        x, rec = _timed_solve(op, wd, eta, TOL, repeats=2)
+        rec["rel_diff_vs_f64_solution"] = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
+        rec["speedup_vs_f64"] = out["plain_f64"]["ms"] / rec["ms"]
+        out[name] = rec
+        op.close()
+    ref.close()
+    return out
+
+
+def _multi_24x48(wd, dev, stream):
+    """12 RHS at 24^3 x 48: spin-colour point sources at the origin, then 12 Gaussian sources."""
+    import torch
+    dims = (24, 24, 24, 48)
+    lx, ly, lz, lt = dims
+    out = {"workload": "24^3x48, kappa 0.12, eps 0.4, tol 1e-10 per RHS, FP32 inner + FP64 reliable updates"}
+    op = wd.WilsonDirac(dims, KAPPA, BC, wd.WD_PREC_MIXED_F32, stream=stream)
+    op.generate_gauge(EPS, GAUGE_SEED, compress12=True)
+    point = torch.zeros((12, lt, lz, ly, lx, 4, 3), dtype=torch.complex128, device=dev)
+    for k in range(12):
+        point[k, 0, 0, 0, 0, k // 3, k % 3] = 1.0
+    gauss = torch.stack([op.generate_source(100 + k) for k in range(12)])
+    for name, src in (("point_sources", point), ("gaussian_sources", gauss)):
+        x = torch.zeros_like(src)
+        wd.cg_solve_multi(op.ctx, src, x, TOL, 20000)   # autotune + graph build on the first call
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, iters, res = wd.cg_solve_multi(op.ctx, src, x, TOL, 20000)
+        t1 = time.perf_counter()
+        ms = wd.wd_get_multi_stats(op.ctx)
+        out[name] = {"ms": 1e3 * (t1 - t0), "status": st, "iterations_max": max(iters),
+                     "iterations_min": min(iters), "true_rel_residual_max": max(res),
+                     "reliable_updates": ms["reliable_updates"], "group_K": ms["group"],
+                     "sites_per_block": ms["sites_per_block"], "multi_dslash_ms": ms["dslash_ms"]}
+    # one right-hand side at a time with the same solver, for comparison
+    x = torch.zeros_like(gauss[0])
+    wd.cg_solve(op.ctx, gauss[0], x, TOL, 20000)
+    t = []
+    for k in range(12):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        wd.cg_solve(op.ctx, gauss[k], x, TOL, 20000)
+        t.append(time.perf_counter() - t0)
+    out["gaussian_one_at_a_time_mixed_ms"] = 1e3 * sum(t)
+    op.close()
+    # plain FP64, one right-hand side (x 12 for the batch-equivalent time)
+    ref = wd.WilsonDirac(dims, KAPPA, BC, wd.WD_PREC_F64, stream=stream)
+    ref.generate_gauge(EPS, GAUGE_SEED)
+    _, rec = _timed_solve(ref, wd, gauss[0], TOL)
+    out["plain_f64_one_rhs"] = rec
+    out["plain_f64_x12_ms"] = 12 * rec["ms"]
+    ref.close()
     return out
 
 

@@ -174,6 +174,20 @@ wd_status cg_solve_multi(wd_ctx* ctx, const double* src, double* x, int nrhs, do
                          double* true_rel_res);
 wd_status wd_get_multi_stats(const wd_ctx* ctx, wd_multi_stats* out);
 
+/*
+ * Seeded synthetic inputs generated on the device (the paper's lattices come with no gauge
+ * ensembles). Random numbers: Philox4x32-10 (Salmon et al., SC11) keyed by `seed`, Box-Muller
+ * Gaussians. wd_generate_gauge draws every link as U = exp(i eps H), H the traceless Hermitian part
+ * of a matrix with N(0,1) real and imaginary entries, re-unitarised to SU(3), straight into the
+ * context's device layouts (as wd_load_gauge would store them; compress12 as there), and also
+ * writes the canonical complex128 field to U_out if it is not NULL (device pointer).
+ * wd_generate_source writes a complex Gaussian spinor field (Re, Im ~ N(0,1)) to `out` (device,
+ * canonical complex128). The same streams are reproducible on a CPU (synthetic/ in this
+ * repository). Errors: WD_EINVAL, WD_ENOMEM, WD_ECUDA.
+ */
+wd_status wd_generate_gauge(wd_ctx* ctx, double eps, unsigned long long seed, int compress12, double* U_out);
+wd_status wd_generate_source(wd_ctx* ctx, unsigned long long seed, double* out);
+
 /* Set an option (WD_OPT_*). Returns WD_EINVAL for an unknown key or a value out of range. */
 wd_status wd_set_option(wd_ctx* ctx, int key, double value);
 

@@ -821,6 +821,44 @@ __global__ void mset_params_kernel(MCgScalars* sc, double tol2, double delta2, i
   }
 }
 
+// Allocate the gauge copies the context's solver needs; returns the 12-real flag in effect.
+wd_status ensure_gauge_buffers(wd_ctx* c, int compress12, bool* need64, bool* need32, int* c12_out) {
+  *need64 = c->wprec == SP64 || is_mixed(c->precision);
+  *need32 = c->wprec != SP64;
+  const int c12 = *need32 && compress12 ? 1 : 0;
+  // graphs hold the gauge pointers and the 12-real flag: rebuild them after any change
+  if ((*need64 && !c->gauge64) || (*need32 && (!c->gauge32 || c->c12 != c12))) {
+    destroy_graph(c);
+    if (c->mexec) cudaGraphExecDestroy(c->mexec);
+    if (c->mgraph) cudaGraphDestroy(c->mgraph);
+    c->mexec = nullptr;
+    c->mgraph = nullptr;
+    c->mgraph_ready = false;
+    c->tuned_block[0] = c->tuned_block[1] = c->tuned_block[2] = 0;
+    c->mK = c->mK64 = 0;
+  }
+  if (*need64 && !c->gauge64) {
+    if (cudaMalloc(&c->gauge64, (size_t)c->V * 4 * 9 * 16) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(WD_ENOMEM, "cudaMalloc of the FP64 gauge field failed");
+    }
+  }
+  if (*need32) {
+    if (c->gauge32 && c->c12 != c12) {
+      cudaFree(c->gauge32);
+      c->gauge32 = nullptr;
+    }
+    if (!c->gauge32 && cudaMalloc(&c->gauge32, (size_t)c->V * 4 * (c12 ? 6 : 9) * 8) != cudaSuccess) {
+      cudaGetLastError();
+      c->gauge32 = nullptr;
+      return fail(WD_ENOMEM, "cudaMalloc of the FP32 gauge field failed");
+    }
+    c->c12 = c12;
+  }
+  *c12_out = c12;
+  return WD_OK;
+}
+
 wd_status check_ctx(const wd_ctx* c) {
   if (!c) return fail(WD_EINVAL, "null context");
   return WD_OK;
@@ -1033,27 +1071,9 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
       return fail(WD_ECUDA, "host-to-device copy of the gauge field failed");
     src = (const double*)c->staging;
   }
-  const bool need64 = c->wprec == SP64 || is_mixed(c->precision);
-  const bool need32 = c->wprec != SP64;
-  const int c12 = need32 && compress12 ? 1 : 0;
-  auto cleanup = [&](wd_status s) { return s; };
-  if (need64 && !c->gauge64) {
-    if (cudaMalloc(&c->gauge64, (size_t)c->V * 4 * 9 * 16) != cudaSuccess) {
-      cudaGetLastError();
-      return cleanup(fail(WD_ENOMEM, "cudaMalloc of the FP64 gauge field failed"));
-    }
-  }
-  if (need32) {
-    if (c->gauge32 && c->c12 != c12) {
-      cudaFree(c->gauge32);
-      c->gauge32 = nullptr;
-    }
-    if (!c->gauge32 && cudaMalloc(&c->gauge32, (size_t)c->V * 4 * (c12 ? 6 : 9) * 8) != cudaSuccess) {
-      cudaGetLastError();
-      return cleanup(fail(WD_ENOMEM, "cudaMalloc of the FP32 gauge field failed"));
-    }
-    c->c12 = c12;
-  }
+  bool need64 = false, need32 = false;
+  int c12 = 0;
+  if ((st = ensure_gauge_buffers(c, compress12, &need64, &need32, &c12)) != WD_OK) return st;
   const int gb = 128;
   if (need64) {
     GaugePtr g;
@@ -1061,7 +1081,7 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
     g.prec = SP64;
     g.c12 = 0;
     if (launch_gauge_load(src, g, c->V, red_to(c, TK_GAUGE, &c->sc->max_dev), gb, c->stream) != cudaSuccess)
-      return cleanup(fail(WD_ECUDA, "gauge load kernel failed to launch"));
+      return fail(WD_ECUDA, "gauge load kernel failed to launch");
   }
   if (need32) {
     GaugePtr g;
@@ -1071,12 +1091,11 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
     // the deviation is measured once (on the FP64 pass when there is one)
     Red r = need64 ? no_red() : red_to(c, TK_GAUGE, &c->sc->max_dev);
     if (launch_gauge_load(src, g, c->V, r, gb, c->stream) != cudaSuccess)
-      return cleanup(fail(WD_ECUDA, "gauge load kernel failed to launch"));
+      return fail(WD_ECUDA, "gauge load kernel failed to launch");
   }
   if (cudaMemcpyAsync(c->sc_host, c->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
-    return cleanup(fail(WD_ECUDA, std::string("gauge load failed: ") + cudaGetErrorString(cudaGetLastError())));
-  cleanup(WD_OK);
+    return fail(WD_ECUDA, std::string("gauge load failed: ") + cudaGetErrorString(cudaGetLastError()));
   const double dev = c->sc_host->max_dev;
   if (max_unitarity_dev) *max_unitarity_dev = dev;
   c->gauge_loaded = true;
@@ -1311,6 +1330,29 @@ wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, doub
     ret = fail(WD_NOT_CONVERGED, "maximum iterations reached before every right-hand side met tol");
   c->mstats.status = ret;
   return ret;
+}
+
+wd_status wd_generate_gauge(wd_ctx* c, double eps, unsigned long long seed, int compress12, double* U_out) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!std::isfinite(eps)) return fail(WD_EINVAL, "eps must be finite");
+  bool need64 = false, need32 = false;
+  int c12 = 0;
+  if ((st = ensure_gauge_buffers(c, compress12, &need64, &need32, &c12)) != WD_OK) return st;
+  WD_CUDA(launch_gen_gauge(c->V, eps, seed, need64 ? c->gauge64 : nullptr, need32 ? c->gauge32 : nullptr, c12, U_out,
+                           c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  c->gauge_loaded = true;
+  return WD_OK;
+}
+
+wd_status wd_generate_source(wd_ctx* c, unsigned long long seed, double* out) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!out) return fail(WD_EINVAL, "out is null");
+  WD_CUDA(launch_gen_source(c->V, seed, out, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return WD_OK;
 }
 
 }  // extern "C"

@@ -173,6 +173,12 @@ cudaError_t launch_macc(FieldPtr xhi, FieldPtr xlo, int V, int N, int grid_x, cu
 cudaError_t launch_mconv(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x, MCgScalars* sc, int count,
                          cudaStream_t st);
 
+// Seeded generation (Philox4x32-10): links into the device layouts (any pointer may be null) and
+// optionally the canonical complex128 copy; Gaussian source in the canonical layout.
+cudaError_t launch_gen_gauge(int V, double eps, unsigned long long seed, void* g64, void* g32, int c12, double* canon,
+                             cudaStream_t st);
+cudaError_t launch_gen_source(int V, unsigned long long seed, double* canon, cudaStream_t st);
+
 // grid size used by a launcher for V sites at a block size
 inline int grid_for(int V, int block) { return (V + block - 1) / block; }
 

@@ -80,6 +80,8 @@ _sig = {
     "wd_apply_multi": (_I, [_P, _P, _P, _I, _I]),
     "cg_solve_multi": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "wd_get_multi_stats": (_I, [_P, ctypes.POINTER(WdMultiStats)]),
+    "wd_generate_gauge": (_I, [_P, _D, ctypes.c_ulonglong, _I, _P]),
+    "wd_generate_source": (_I, [_P, ctypes.c_ulonglong, _P]),
     "wd_dslash_noalloc": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _P, _P, _P, _I, _P, _P]),
     "wd_last_error": (ctypes.c_char_p, []),
     "wd_version": (ctypes.c_char_p, []),
@@ -161,6 +163,19 @@ def cg_solve(ctx, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
                        ctypes.byref(res))
     _check(st, "cg_solve", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
     return st, it.value, res.value
+
+
+def wd_generate_gauge(ctx, eps: float, seed: int, compress12: bool = False, U_out: torch.Tensor = None) -> None:
+    if U_out is not None and (U_out.dtype != torch.complex128 or not U_out.is_cuda or not U_out.is_contiguous()):
+        raise ValueError("U_out must be a contiguous complex128 CUDA tensor")
+    _check(_lib.wd_generate_gauge(_P(ctx), float(eps), int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(compress12)),
+                                  _P(_ptr(U_out)) if U_out is not None else None), "wd_generate_gauge")
+
+
+def wd_generate_source(ctx, seed: int, out: torch.Tensor) -> None:
+    if out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous complex128 CUDA tensor")
+    _check(_lib.wd_generate_source(_P(ctx), int(seed) & 0xFFFFFFFFFFFFFFFF, _P(_ptr(out))), "wd_generate_source")
 
 
 def _check_multi(t: torch.Tensor, name: str) -> int:
@@ -280,6 +295,17 @@ class WilsonDirac:
 
     def time_dslash(self, dagger=False, launches=20) -> float:
         return wd_time_dslash(self.ctx, dagger, launches)
+
+    def generate_gauge(self, eps, seed, compress12=False, return_field=False):
+        lx, ly, lz, lt = self.dims
+        U = torch.empty((lt, lz, ly, lx, 4, 3, 3), dtype=torch.complex128, device=self.device) if return_field else None
+        wd_generate_gauge(self.ctx, eps, seed, compress12, U)
+        return U
+
+    def generate_source(self, seed):
+        out = torch.empty(self.spinor_shape, dtype=torch.complex128, device=self.device)
+        wd_generate_source(self.ctx, seed, out)
+        return out
 
     def apply_multi(self, psi, dagger=False, out=None):
         if out is None:
