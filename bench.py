@@ -264,6 +264,7 @@ def run_native(args, rank, world):
         out["dslash_sweep"] = _sweep(wd, dev, stream, args.sweep)
         out["mixed_32x64"] = _mixed_32x64(wd, dev, stream)
         out["multi_rhs_24x48"] = _multi_24x48(wd, dev, stream)
+        out["serving"] = _serving(wd)
         out["cpu_baseline"] = _cpu_baseline(iters)
     op.close()
     if rank == 0:
@@ -436,6 +437,57 @@ def _multi_24x48(wd, dev, stream):
     out["plain_f64_one_rhs"] = rec
     out["plain_f64_x12_ms"] = 12 * rec["ms"]
     ref.close()
+    return out
+
+
+def _serving(wd, n_req=60, rate=200.0, seed=7):
+    """Poisson stream of single-RHS solves through the serving runtime (continuous admission).
+
+    Sizes uniform over {8^4, 12^4, 16^4, 16^3x32, 24^3x48, 32^3x64}, kappa U[0.115, 0.124], tol in
+    {1e-8, 1e-10}, eps U[0.3, 0.5], a seeded gauge field and source per request, 150 GB budget.
+    Mixed precision on 4 concurrent slots against plain FP64 one request at a time (1 slot), same
+    requests and arrival times. One untimed request per size first warms the resident contexts.
+    """
+    rng = np.random.default_rng(seed)
+    sizes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (24, 24, 24, 48), (32, 32, 32, 64)]
+    reqs, t = [], 0.0
+    for i in range(n_req):
+        t += rng.exponential(1.0 / rate)
+        reqs.append(dict(t=t, dims=sizes[int(rng.integers(6))], kappa=float(rng.uniform(0.115, 0.124)),
+                         tol=float([1e-8, 1e-10][int(rng.integers(2))]), eps=float(rng.uniform(0.3, 0.5)),
+                         gauge_seed=10000 + i, source_seed=20000 + i))
+
+    def run(precision, slots):
+        srv = wd.Server(150e9, slots)
+        warm = [srv.submit(dims=d, kappa=0.12, eps=0.4, gauge_seed=1, source_seed=2, tol=1e-8, precision=precision)
+                for d in sizes for _ in range(slots)]
+        for w in warm:
+            srv.wait(w)
+        t0 = time.perf_counter()
+        ids = []
+        for q in reqs:
+            dt = q["t"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(dims=q["dims"], kappa=q["kappa"], eps=q["eps"], gauge_seed=q["gauge_seed"],
+                                  source_seed=q["source_seed"], tol=q["tol"], precision=precision))
+        res = [srv.wait(i) for i in ids]
+        t1 = time.perf_counter()
+        st = srv.stats()
+        srv.close()
+        lat = np.array([r["latency_ms"] for r in res])
+        ok = [r for r in res if r["status"] == 0]
+        worst = max((r["true_rel_residual"] / q["tol"]) for r, q in zip(res, reqs))
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_solve_ms": float(np.mean([r["solve_ms"] for r in res])),
+                "solves_per_s": len(res) / (t1 - t0), "completed_ok": len(ok), "requests": len(res),
+                "max_true_residual_over_tol": float(worst), "slots": slots,
+                "warm_hits": st["warm_hits"], "evictions": st["evictions"], "peak_gb": st["peak_bytes"] / 1e9}
+
+    out = {"workload": f"{n_req} requests, Poisson arrivals at {rate:g}/s (offered), sizes 8^4..32^3x64, "
+                       "kappa U[0.115,0.124], tol {1e-8,1e-10}, eps U[0.3,0.5], 150 GB budget"}
+    out["mixed_f32_4_slots"] = run(wd.WD_PREC_MIXED_F32, 4)
+    out["plain_f64_one_at_a_time"] = run(wd.WD_PREC_F64, 1)
     return out
 
 

@@ -112,6 +112,10 @@ typedef struct {
 wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int precision,
                     void* cuda_stream, wd_ctx** out);
 
+/* Change the hopping parameter of an existing context (|kappa| < 1). Every later operator
+ * application and solve uses it; links, workspace and graphs are kept. */
+wd_status wd_set_kappa(wd_ctx* ctx, double kappa);
+
 /* Free every device resource of the context. Null is ignored. */
 void wd_destroy(wd_ctx* ctx);
 
@@ -187,6 +191,66 @@ wd_status wd_get_multi_stats(const wd_ctx* ctx, wd_multi_stats* out);
  */
 wd_status wd_generate_gauge(wd_ctx* ctx, double eps, unsigned long long seed, int compress12, double* U_out);
 wd_status wd_generate_source(wd_ctx* ctx, unsigned long long seed, double* out);
+
+/*
+ * Serving: a persistent request loop with continuous admission (no counterpart in the paper,
+ * which runs one solve at a time). Each request is one single-RHS solve with its own lattice,
+ * kappa, tolerance, seeded gauge field (wd_generate_gauge with eps, gauge_seed) and source
+ * (seeded Gaussian, or src_host). A scheduler admits queued requests into `slots` execution
+ * slots as slots free up and as device memory allows (an estimate of each request's footprint
+ * is charged against budget_bytes). Every slot has its own CUDA stream and host thread, so admitted
+ * solves overlap on the device; a slot keeps the contexts it created resident (least recently used
+ * ones are evicted when a new volume does not fit), and a request whose volume and precision match
+ * an idle slot's resident context goes there first (no allocation or graph rebuild). Results agree
+ * with a solve alone up to the tolerance (same fields, same solver).
+ *
+ * wd_server_submit queues a request (returns its id at once); wd_server_wait blocks until it is
+ * done; wd_server_poll returns immediately (*done = 0/1). A finished result is returned once and
+ * then forgotten. wd_server_destroy finishes running solves, drops queued ones and frees all.
+ * Errors: WD_EINVAL (bad request), WD_ENOMEM (a request larger than the whole budget), WD_ECUDA.
+ */
+typedef struct wd_server wd_server;
+
+typedef struct {
+  int dims[4];
+  double kappa;
+  double eps;                      /* link spread of the generated gauge field                 */
+  unsigned long long gauge_seed;
+  unsigned long long source_seed;  /* ignored when src_host is set                             */
+  double tol;
+  int maxit;
+  int precision;                   /* WD_PREC_*                                                */
+  int boundary_set;                /* 0: boundary (1, 1, 1, -1); 1: use boundary[]             */
+  int boundary[4];
+  const double* src_host;          /* optional host source, canonical complex128               */
+  double* x_host;                  /* optional host buffer for the solution, canonical          */
+} wd_request;
+
+typedef struct {
+  int status;                      /* wd_status of the solve                                    */
+  int iterations;
+  int reliable_updates;
+  int slot;                        /* execution slot that ran it                                */
+  double true_rel_residual;
+  double queue_ms;                 /* submit -> start                                           */
+  double solve_ms;                 /* start -> done (fields generated, solved, copied out)      */
+  double latency_ms;               /* submit -> done                                            */
+} wd_result;
+
+typedef struct {
+  long long submitted, admitted, completed, failed;
+  long long warm_hits;             /* requests that ran on an already resident context          */
+  long long evictions;             /* resident contexts freed to make room                      */
+  int pending;
+  double used_bytes, peak_bytes;   /* device memory charged to resident contexts                */
+} wd_server_stats;
+
+wd_status wd_server_create(double budget_bytes, int slots, wd_server** out);
+wd_status wd_server_submit(wd_server* srv, const wd_request* req, long long* id);
+wd_status wd_server_wait(wd_server* srv, long long id, wd_result* out);
+wd_status wd_server_poll(wd_server* srv, long long id, wd_result* out, int* done);
+wd_status wd_server_get_stats(wd_server* srv, wd_server_stats* out);
+void wd_server_destroy(wd_server* srv);
 
 /* Set an option (WD_OPT_*). Returns WD_EINVAL for an unknown key or a value out of range. */
 wd_status wd_set_option(wd_ctx* ctx, int key, double value);

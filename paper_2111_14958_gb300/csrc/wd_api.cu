@@ -194,6 +194,7 @@ cudaError_t dslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fi
   d.skip = skip;
   d.red = norm_dst ? red_to(c, slot, norm_dst) : no_red();
   d.block = dslash_block(c, in.prec);
+  d.kappa_dev = &c->sc->kappa;
   return launch_dslash(d, st);
 }
 
@@ -592,6 +593,7 @@ MDslashCall mcall(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fie
   d.partials = c->mpartials;
   d.tickets = &c->msc->ticket[slot];
   d.result = result;
+  d.kappa_dev = &c->sc->kappa;
   return d;
 }
 
@@ -966,7 +968,8 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
     return bail(fail(WD_ENOMEM, "pinned host allocation failed"));
   }
   memset(c->sc_host, 0, sizeof(CgScalars));
-  if (cudaMemsetAsync(c->sc, 0, sizeof(CgScalars), c->stream) != cudaSuccess ||
+  c->sc_host->kappa = kappa;
+  if (cudaMemcpyAsync(c->sc, c->sc_host, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return bail(fail(WD_ECUDA, "workspace initialisation failed"));
   *out = c;
@@ -1351,6 +1354,18 @@ wd_status wd_generate_source(wd_ctx* c, unsigned long long seed, double* out) {
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!out) return fail(WD_EINVAL, "out is null");
   WD_CUDA(launch_gen_source(c->V, seed, out, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return WD_OK;
+}
+
+wd_status wd_set_kappa(wd_ctx* c, double kappa) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!std::isfinite(kappa) || std::fabs(kappa) >= 1.0) return fail(WD_EINVAL, "kappa must be finite with |kappa| < 1");
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  c->kappa = kappa;
+  c->sc_host->kappa = kappa;
+  WD_CUDA(cudaMemcpyAsync(&c->sc->kappa, &c->sc_host->kappa, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   WD_CUDA(cudaStreamSynchronize(c->stream));
   return WD_OK;
 }

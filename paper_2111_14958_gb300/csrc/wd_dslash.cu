@@ -29,7 +29,8 @@ struct DslashArgs {
   Geom g;
   GaugeRef<typename RealOf<SP>::type, C12> u;
   SpinorRef<SP> in, out, b;
-  typename RealOf<SP>::type mkappa;  // -kappa
+  typename RealOf<SP>::type mkappa;  // -kappa (used when kappa_dev is null)
+  const double* kappa_dev;
   const int* skip;
   double* partials;
   unsigned* ticket;
@@ -37,14 +38,14 @@ struct DslashArgs {
 };
 
 template <int MU, int S_FWD, int SP, bool C12, typename R>
-__device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, int s, const int (&c)[4],
+__device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int s, const int (&c)[4],
                                          Cx<R> (&acc)[12]) {
   const int V = a.g.V;
   // forward hop n -> n + mu with U_mu(n)
   {
     const bool wrap = c[MU] == a.g.L[MU] - 1;
     const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -a.mkappa : a.mkappa;
+    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12];
     load_spinor(a.in, nb, V, psi);
     Cx<R> h[6];
@@ -59,7 +60,7 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, int s, co
   {
     const bool wrap = c[MU] == 0;
     const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -a.mkappa : a.mkappa;
+    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12];
     load_spinor(a.in, nb, V, psi);
     Cx<R> h[6];
@@ -100,14 +101,15 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
       c[2] = r % a.g.L[2];
       c[3] = r / a.g.L[2];
     }
+    const R mk = a.kappa_dev ? (R)(-*a.kappa_dev) : a.mkappa;
     Cx<R> acc[12];
     load_spinor(a.in, s, V, acc);
     // D: forward (1 - gamma), backward (1 + gamma); D^dagger: the reverse
     constexpr int SF = DAG ? +1 : -1;
-    hop_pair<0, SF>(a, s, c, acc);
-    hop_pair<1, SF>(a, s, c, acc);
-    hop_pair<2, SF>(a, s, c, acc);
-    hop_pair<3, SF>(a, s, c, acc);
+    hop_pair<0, SF>(a, mk, s, c, acc);
+    hop_pair<1, SF>(a, mk, s, c, acc);
+    hop_pair<2, SF>(a, mk, s, c, acc);
+    hop_pair<3, SF>(a, mk, s, c, acc);
     if (EPI == EPI_RESID) {
       Cx<R> bv[12];
       load_spinor(a.b, s, V, bv);
@@ -138,6 +140,7 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
     a.b.norm = c.b.norm;
   }
   a.mkappa = (typename RealOf<SP>::type)(-c.kappa);
+  a.kappa_dev = c.kappa_dev;
   a.skip = c.skip;
   a.partials = c.red.partials;
   a.ticket = c.red.ticket;

@@ -47,6 +47,7 @@ struct CgScalars {
   double max_dev;    // gauge unitarity check
   double rr_ref;     // mixed precision: ||r||^2 at the last reliable update
   double delta2;     // mixed precision: reliable-update trigger factor, squared
+  double kappa;      // hopping parameter read by every dslash of the context (settable between solves)
   double scratch[4];
   int iter;          // cumulative iterations
   int maxit;
@@ -83,6 +84,7 @@ struct DslashCall {
   const int* skip;  // optional: if *skip != 0 the launch does nothing
   Red red;          // optional |out|^2
   int block;
+  const double* kappa_dev;  // optional: kappa read from device memory (overrides `kappa`)
 };
 
 // Launchers. Each returns cudaGetLastError() after the launch.
@@ -154,6 +156,7 @@ struct MDslashCall {
   double* partials;     // >= nrhs * grid_x
   unsigned* tickets;    // >= nrhs / group counters
   double* result;       // optional per-RHS |out|^2
+  const double* kappa_dev;  // optional: kappa read from device memory (overrides `kappa`)
 };
 
 cudaError_t launch_dslash_multi(const MDslashCall& c, cudaStream_t st);

@@ -182,6 +182,7 @@ struct MArgs {
   GaugeRef<typename MReal<SP>::type, C12> u;
   MSpinor<SP> in, out, b;
   typename MReal<SP>::type mkappa;
+  const double* kappa_dev;
   int N, K;            // total RHS, RHS per group (blockDim.x = K * sites per block)
   const int* status;   // optional per-RHS status: only RUNNING right-hand sides are computed
   double* partials;
@@ -190,12 +191,12 @@ struct MArgs {
 };
 
 template <int MU, int SF, int SP, bool C12, typename R>
-__device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, int s, int r, const int (&c)[4], Cx<R> (&acc)[12]) {
+__device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r, const int (&c)[4], Cx<R> (&acc)[12]) {
   const int V = a.g.V, N = a.N;
   {
     const bool wrap = c[MU] == a.g.L[MU] - 1;
     const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -a.mkappa : a.mkappa;
+    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12], h[6], u[9], chi[6];
     mload(a.in, nb, r, V, N, psi);
     spin_project<MU, SF>(psi, h);
@@ -206,7 +207,7 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, int s, int r, cons
   {
     const bool wrap = c[MU] == 0;
     const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -a.mkappa : a.mkappa;
+    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12], h[6], u[9], chi[6];
     mload(a.in, nb, r, V, N, psi);
     spin_project<MU, -SF>(psi, h);
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(256, MMinBlocks<SP>::value) dslash_multi_kerne
   const int r = blockIdx.y * K + rl;
   const bool live = sl < spb && (a.status == nullptr || a.status[r] == ST_RUNNING);
   double n2 = 0.0;
+  const R mk = a.kappa_dev ? (R)(-*a.kappa_dev) : a.mkappa;
   if (live) {
     for (int s = blockIdx.x * spb + sl; s < V; s += gridDim.x * spb) {
       int c[4];
@@ -244,10 +246,10 @@ __global__ void __launch_bounds__(256, MMinBlocks<SP>::value) dslash_multi_kerne
       Cx<R> acc[12];
       mload(a.in, s, r, V, a.N, acc);
       constexpr int SF = DAG ? +1 : -1;
-      mhop<0, SF>(a, s, r, c, acc);
-      mhop<1, SF>(a, s, r, c, acc);
-      mhop<2, SF>(a, s, r, c, acc);
-      mhop<3, SF>(a, s, r, c, acc);
+      mhop<0, SF>(a, mk, s, r, c, acc);
+      mhop<1, SF>(a, mk, s, r, c, acc);
+      mhop<2, SF>(a, mk, s, r, c, acc);
+      mhop<3, SF>(a, mk, s, r, c, acc);
       if (EPI == EPI_RESID) {
         Cx<R> bv[12];
         mload(a.b, s, r, V, a.N, bv);
@@ -276,6 +278,7 @@ static cudaError_t mlaunch_t(const MDslashCall& c, cudaStream_t st) {
   a.out = mview<SP>(c.out);
   a.b = mview<SP>(c.b);
   a.mkappa = (typename MReal<SP>::type)(-c.kappa);
+  a.kappa_dev = c.kappa_dev;
   a.N = c.nrhs;
   a.K = c.group;
   a.status = c.status;

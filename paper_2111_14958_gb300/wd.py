@@ -58,6 +58,27 @@ class WdMultiStats(ctypes.Structure):
                 ("status", ctypes.c_int), ("solve_ms", ctypes.c_double), ("dslash_ms", ctypes.c_double)]
 
 
+class WdRequest(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("kappa", ctypes.c_double), ("eps", ctypes.c_double),
+                ("gauge_seed", ctypes.c_ulonglong), ("source_seed", ctypes.c_ulonglong),
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
+                ("boundary_set", ctypes.c_int), ("boundary", ctypes.c_int * 4),
+                ("src_host", ctypes.c_void_p), ("x_host", ctypes.c_void_p)]
+
+
+class WdResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("slot", ctypes.c_int), ("true_rel_residual", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class WdServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("warm_hits", ctypes.c_longlong), ("evictions", ctypes.c_longlong), ("pending", ctypes.c_int),
+                ("used_bytes", ctypes.c_double), ("peak_bytes", ctypes.c_double)]
+
+
 class WdStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
@@ -71,6 +92,7 @@ _D = ctypes.c_double
 _sig = {
     "wd_create": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_P)]),
     "wd_destroy": (None, [_P]),
+    "wd_set_kappa": (_I, [_P, _D]),
     "wd_load_gauge": (_I, [_P, _P, _I, _I, ctypes.POINTER(_D)]),
     "wd_apply": (_I, [_P, _P, _P, _I]),
     "cg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -83,6 +105,12 @@ _sig = {
     "wd_generate_gauge": (_I, [_P, _D, ctypes.c_ulonglong, _I, _P]),
     "wd_generate_source": (_I, [_P, ctypes.c_ulonglong, _P]),
     "wd_dslash_noalloc": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _P, _P, _P, _I, _P, _P]),
+    "wd_server_create": (_I, [_D, _I, ctypes.POINTER(_P)]),
+    "wd_server_submit": (_I, [_P, ctypes.POINTER(WdRequest), ctypes.POINTER(ctypes.c_longlong)]),
+    "wd_server_wait": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(WdResult)]),
+    "wd_server_poll": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(WdResult), ctypes.POINTER(_I)]),
+    "wd_server_get_stats": (_I, [_P, ctypes.POINTER(WdServerStats)]),
+    "wd_server_destroy": (None, [_P]),
     "wd_last_error": (ctypes.c_char_p, []),
     "wd_version": (ctypes.c_char_p, []),
 }
@@ -135,6 +163,10 @@ def wd_create(dims, kappa: float, boundary=(1, 1, 1, -1), precision: int = WD_PR
     _check(_lib.wd_create(d, float(kappa), b, int(precision), _P(_stream_handle(stream)), ctypes.byref(out)),
            "wd_create")
     return out.value
+
+
+def wd_set_kappa(ctx, kappa: float) -> None:
+    _check(_lib.wd_set_kappa(_P(ctx), float(kappa)), "wd_set_kappa")
 
 
 def wd_destroy(ctx) -> None:
@@ -273,6 +305,10 @@ class WilsonDirac:
         except Exception:
             pass
 
+    def set_kappa(self, kappa):
+        wd_set_kappa(self.ctx, kappa)
+        self.kappa = float(kappa)
+
     def load_gauge(self, U, compress12=False, check=True) -> float:
         return wd_load_gauge(self.ctx, U.contiguous(), compress12, check)
 
@@ -320,3 +356,74 @@ class WilsonDirac:
 
     def multi_stats(self):
         return wd_get_multi_stats(self.ctx)
+
+
+# ------------------------------------------------------------------ serving
+
+def _struct_dict(obj):
+    return {name: getattr(obj, name) for name, _ in obj._fields_}
+
+
+class Server:
+    """Persistent solve server (wd_server_*): continuous admission of single-RHS requests."""
+
+    def __init__(self, budget_bytes: float, slots: int = 4):
+        h = _P()
+        _check(_lib.wd_server_create(float(budget_bytes), int(slots), ctypes.byref(h)), "wd_server_create")
+        self.h = h.value
+        self._keep = {}
+
+    def submit(self, dims, kappa, eps, gauge_seed, source_seed, tol, precision=WD_PREC_MIXED_F32, maxit=20000,
+               boundary=None, src_host: torch.Tensor = None, x_host: torch.Tensor = None) -> int:
+        r = WdRequest()
+        for i in range(4):
+            r.dims[i] = int(dims[i])
+        r.kappa, r.eps, r.tol = float(kappa), float(eps), float(tol)
+        r.gauge_seed = int(gauge_seed) & 0xFFFFFFFFFFFFFFFF
+        r.source_seed = int(source_seed) & 0xFFFFFFFFFFFFFFFF
+        r.maxit, r.precision = int(maxit), int(precision)
+        if boundary is not None:
+            r.boundary_set = 1
+            for i in range(4):
+                r.boundary[i] = int(boundary[i])
+        for t in (src_host, x_host):
+            if t is not None and (t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous()):
+                raise ValueError("src_host / x_host must be contiguous complex128 CPU tensors")
+        r.src_host = src_host.data_ptr() if src_host is not None else None
+        r.x_host = x_host.data_ptr() if x_host is not None else None
+        rid = ctypes.c_longlong()
+        _check(_lib.wd_server_submit(_P(self.h), ctypes.byref(r), ctypes.byref(rid)), "wd_server_submit")
+        self._keep[rid.value] = (src_host, x_host)
+        return rid.value
+
+    def wait(self, rid: int) -> dict:
+        res = WdResult()
+        _check(_lib.wd_server_wait(_P(self.h), ctypes.c_longlong(rid), ctypes.byref(res)), "wd_server_wait")
+        self._keep.pop(rid, None)
+        return _struct_dict(res)
+
+    def poll(self, rid: int):
+        res = WdResult()
+        done = _I(0)
+        _check(_lib.wd_server_poll(_P(self.h), ctypes.c_longlong(rid), ctypes.byref(res), ctypes.byref(done)),
+               "wd_server_poll")
+        if done.value:
+            self._keep.pop(rid, None)
+            return _struct_dict(res)
+        return None
+
+    def stats(self) -> dict:
+        s = WdServerStats()
+        _check(_lib.wd_server_get_stats(_P(self.h), ctypes.byref(s)), "wd_server_get_stats")
+        return _struct_dict(s)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.wd_server_destroy(_P(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

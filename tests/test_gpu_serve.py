@@ -1,0 +1,127 @@
+"""The serving runtime: continuous admission, overlap, memory budget, results as if solved alone."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import cg as ocg
+from tests.gpu_util import rel, require_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+BC = (1, 1, 1, -1)
+
+
+def _mix(wd, n):
+    sizes = [(4, 4, 4, 4), (6, 4, 4, 6), (8, 8, 8, 8), (4, 4, 4, 8)]
+    kappas = [0.115, 0.12, 0.124]
+    tols = [1e-8, 1e-10]
+    precs = [wd.WD_PREC_MIXED_F32, wd.WD_PREC_F64, wd.WD_PREC_MIXED_F16]
+    rng = np.random.default_rng(5)
+    out = []
+    for i in range(n):
+        out.append(dict(dims=sizes[i % 4], kappa=float(kappas[i % 3]), eps=float(rng.uniform(0.3, 0.5)),
+                        gauge_seed=1000 + i, source_seed=2000 + i, tol=tols[i % 2], precision=precs[i % 3]))
+    return out
+
+
+def _alone(wd, q):
+    op = wd.WilsonDirac(q["dims"], q["kappa"], BC, q["precision"])
+    op.generate_gauge(q["eps"], q["gauge_seed"], compress12=q["precision"] != wd.WD_PREC_F64)
+    src = op.generate_source(q["source_seed"])
+    x, iters, res, st = op.solve(src, tol=q["tol"], maxit=20000)
+    op.close()
+    return to_np(x), iters, res, st
+
+
+def test_mixed_requests_match_solves_alone():
+    wd = require_gpu()
+    reqs = _mix(wd, 12)
+    srv = wd.Server(budget_bytes=4e9, slots=3)
+    outs = []
+    for q in reqs:
+        lx, ly, lz, lt = q["dims"]
+        x = torch.empty((lt, lz, ly, lx, 4, 3), dtype=torch.complex128)
+        outs.append((srv.submit(x_host=x, **q), x))
+    results = [srv.wait(rid) for rid, _ in outs]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 12 and st["failed"] == 0
+    assert len({r["slot"] for r in results}) > 1          # work ran on several slots
+    for q, (rid, x), r in zip(reqs, outs, results):
+        assert r["status"] == wd.WD_OK, (q, r)
+        assert r["latency_ms"] >= r["solve_ms"] > 0
+        U = synthetic.gauge_field_philox(q["dims"], q["eps"], q["gauge_seed"])
+        eta = synthetic.gaussian_source_philox(q["dims"], q["source_seed"])
+        xs = x.numpy()
+        assert ocg.true_residual(U, eta, xs, q["kappa"]) <= q["tol"] * 1.01
+        xa, ia, ra, sa = _alone(wd, q)
+        assert sa == wd.WD_OK
+        # both solve the same system to tol: they agree to the conditioning of D times tol
+        assert rel(xs, xa) < 200 * q["tol"]
+
+
+def test_budget_limits_residency_and_oversize_is_rejected():
+    wd = require_gpu()
+    q = dict(dims=(8, 8, 8, 8), kappa=0.12, eps=0.4, source_seed=1, tol=1e-8, precision=wd.WD_PREC_MIXED_F32)
+    srv = wd.Server(budget_bytes=12e6, slots=4)   # room for one 8^4 request at a time
+    ids = [srv.submit(gauge_seed=7 + i, **q) for i in range(6)]
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    assert all(r["status"] == wd.WD_OK for r in res)
+    assert st["peak_bytes"] <= 12e6
+    with pytest.raises(wd.WdError) as e:
+        srv.submit(dims=(32, 32, 32, 32), kappa=0.12, eps=0.4, gauge_seed=1, source_seed=1, tol=1e-8)
+    assert e.value.status == wd.WD_ENOMEM
+    srv.close()
+
+
+def test_poll_and_host_source():
+    wd = require_gpu()
+    dims = (4, 4, 4, 4)
+    eta = torch.from_numpy(synthetic.gaussian_source(dims, 3)).contiguous()
+    x = torch.empty_like(eta)
+    srv = wd.Server(budget_bytes=1e9, slots=1)
+    rid = srv.submit(dims=dims, kappa=0.12, eps=0.4, gauge_seed=9, source_seed=0, tol=1e-10,
+                     precision=wd.WD_PREC_F64, src_host=eta, x_host=x)
+    r = None
+    for _ in range(20000):
+        r = srv.poll(rid)
+        if r is not None:
+            break
+        time.sleep(0.001)
+    assert r is not None and r["status"] == wd.WD_OK
+    U = synthetic.gauge_field_philox(dims, 0.4, 9)
+    assert ocg.true_residual(U, eta.numpy(), x.numpy(), 0.12) <= 1e-10
+    srv.close()
+
+
+def test_set_kappa_reuses_context():
+    wd = require_gpu()
+    dims = (4, 4, 4, 6)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_MIXED_F32)
+    op.generate_gauge(0.4, 3, compress12=True)
+    src = op.generate_source(4)
+    U = synthetic.gauge_field_philox(dims, 0.4, 3)
+    eta = synthetic.gaussian_source_philox(dims, 4)
+    for kappa in (0.12, 0.115, 0.124):
+        op.set_kappa(kappa)
+        x, iters, res, st = op.solve(src, tol=1e-10)
+        assert st == wd.WD_OK
+        assert ocg.true_residual(U, eta, to_np(x), kappa) <= 1e-10
+    op.close()
+
+
+def test_same_volume_request_runs_on_the_resident_context():
+    wd = require_gpu()
+    q = dict(dims=(6, 6, 6, 6), eps=0.4, source_seed=1, tol=1e-10, precision=wd.WD_PREC_MIXED_F32)
+    srv = wd.Server(budget_bytes=1e9, slots=2)
+    a = srv.wait(srv.submit(kappa=0.12, gauge_seed=1, **q))
+    b = srv.wait(srv.submit(kappa=0.124, gauge_seed=2, **q))   # same volume, other kappa and field
+    st = srv.stats()
+    srv.close()
+    assert a["status"] == b["status"] == wd.WD_OK
+    assert st["warm_hits"] == 1 and b["slot"] == a["slot"]
+    assert b["true_rel_residual"] <= 1e-10
