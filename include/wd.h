@@ -55,7 +55,13 @@ enum {
   WD_PREC_F64 = 64,        /* plain FP64 CG: FP64 spinors, FP64 links, FP64 arithmetic             */
   WD_PREC_F32 = 32,        /* plain FP32 CG: FP32 spinors and links, FP64 reductions               */
   WD_PREC_MIXED_F32 = 6432,/* FP32 inner CG with FP64 reliable updates (FP64 solution, residual)   */
-  WD_PREC_MIXED_F16 = 6416 /* FP16 spinors with per-site FP32 norm inside, FP64 reliable updates   */
+  WD_PREC_MIXED_F16 = 6416, /* FP16 spinors with per-site FP32 norm inside, FP64 reliable updates  */
+  /* Flag ORed into any of the above: even-odd (Schur) preconditioning. Every extent must be even.
+   * Fields are stored in parity order and cg_solve runs on M = 1 - kappa^2 H_eo H_oe over the even
+   * sites (b_e = eta_e + kappa H_eo eta_o; x_o = eta_o + kappa H_oe x_e afterwards), with the same
+   * tolerance on the full-system residual ||eta - D x|| / ||eta||. Multi-RHS calls are not
+   * available on such a context. */
+  WD_EVEN_ODD = 0x10000
 };
 
 /* Options for wd_set_option. */

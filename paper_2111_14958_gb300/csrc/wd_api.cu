@@ -57,6 +57,9 @@ struct wd_ctx {
 
   // working (inner) precision of the Krylov vectors and its gauge copy
   int wprec;  // SP64 / SP32 / SP16
+  int eo;     // fields stored in parity order; CG on the even-site Schur complement
+  int nsolve; // sites the Krylov vectors span: V, or V/2 (even half) for even-odd
+  FieldPtr t, t64;  // even-odd: odd-site temporaries of the two-step operator
   FieldPtr x, r, p, q, s, eta;  // plain modes: all in wprec; mixed: r, p, q, s in wprec, x = x_lo (SP32)
   // FP64 operator and outer vectors (FP64 context and mixed modes)
   FieldPtr x64, r64, eta64;
@@ -198,6 +201,53 @@ cudaError_t dslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fi
   return launch_dslash(d, st);
 }
 
+const GeomH* eo_geom(const wd_ctx* c) { return c->eo ? &c->geom : nullptr; }
+
+// Even-odd half hopping: out = [b -] ([self] + sign * kappa * H in) on the sites of `parity`.
+cudaError_t eo_half(wd_ctx* c, FieldPtr in, FieldPtr out, int parity, double sign, int dagger, const FieldPtr* self,
+                    const FieldPtr* b, double* norm_dst, int slot, const int* skip, cudaStream_t st) {
+  EoCall e;
+  memset(&e, 0, sizeof(e));
+  e.g = c->geom;
+  e.u = gauge_for(c, in.prec);
+  e.in = in;
+  e.out = out;
+  if (self) e.self = *self;
+  if (b) e.b = *b;
+  e.parity = parity;
+  e.sign = sign;
+  e.dagger = dagger;
+  e.use_self = self != nullptr;
+  e.resid = b != nullptr;
+  e.kappa_dev = &c->sc->kappa;
+  e.skip = skip;
+  e.red = norm_dst ? red_to(c, slot, norm_dst) : no_red();
+  e.block = dslash_block(c, in.prec);
+  return launch_dslash_eo(e, st);
+}
+
+FieldPtr none_field();
+
+// The solver's operator: A = D (lexicographic contexts) or A = M = 1 - kappa^2 H_eo H_oe on the even
+// sites (even-odd contexts; two half launches through the odd temporary). out = A in, or
+// out = b - A in for EPI_RESID; optional |out|^2 (over the sites the operator acts on).
+cudaError_t op(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, FieldPtr b, double* norm_dst, int slot,
+               const int* skip, cudaStream_t st) {
+  if (!c->eo) return dslash(c, in, out, dagger, epi, b, norm_dst, slot, skip, st);
+  cudaError_t e;
+  FieldPtr t = in.prec == SP64 ? c->t64 : c->t;
+  if ((e = eo_half(c, in, t, 1, +1.0, dagger, nullptr, nullptr, nullptr, 0, skip, st)) != cudaSuccess) return e;
+  return eo_half(c, t, out, 0, -1.0, dagger, &in, epi == EPI_RESID ? &b : nullptr, norm_dst, slot, skip, st);
+}
+
+// out = D in (or D^dagger in) on the whole lattice, whatever the storage order.
+cudaError_t full_D(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, cudaStream_t st) {
+  if (!c->eo) return dslash(c, in, out, dagger, EPI_PLAIN, none_field(), nullptr, 0, nullptr, st);
+  cudaError_t e;
+  if ((e = eo_half(c, in, out, 0, -1.0, dagger, &in, nullptr, nullptr, 0, nullptr, st)) != cudaSuccess) return e;
+  return eo_half(c, in, out, 1, -1.0, dagger, &in, nullptr, nullptr, 0, nullptr, st);
+}
+
 FieldPtr none_field() {
   FieldPtr f;
   f.p = nullptr;
@@ -213,9 +263,9 @@ cudaError_t plain_prologue(wd_ctx* c, cudaStream_t st, int use_cond, unsigned lo
   CgScalars* sc = c->sc;
   if ((e = launch_cg_init(sc, 0, st)) != cudaSuccess) return e;
   // r = eta - D x
-  if ((e = dslash(c, c->x, c->r, 0, EPI_RESID, c->eta, &sc->rr, TK_DSLASH_A, nullptr, st)) != cudaSuccess) return e;
+  if ((e = op(c, c->x, c->r, 0, EPI_RESID, c->eta, &sc->rr, TK_DSLASH_A, nullptr, st)) != cudaSuccess) return e;
   // p = D^dag r, gamma = |p|^2
-  if ((e = dslash(c, c->r, c->p, 1, EPI_PLAIN, none_field(), &sc->gamma, TK_DSLASH_B, nullptr, st)) != cudaSuccess)
+  if ((e = op(c, c->r, c->p, 1, EPI_PLAIN, none_field(), &sc->gamma, TK_DSLASH_B, nullptr, st)) != cudaSuccess)
     return e;
   return launch_cg_check(sc, use_cond, cond, st);
 }
@@ -225,21 +275,25 @@ cudaError_t plain_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long l
   CgScalars* sc = c->sc;
   const int bb = c->block_blas;
   // q = D p, |q|^2
-  if ((e = dslash(c, c->p, c->q, 0, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
+  if ((e = op(c, c->p, c->q, 0, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
     return e;
   // alpha; r -= alpha q; |r|^2
-  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->V, sc, c->partials, bb, c->sms, st)) != cudaSuccess) return e;
+  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->nsolve, c->V, sc, c->partials, bb, c->sms, st)) != cudaSuccess) return e;
   // s = D^dag r, gamma' = |s|^2
-  if ((e = dslash(c, c->r, c->s, 1, EPI_PLAIN, none_field(), &sc->gamma_new, TK_DSLASH_B, &sc->status, st)) !=
+  if ((e = op(c, c->r, c->s, 1, EPI_PLAIN, none_field(), &sc->gamma_new, TK_DSLASH_B, &sc->status, st)) !=
       cudaSuccess)
     return e;
   // x += alpha p; p = s + beta p; loop condition
-  return launch_cg_update_xp(c->wprec, c->x, c->p, c->s, c->V, sc, c->partials, use_cond, cond, bb, c->sms, st);
+  return launch_cg_update_xp(c->wprec, c->x, c->p, c->s, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb, c->sms, st);
 }
 
 cudaError_t plain_epilogue(wd_ctx* c, cudaStream_t st) {
-  // true residual eta - D x into q
-  return dslash(c, c->x, c->q, 0, EPI_RESID, c->eta, &c->sc->rr_true, TK_DSLASH_C, nullptr, st);
+  // true residual eta - D x into q (even-odd: b_e - M x_e, which equals the full residual once the
+  // odd half is reconstructed below)
+  cudaError_t e = op(c, c->x, c->q, 0, EPI_RESID, c->eta, &c->sc->rr_true, TK_DSLASH_C, nullptr, st);
+  if (e != cudaSuccess || !c->eo) return e;
+  // x_o = eta_o + kappa H_oe x_e
+  return eo_half(c, c->x, c->x, 1, +1.0, 0, &c->eta, nullptr, nullptr, 0, nullptr, st);
 }
 
 // ---------------------------------------------------------------- mixed precision CG
@@ -250,12 +304,12 @@ cudaError_t mixed_prologue(wd_ctx* c, cudaStream_t st, int use_cond, unsigned lo
   const int bb = c->block_blas;
   if ((e = launch_cg_init(sc, 0, st)) != cudaSuccess) return e;
   // r_hi = eta - D x_hi (FP64); x_lo = 0; r_lo = r_hi
-  if ((e = dslash(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, nullptr, st)) != cudaSuccess)
+  if ((e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, nullptr, st)) != cudaSuccess)
     return e;
   if ((e = launch_zero(c->x.p, spinor_bytes(c->x.prec, c->V), st)) != cudaSuccess) return e;
-  if ((e = launch_mp_convert(c->r64, c->r, c->V, sc, c->partials, 0, nullptr, bb, st)) != cudaSuccess) return e;
+  if ((e = launch_mp_convert(c->r64, c->r, c->nsolve, c->V, sc, c->partials, 0, nullptr, bb, st)) != cudaSuccess) return e;
   // p = D^dag r_lo
-  if ((e = dslash(c, c->r, c->p, 1, EPI_PLAIN, none_field(), &sc->gamma, TK_DSLASH_B, nullptr, st)) != cudaSuccess)
+  if ((e = op(c, c->r, c->p, 1, EPI_PLAIN, none_field(), &sc->gamma, TK_DSLASH_B, nullptr, st)) != cudaSuccess)
     return e;
   return launch_cg_check(sc, use_cond, cond, st);
 }
@@ -265,33 +319,35 @@ cudaError_t mixed_update(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
   CgScalars* sc = c->sc;
   const int bb = c->block_blas;
-  if ((e = launch_mp_accumulate(c->x64, c->x, c->V, nullptr, bb, st)) != cudaSuccess) return e;
-  if ((e = dslash(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, nullptr, st)) != cudaSuccess)
+  if ((e = launch_mp_accumulate(c->x64, c->x, c->nsolve, c->V, nullptr, bb, st)) != cudaSuccess) return e;
+  if ((e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, nullptr, st)) != cudaSuccess)
     return e;
-  return launch_mp_convert(c->r64, c->r, c->V, sc, c->partials, 1, nullptr, bb, st);
+  return launch_mp_convert(c->r64, c->r, c->nsolve, c->V, sc, c->partials, 1, nullptr, bb, st);
 }
 
 cudaError_t mixed_body_a(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long upd) {
   cudaError_t e;
   CgScalars* sc = c->sc;
-  if ((e = dslash(c, c->p, c->q, 0, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
+  if ((e = op(c, c->p, c->q, 0, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
     return e;
-  return launch_mp_update_rx(c->wprec, c->r, c->q, c->p, c->x, c->V, sc, c->partials, use_cond, upd, c->block_blas, st);
+  return launch_mp_update_rx(c->wprec, c->r, c->q, c->p, c->x, c->nsolve, c->V, sc, c->partials, use_cond, upd, c->block_blas, st);
 }
 
 cudaError_t mixed_body_b(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
   cudaError_t e;
   CgScalars* sc = c->sc;
-  if ((e = dslash(c, c->r, c->s, 1, EPI_PLAIN, none_field(), &sc->gamma_new, TK_DSLASH_B, &sc->status, st)) !=
+  if ((e = op(c, c->r, c->s, 1, EPI_PLAIN, none_field(), &sc->gamma_new, TK_DSLASH_B, &sc->status, st)) !=
       cudaSuccess)
     return e;
-  return launch_mp_update_p(c->wprec, c->p, c->s, c->V, sc, c->partials, use_cond, cond, c->block_blas, st);
+  return launch_mp_update_p(c->wprec, c->p, c->s, c->nsolve, c->V, sc, c->partials, use_cond, cond, c->block_blas, st);
 }
 
 cudaError_t mixed_epilogue(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
-  if ((e = launch_mp_accumulate(c->x64, c->x, c->V, nullptr, c->block_blas, st)) != cudaSuccess) return e;
-  return dslash(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &c->sc->rr_true, TK_DSLASH_C, nullptr, st);
+  if ((e = launch_mp_accumulate(c->x64, c->x, c->nsolve, c->V, nullptr, c->block_blas, st)) != cudaSuccess) return e;
+  e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &c->sc->rr_true, TK_DSLASH_C, nullptr, st);
+  if (e != cudaSuccess || !c->eo) return e;
+  return eo_half(c, c->x64, c->x64, 1, +1.0, 0, &c->eta64, nullptr, nullptr, 0, nullptr, st);
 }
 
 // reliable update with skip flags instead of a conditional node: each kernel checks the flag
@@ -299,11 +355,11 @@ cudaError_t mixed_update_flagged(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
   CgScalars* sc = c->sc;
   const int bb = c->block_blas;
-  if ((e = launch_mp_accumulate(c->x64, c->x, c->V, &sc->need_update, bb, st)) != cudaSuccess) return e;
-  if ((e = dslash(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, &sc->no_update, st)) !=
+  if ((e = launch_mp_accumulate(c->x64, c->x, c->nsolve, c->V, &sc->need_update, bb, st)) != cudaSuccess) return e;
+  if ((e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, &sc->no_update, st)) !=
       cudaSuccess)
     return e;
-  return launch_mp_convert(c->r64, c->r, c->V, sc, c->partials, 1, &sc->need_update, bb, st);
+  return launch_mp_convert(c->r64, c->r, c->nsolve, c->V, sc, c->partials, 1, &sc->need_update, bb, st);
 }
 
 // ---------------------------------------------------------------- graph construction
@@ -471,10 +527,10 @@ wd_status autotune_single(wd_ctx* c) {
     const int reps = prec == SP64 ? 2 : 4;
     for (int b : cands) {
       c->tuned_block[prec] = b;
-      WD_CUDA(dslash(c, in, out, 0, EPI_PLAIN, none_field(), &c->sc->scratch[1], TK_MISC, nullptr, c->stream));
+      WD_CUDA(op(c, in, out, 0, EPI_PLAIN, none_field(), &c->sc->scratch[1], TK_MISC, nullptr, c->stream));
       WD_CUDA(cudaEventRecord(c->ev0, c->stream));
       for (int i = 0; i < reps; ++i)
-        WD_CUDA(dslash(c, in, out, 0, EPI_PLAIN, none_field(), &c->sc->scratch[1], TK_MISC, nullptr, c->stream));
+        WD_CUDA(op(c, in, out, 0, EPI_PLAIN, none_field(), &c->sc->scratch[1], TK_MISC, nullptr, c->stream));
       WD_CUDA(cudaEventRecord(c->ev1, c->stream));
       WD_CUDA(cudaEventSynchronize(c->ev1));
       float ms = 0.f;
@@ -896,6 +952,12 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
       bc[i] = boundary[i];
     }
   }
+  const int eo = (precision & WD_EVEN_ODD) ? 1 : 0;
+  precision &= ~WD_EVEN_ODD;
+  if (eo) {
+    for (int i = 0; i < 4; ++i)
+      if (dims[i] % 2) return fail(WD_EINVAL, "even-odd preconditioning needs every extent even");
+  }
   int wprec;
   switch (precision) {
     case WD_PREC_F64: wprec = SP64; break;
@@ -913,6 +975,8 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
   c->V = (int)V;
   c->precision = precision;
   c->wprec = wprec;
+  c->eo = eo;
+  c->nsolve = eo ? (int)(V / 2) : (int)V;
   c->kappa = kappa;
   c->geom.L[0] = dims[0];
   c->geom.L[1] = dims[1];
@@ -956,6 +1020,11 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
     if ((st = alloc_field(c, &c->r64, SP64)) != WD_OK) return bail(st);
     if ((st = alloc_field(c, &c->eta64, SP64)) != WD_OK) return bail(st);
   }
+  if (eo) {
+    if ((st = alloc_field(c, &c->t, wprec)) != WD_OK) return bail(st);
+    if (mixed && (st = alloc_field(c, &c->t64, SP64)) != WD_OK) return bail(st);
+    if (wprec == SP64) c->t64 = c->t;
+  }
   // the largest grid of any reduction: 12 V words at 32 threads per block, or 4 V links
   c->partials_len = (size_t)(12 * V / 32 + 64);
   if (cudaMalloc(&c->partials, sizeof(double) * c->partials_len) != cudaSuccess ||
@@ -990,6 +1059,9 @@ void wd_destroy(wd_ctx* c) {
   free_field(&c->x64);
   free_field(&c->r64);
   free_field(&c->eta64);
+  if (c->t64.p == c->t.p) c->t64.p = nullptr;
+  free_field(&c->t);
+  free_field(&c->t64);
   if (c->gauge64) cudaFree(c->gauge64);
   if (c->gauge32) cudaFree(c->gauge32);
   if (c->staging) cudaFree(c->staging);
@@ -1083,7 +1155,7 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
     g.p = c->gauge64;
     g.prec = SP64;
     g.c12 = 0;
-    if (launch_gauge_load(src, g, c->V, red_to(c, TK_GAUGE, &c->sc->max_dev), gb, c->stream) != cudaSuccess)
+    if (launch_gauge_load(src, g, c->V, eo_geom(c), red_to(c, TK_GAUGE, &c->sc->max_dev), gb, c->stream) != cudaSuccess)
       return fail(WD_ECUDA, "gauge load kernel failed to launch");
   }
   if (need32) {
@@ -1093,7 +1165,7 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
     g.c12 = c12;
     // the deviation is measured once (on the FP64 pass when there is one)
     Red r = need64 ? no_red() : red_to(c, TK_GAUGE, &c->sc->max_dev);
-    if (launch_gauge_load(src, g, c->V, r, gb, c->stream) != cudaSuccess)
+    if (launch_gauge_load(src, g, c->V, eo_geom(c), r, gb, c->stream) != cudaSuccess)
       return fail(WD_ECUDA, "gauge load kernel failed to launch");
   }
   if (cudaMemcpyAsync(c->sc_host, c->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -1116,15 +1188,15 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
   if ((st = autotune_single(c)) != WD_OK) return st;
   const int bb = c->block_blas;
   if (c->precision == WD_PREC_F32) {
-    WD_CUDA(launch_pack_c64((const float*)in, c->q, c->V, bb, c->stream));
-    WD_CUDA(dslash(c, c->q, c->s, dagger ? 1 : 0, EPI_PLAIN, none_field(), nullptr, 0, nullptr, c->stream));
-    WD_CUDA(launch_unpack_c64(c->s, (float*)out, c->V, bb, c->stream));
+    WD_CUDA(launch_pack_c64((const float*)in, c->q, c->V, eo_geom(c), bb, c->stream));
+    WD_CUDA(full_D(c, c->q, c->s, dagger ? 1 : 0, c->stream));
+    WD_CUDA(launch_unpack_c64(c->s, (float*)out, c->V, eo_geom(c), bb, c->stream));
   } else {
     FieldPtr a = c->wprec == SP64 ? c->q : c->x64;
     FieldPtr b = c->wprec == SP64 ? c->s : c->r64;
-    WD_CUDA(launch_pack((const double*)in, a, c->V, no_red(), bb, c->stream));
-    WD_CUDA(dslash(c, a, b, dagger ? 1 : 0, EPI_PLAIN, none_field(), nullptr, 0, nullptr, c->stream));
-    WD_CUDA(launch_unpack(b, (double*)out, c->V, bb, c->stream));
+    WD_CUDA(launch_pack((const double*)in, a, c->V, eo_geom(c), no_red(), bb, c->stream));
+    WD_CUDA(full_D(c, a, b, dagger ? 1 : 0, c->stream));
+    WD_CUDA(launch_unpack(b, (double*)out, c->V, eo_geom(c), bb, c->stream));
   }
   WD_CUDA(cudaStreamSynchronize(c->stream));
   return WD_OK;
@@ -1146,8 +1218,13 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
   FieldPtr xs = mixed ? c->x64 : c->x;
   set_params_kernel<<<1, 32, 0, c->stream>>>(sc, tol * tol, c->delta * c->delta, maxit, nullptr);
   WD_CUDA(cudaGetLastError());
-  WD_CUDA(launch_pack((const double*)src, eta, c->V, red_to(c, TK_PACK, &sc->eta2), bb, c->stream));
-  WD_CUDA(launch_pack((const double*)x, xs, c->V, no_red(), bb, c->stream));
+  WD_CUDA(launch_pack((const double*)src, eta, c->V, eo_geom(c), red_to(c, TK_PACK, &sc->eta2), bb, c->stream));
+  WD_CUDA(launch_pack((const double*)x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
+  if (c->eo) {
+    // Schur source on the even sites, in place: b_e = eta_e + kappa H_eo eta_o (eta_o is kept for
+    // the reconstruction x_o = eta_o + kappa H_oe x_e)
+    WD_CUDA(eo_half(c, eta, eta, 0, +1.0, 0, &eta, nullptr, nullptr, 0, nullptr, c->stream));
+  }
   if ((st = autotune_single(c)) != WD_OK) return st;
   if (c->use_graph) {
     if ((st = build_graph(c)) != WD_OK) return st;
@@ -1178,7 +1255,7 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
     }
     ++restarts;
   }
-  WD_CUDA(launch_unpack(xs, (double*)x, c->V, bb, c->stream));
+  WD_CUDA(launch_unpack(xs, (double*)x, c->V, eo_geom(c), bb, c->stream));
   WD_CUDA(cudaStreamSynchronize(c->stream));
   const CgScalars& h = *c->sc_host;
   const auto t1 = std::chrono::steady_clock::now();
@@ -1214,10 +1291,10 @@ wd_status wd_time_dslash(wd_ctx* c, int dagger, int launches, double* avg_ms) {
   if ((st = autotune_single(c)) != WD_OK) return st;
   // the solver's dominant dslash: the working precision one, with its fused norm
   FieldPtr in = c->p, out = c->q;
-  WD_CUDA(dslash(c, in, out, dagger, EPI_PLAIN, none_field(), &c->sc->scratch[0], TK_MISC, nullptr, c->stream));
+  WD_CUDA(op(c, in, out, dagger, EPI_PLAIN, none_field(), &c->sc->scratch[0], TK_MISC, nullptr, c->stream));
   WD_CUDA(cudaEventRecord(c->ev0, c->stream));
   for (int i = 0; i < launches; ++i)
-    WD_CUDA(dslash(c, in, out, dagger, EPI_PLAIN, none_field(), &c->sc->scratch[0], TK_MISC, nullptr, c->stream));
+    WD_CUDA(op(c, in, out, dagger, EPI_PLAIN, none_field(), &c->sc->scratch[0], TK_MISC, nullptr, c->stream));
   WD_CUDA(cudaEventRecord(c->ev1, c->stream));
   WD_CUDA(cudaEventSynchronize(c->ev1));
   float ms = 0.f;
@@ -1237,6 +1314,7 @@ wd_status wd_apply_multi(wd_ctx* c, const double* in, double* out, int nrhs, int
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!in || !out || in == out) return fail(WD_EINVAL, "null or aliased field pointer");
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(WD_EINVAL, "nrhs must be in [1, 16]");
+  if (c->eo) return fail(WD_EINVAL, "multi-RHS calls need a context without WD_EVEN_ODD");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
   if ((st = ensure_multi(c, nrhs)) != WD_OK) return st;
   if ((st = ensure_multi_tuned(c)) != WD_OK) return st;
@@ -1260,6 +1338,7 @@ wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, doub
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(WD_EINVAL, "nrhs must be in [1, 16]");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(WD_EINVAL, "tol must be a positive finite number");
   if (maxit < 0 || maxit > 10000000) return fail(WD_EINVAL, "maxit must be in [0, 10^7]");
+  if (c->eo) return fail(WD_EINVAL, "multi-RHS calls need a context without WD_EVEN_ODD");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
   const auto t0 = std::chrono::steady_clock::now();
   if ((st = ensure_multi(c, nrhs)) != WD_OK) return st;
@@ -1342,7 +1421,7 @@ wd_status wd_generate_gauge(wd_ctx* c, double eps, unsigned long long seed, int 
   bool need64 = false, need32 = false;
   int c12 = 0;
   if ((st = ensure_gauge_buffers(c, compress12, &need64, &need32, &c12)) != WD_OK) return st;
-  WD_CUDA(launch_gen_gauge(c->V, eps, seed, need64 ? c->gauge64 : nullptr, need32 ? c->gauge32 : nullptr, c12, U_out,
+  WD_CUDA(launch_gen_gauge(c->V, eo_geom(c), eps, seed, need64 ? c->gauge64 : nullptr, need32 ? c->gauge32 : nullptr, c12, U_out,
                            c->stream));
   WD_CUDA(cudaStreamSynchronize(c->stream));
   c->gauge_loaded = true;

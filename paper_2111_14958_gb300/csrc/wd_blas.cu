@@ -18,8 +18,29 @@ struct Work<P64> {
   typedef double R;
 };
 
+// Canonical (lexicographic) site n -> storage site: n itself, or its parity-ordered index when the
+// context stores fields even-odd (L = extents; all even).
+struct SiteMap {
+  int eo;
+  int L[4];
+  int V;
+};
+
+__device__ __forceinline__ int map_site(const SiteMap& m, int n) {
+  if (!m.eo) return n;
+  int r = n;
+  const int x = r % m.L[0];
+  r /= m.L[0];
+  const int y = r % m.L[1];
+  r /= m.L[1];
+  const int z = r % m.L[2];
+  const int t = r / m.L[2];
+  const int par = (x + y + z + t) & 1;
+  return par * (m.V >> 1) + (x >> 1) + (m.L[0] >> 1) * (y + m.L[1] * (z + m.L[2] * t));
+}
+
 template <int SP, bool NORM>
-__global__ void pack_kernel(const double2* __restrict__ canon, SpinorRef<SP> out, int V, double* partials,
+__global__ void pack_kernel(const double2* __restrict__ canon, SpinorRef<SP> out, int V, SiteMap m, double* partials,
                             unsigned* ticket, double* result) {
   typedef typename Work<SP>::R R;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -33,7 +54,7 @@ __global__ void pack_kernel(const double2* __restrict__ canon, SpinorRef<SP> out
       n2 = fma(d.y, d.y, n2);
       v[c] = cx<R>((R)d.x, (R)d.y);
     }
-    store_spinor(out, s, V, v);
+    store_spinor(out, map_site(m, s), V, v);
   }
   if (NORM) {
     double a[1] = {n2}, tot[1];
@@ -41,7 +62,7 @@ __global__ void pack_kernel(const double2* __restrict__ canon, SpinorRef<SP> out
   }
 }
 
-__global__ void pack_c64_kernel(const float2* __restrict__ canon, SpinorRef<P32> out, int V) {
+__global__ void pack_c64_kernel(const float2* __restrict__ canon, SpinorRef<P32> out, int V, SiteMap m) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   Cx<float> v[12];
@@ -50,25 +71,25 @@ __global__ void pack_c64_kernel(const float2* __restrict__ canon, SpinorRef<P32>
     const float2 d = canon[(size_t)s * 12 + c];
     v[c] = cx(d.x, d.y);
   }
-  store_spinor(out, s, V, v);
+  store_spinor(out, map_site(m, s), V, v);
 }
 
 template <int SP>
-__global__ void unpack_kernel(SpinorRef<SP> in, double2* __restrict__ canon, int V) {
+__global__ void unpack_kernel(SpinorRef<SP> in, double2* __restrict__ canon, int V, SiteMap m) {
   typedef typename Work<SP>::R R;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   Cx<R> v[12];
-  load_spinor(in, s, V, v);
+  load_spinor(in, map_site(m, s), V, v);
 #pragma unroll
   for (int c = 0; c < 12; ++c) canon[(size_t)s * 12 + c] = make_double2((double)v[c].re, (double)v[c].im);
 }
 
-__global__ void unpack_c64_kernel(SpinorRef<P32> in, float2* __restrict__ canon, int V) {
+__global__ void unpack_c64_kernel(SpinorRef<P32> in, float2* __restrict__ canon, int V, SiteMap m) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   Cx<float> v[12];
-  load_spinor(in, s, V, v);
+  load_spinor(in, map_site(m, s), V, v);
 #pragma unroll
   for (int c = 0; c < 12; ++c) canon[(size_t)s * 12 + c] = make_float2(v[c].re, v[c].im);
 }
@@ -96,47 +117,61 @@ SpinorRef<P16> view<P16>(FieldPtr f) {
   return r;
 }
 
+static SiteMap site_map(const GeomH* eo) {
+  SiteMap m;
+  m.eo = eo != nullptr;
+  for (int i = 0; i < 4; ++i) m.L[i] = eo ? eo->L[i] : 0;
+  m.V = eo ? eo->V : 0;
+  return m;
+}
+
 template <int SP>
-static cudaError_t pack_t(const double* canon, FieldPtr out, int V, Red red, int block, cudaStream_t st) {
+static cudaError_t pack_t(const double* canon, FieldPtr out, int V, const GeomH* eo, Red red, int block,
+                          cudaStream_t st) {
   const int grid = grid_for(V, block);
   const double2* c2 = reinterpret_cast<const double2*>(canon);
+  const SiteMap m = site_map(eo);
   if (red.result)
-    pack_kernel<SP, true><<<grid, block, 0, st>>>(c2, view<SP>(out), V, red.partials, red.ticket, red.result);
+    pack_kernel<SP, true><<<grid, block, 0, st>>>(c2, view<SP>(out), V, m, red.partials, red.ticket, red.result);
   else
-    pack_kernel<SP, false><<<grid, block, 0, st>>>(c2, view<SP>(out), V, nullptr, nullptr, nullptr);
+    pack_kernel<SP, false><<<grid, block, 0, st>>>(c2, view<SP>(out), V, m, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const double* canon, FieldPtr out, int V, Red red, int block, cudaStream_t st) {
+cudaError_t launch_pack(const double* canon, FieldPtr out, int V, const GeomH* eo, Red red, int block,
+                        cudaStream_t st) {
   switch (out.prec) {
-    case SP64: return pack_t<P64>(canon, out, V, red, block, st);
-    case SP32: return pack_t<P32>(canon, out, V, red, block, st);
-    case SP16: return pack_t<P16>(canon, out, V, red, block, st);
+    case SP64: return pack_t<P64>(canon, out, V, eo, red, block, st);
+    case SP32: return pack_t<P32>(canon, out, V, eo, red, block, st);
+    case SP16: return pack_t<P16>(canon, out, V, eo, red, block, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_pack_c64(const float* canon, FieldPtr out, int V, int block, cudaStream_t st) {
+cudaError_t launch_pack_c64(const float* canon, FieldPtr out, int V, const GeomH* eo, int block, cudaStream_t st) {
   if (out.prec != SP32) return cudaErrorInvalidValue;
-  pack_c64_kernel<<<grid_for(V, block), block, 0, st>>>(reinterpret_cast<const float2*>(canon), view<P32>(out), V);
+  pack_c64_kernel<<<grid_for(V, block), block, 0, st>>>(reinterpret_cast<const float2*>(canon), view<P32>(out), V,
+                                                        site_map(eo));
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(FieldPtr in, double* canon, int V, int block, cudaStream_t st) {
+cudaError_t launch_unpack(FieldPtr in, double* canon, int V, const GeomH* eo, int block, cudaStream_t st) {
   double2* c2 = reinterpret_cast<double2*>(canon);
   const int grid = grid_for(V, block);
+  const SiteMap m = site_map(eo);
   switch (in.prec) {
-    case SP64: unpack_kernel<P64><<<grid, block, 0, st>>>(view<P64>(in), c2, V); break;
-    case SP32: unpack_kernel<P32><<<grid, block, 0, st>>>(view<P32>(in), c2, V); break;
-    case SP16: unpack_kernel<P16><<<grid, block, 0, st>>>(view<P16>(in), c2, V); break;
+    case SP64: unpack_kernel<P64><<<grid, block, 0, st>>>(view<P64>(in), c2, V, m); break;
+    case SP32: unpack_kernel<P32><<<grid, block, 0, st>>>(view<P32>(in), c2, V, m); break;
+    case SP16: unpack_kernel<P16><<<grid, block, 0, st>>>(view<P16>(in), c2, V, m); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_c64(FieldPtr in, float* canon, int V, int block, cudaStream_t st) {
+cudaError_t launch_unpack_c64(FieldPtr in, float* canon, int V, const GeomH* eo, int block, cudaStream_t st) {
   if (in.prec != SP32) return cudaErrorInvalidValue;
-  unpack_c64_kernel<<<grid_for(V, block), block, 0, st>>>(view<P32>(in), reinterpret_cast<float2*>(canon), V);
+  unpack_c64_kernel<<<grid_for(V, block), block, 0, st>>>(view<P32>(in), reinterpret_cast<float2*>(canon), V,
+                                                          site_map(eo));
   return cudaGetLastError();
 }
 
@@ -145,12 +180,12 @@ cudaError_t launch_unpack_c64(FieldPtr in, float* canon, int V, int block, cudaS
 // One thread per (site, mu). Stores the link in the device layout and measures its distance
 // from SU(3): max(|U^dag U - 1|_max, |det U - 1|).
 template <int GP, bool C12, bool CHECK>
-__global__ void gauge_load_kernel(const double2* __restrict__ canon, void* out, int V, double* partials,
+__global__ void gauge_load_kernel(const double2* __restrict__ canon, void* out, int V, SiteMap m, double* partials,
                                   unsigned* ticket, double* result) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // i = 4 * s + mu
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // i = 4 * n + mu, n canonical
   double dev = 0.0;
   if (i < 4 * V) {
-    const int s = i >> 2, mu = i & 3;
+    const int s = map_site(m, i >> 2), mu = i & 3;
     Cx<double> u[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -207,17 +242,19 @@ __global__ void gauge_load_kernel(const double2* __restrict__ canon, void* out, 
   }
 }
 
-cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, Red red, int block, cudaStream_t st) {
+cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, const GeomH* eo, Red red, int block,
+                              cudaStream_t st) {
   const int grid = grid_for(4 * V, block);
+  const SiteMap m = site_map(eo);
   const double2* c2 = reinterpret_cast<const double2*>(canon);
   void* o = const_cast<void*>(out.p);
   const bool chk = red.result != nullptr;
 #define WD_GL(GP, C12)                                                                                        \
   do {                                                                                                        \
     if (chk)                                                                                                  \
-      gauge_load_kernel<GP, C12, true><<<grid, block, 0, st>>>(c2, o, V, red.partials, red.ticket, red.result); \
+      gauge_load_kernel<GP, C12, true><<<grid, block, 0, st>>>(c2, o, V, m, red.partials, red.ticket, red.result); \
     else                                                                                                      \
-      gauge_load_kernel<GP, C12, false><<<grid, block, 0, st>>>(c2, o, V, nullptr, nullptr, nullptr);         \
+      gauge_load_kernel<GP, C12, false><<<grid, block, 0, st>>>(c2, o, V, m, nullptr, nullptr, nullptr);         \
   } while (0)
   if (out.prec == SP64)
     WD_GL(P64, false);
@@ -264,7 +301,7 @@ __global__ void cg_check_kernel(CgScalars* sc, int use_cond, cudaGraphConditiona
 
 // alpha = gamma / ||q||^2; r -= alpha q; ||r||^2. Converged or breakdown is decided here.
 template <int SP>
-__global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int V, CgScalars* sc, double* partials) {
+__global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int V, CgScalars* sc, double* partials) {
   typedef typename Work<SP>::R R;
   if (sc->status != ST_RUNNING) return;  // uniform
   const double qq = sc->qq, gamma = sc->gamma;
@@ -273,7 +310,7 @@ __global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int V, CgSc
   const R a = (R)alpha;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double n2 = 0.0;
-  if (ok && s < V) {
+  if (ok && s < n) {
     Cx<R> rv[12], qv[12];
     load_spinor(r, s, V, rv);
     load_spinor(q, s, V, qv);
@@ -300,7 +337,7 @@ __global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int V, CgSc
 // applies the iteration limit and sets the loop condition. Every block always takes a ticket, so
 // the condition is set on every pass: the loop cannot run on without an update.
 template <int SP>
-__global__ void cg_update_xp_kernel(SpinorRef<SP> x, SpinorRef<SP> p, SpinorRef<SP> sv, int V, CgScalars* sc,
+__global__ void cg_update_xp_kernel(SpinorRef<SP> x, SpinorRef<SP> p, SpinorRef<SP> sv, int n, int V, CgScalars* sc,
                                     double* partials, int use_cond, cudaGraphConditionalHandle cond) {
   typedef typename Work<SP>::R R;
   const int st0 = sc->status;  // uniform: only this kernel's last block changes it below
@@ -311,7 +348,7 @@ __global__ void cg_update_xp_kernel(SpinorRef<SP> x, SpinorRef<SP> p, SpinorRef<
   const double beta = do_p ? gnew / gold : 0.0;
   const R a = (R)alpha, b = (R)beta;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < V && do_x) {
+  if (s < n && do_x) {
     Cx<R> xv[12], pv[12];
     load_spinor(x, s, V, xv);
     load_spinor(p, s, V, pv);
@@ -360,36 +397,36 @@ cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int V, CgScalars* sc, double* partials, int block,
-                               int sms, cudaStream_t st) {
-  const int grid = grid_for(V, block);
+cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, CgScalars* sc, double* partials,
+                               int block, int sms, cudaStream_t st) {
+  const int grid = grid_for(n, block);
   (void)sms;
   switch (prec) {
-    case SP64: cg_update_r_kernel<P64><<<grid, block, 0, st>>>(view<P64>(r), view<P64>(q), V, sc, partials); break;
-    case SP32: cg_update_r_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), V, sc, partials); break;
-    case SP16: cg_update_r_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), V, sc, partials); break;
+    case SP64: cg_update_r_kernel<P64><<<grid, block, 0, st>>>(view<P64>(r), view<P64>(q), n, V, sc, partials); break;
+    case SP32: cg_update_r_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), n, V, sc, partials); break;
+    case SP16: cg_update_r_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), n, V, sc, partials); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int V, CgScalars* sc,
+cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int n, int V, CgScalars* sc,
                                 double* partials, int use_cond, unsigned long long cond, int block, int sms,
                                 cudaStream_t st) {
-  const int grid = grid_for(V, block);
+  const int grid = grid_for(n, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
   (void)sms;
   switch (prec) {
     case SP64:
-      cg_update_xp_kernel<P64><<<grid, block, 0, st>>>(view<P64>(x), view<P64>(p), view<P64>(s), V, sc, partials,
+      cg_update_xp_kernel<P64><<<grid, block, 0, st>>>(view<P64>(x), view<P64>(p), view<P64>(s), n, V, sc, partials,
                                                        use_cond, h);
       break;
     case SP32:
-      cg_update_xp_kernel<P32><<<grid, block, 0, st>>>(view<P32>(x), view<P32>(p), view<P32>(s), V, sc, partials,
+      cg_update_xp_kernel<P32><<<grid, block, 0, st>>>(view<P32>(x), view<P32>(p), view<P32>(s), n, V, sc, partials,
                                                        use_cond, h);
       break;
     case SP16:
-      cg_update_xp_kernel<P16><<<grid, block, 0, st>>>(view<P16>(x), view<P16>(p), view<P16>(s), V, sc, partials,
+      cg_update_xp_kernel<P16><<<grid, block, 0, st>>>(view<P16>(x), view<P16>(p), view<P16>(s), n, V, sc, partials,
                                                        use_cond, h);
       break;
     default: return cudaErrorInvalidValue;
@@ -407,7 +444,7 @@ cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, in
 // alpha = gamma / ||q||^2; r_lo -= alpha q; x_lo += alpha p; ||r_lo||^2; decide on an update.
 template <int SPW>
 __global__ void mp_update_rx_kernel(SpinorRef<SPW> r, SpinorRef<SPW> q, SpinorRef<SPW> p, SpinorRef<P32> xlo,
-                                    int V, CgScalars* sc, double* partials, int use_cond,
+                                    int n, int V, CgScalars* sc, double* partials, int use_cond,
                                     cudaGraphConditionalHandle upd) {
   typedef float R;
   const int st0 = sc->status;
@@ -417,7 +454,7 @@ __global__ void mp_update_rx_kernel(SpinorRef<SPW> r, SpinorRef<SPW> q, SpinorRe
   const R a = (R)alpha;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double n2 = 0.0;
-  if (ok && s < V) {
+  if (ok && s < n) {
     Cx<R> rv[12], qv[12], pv[12], xv[12];
     load_spinor(r, s, V, rv);
     load_spinor(q, s, V, qv);
@@ -456,10 +493,10 @@ __global__ void mp_update_rx_kernel(SpinorRef<SPW> r, SpinorRef<SPW> q, SpinorRe
 }
 
 // x_hi += x_lo; x_lo = 0
-__global__ void mp_accumulate_kernel(SpinorRef<P64> xhi, SpinorRef<P32> xlo, int V, const int* skip) {
+__global__ void mp_accumulate_kernel(SpinorRef<P64> xhi, SpinorRef<P32> xlo, int n, int V, const int* skip) {
   if (skip != nullptr && *skip == 0) return;  // runs only when an update is pending
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= V) return;
+  if (s >= n) return;
   Cx<double> xh[12];
   Cx<float> xl[12];
   load_spinor(xhi, s, V, xh);
@@ -477,11 +514,11 @@ __global__ void mp_accumulate_kernel(SpinorRef<P64> xhi, SpinorRef<P32> xlo, int
 // r_lo = r_hi (FP64 -> W). The last block adopts ||r_hi||^2 as the new reference and decides
 // convergence on this FP64 residual. count = 0 for the initial conversion.
 template <int SPW>
-__global__ void mp_convert_kernel(SpinorRef<P64> rhi, SpinorRef<SPW> rlo, int V, CgScalars* sc, double* partials,
+__global__ void mp_convert_kernel(SpinorRef<P64> rhi, SpinorRef<SPW> rlo, int n, int V, CgScalars* sc, double* partials,
                                   int count, const int* skip) {
   if (skip != nullptr && *skip == 0) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < V) {
+  if (s < n) {
     Cx<double> h[12];
     Cx<float> l[12];
     load_spinor(rhi, s, V, h);
@@ -506,7 +543,7 @@ __global__ void mp_convert_kernel(SpinorRef<P64> rhi, SpinorRef<SPW> rlo, int V,
 
 // p = s + beta p. The last block advances the iteration and sets the loop condition.
 template <int SPW>
-__global__ void mp_update_p_kernel(SpinorRef<SPW> p, SpinorRef<SPW> sv, int V, CgScalars* sc, double* partials,
+__global__ void mp_update_p_kernel(SpinorRef<SPW> p, SpinorRef<SPW> sv, int n, int V, CgScalars* sc, double* partials,
                                    int use_cond, cudaGraphConditionalHandle cond) {
   typedef float R;
   const int st0 = sc->status;
@@ -515,7 +552,7 @@ __global__ void mp_update_p_kernel(SpinorRef<SPW> p, SpinorRef<SPW> sv, int V, C
   const double beta = do_p ? gnew / gold : 0.0;
   const R b = (R)beta;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (do_p && s < V) {
+  if (do_p && s < n) {
     Cx<R> pv[12], svv[12];
     load_spinor(p, s, V, pv);
     load_spinor(sv, s, V, svv);
@@ -550,18 +587,19 @@ __global__ void zero_kernel(float4* p, size_t n4) {
   if (i < n4) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int V, CgScalars* sc,
-                                double* partials, int use_cond, unsigned long long upd, int block, cudaStream_t st) {
-  const int grid = grid_for(V, block);
+cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int n, int V,
+                                CgScalars* sc, double* partials, int use_cond, unsigned long long upd, int block,
+                                cudaStream_t st) {
+  const int grid = grid_for(n, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)upd;
   if (xlo.prec != SP32) return cudaErrorInvalidValue;
   switch (precw) {
     case SP32:
-      mp_update_rx_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), view<P32>(p), view<P32>(xlo), V, sc,
+      mp_update_rx_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), view<P32>(p), view<P32>(xlo), n, V, sc,
                                                        partials, use_cond, h);
       break;
     case SP16:
-      mp_update_rx_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), view<P16>(p), view<P32>(xlo), V, sc,
+      mp_update_rx_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), view<P16>(p), view<P32>(xlo), n, V, sc,
                                                        partials, use_cond, h);
       break;
     default: return cudaErrorInvalidValue;
@@ -569,38 +607,39 @@ cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, F
   return cudaGetLastError();
 }
 
-cudaError_t launch_mp_accumulate(FieldPtr xhi, FieldPtr xlo, int V, const int* skip, int block, cudaStream_t st) {
+cudaError_t launch_mp_accumulate(FieldPtr xhi, FieldPtr xlo, int n, int V, const int* skip, int block,
+                                 cudaStream_t st) {
   if (xhi.prec != SP64 || xlo.prec != SP32) return cudaErrorInvalidValue;
-  mp_accumulate_kernel<<<grid_for(V, block), block, 0, st>>>(view<P64>(xhi), view<P32>(xlo), V, skip);
+  mp_accumulate_kernel<<<grid_for(n, block), block, 0, st>>>(view<P64>(xhi), view<P32>(xlo), n, V, skip);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mp_convert(FieldPtr rhi, FieldPtr rlo, int V, CgScalars* sc, double* partials, int count,
+cudaError_t launch_mp_convert(FieldPtr rhi, FieldPtr rlo, int n, int V, CgScalars* sc, double* partials, int count,
                               const int* skip, int block, cudaStream_t st) {
-  const int grid = grid_for(V, block);
+  const int grid = grid_for(n, block);
   if (rhi.prec != SP64) return cudaErrorInvalidValue;
   switch (rlo.prec) {
     case SP32:
-      mp_convert_kernel<P32><<<grid, block, 0, st>>>(view<P64>(rhi), view<P32>(rlo), V, sc, partials, count, skip);
+      mp_convert_kernel<P32><<<grid, block, 0, st>>>(view<P64>(rhi), view<P32>(rlo), n, V, sc, partials, count, skip);
       break;
     case SP16:
-      mp_convert_kernel<P16><<<grid, block, 0, st>>>(view<P64>(rhi), view<P16>(rlo), V, sc, partials, count, skip);
+      mp_convert_kernel<P16><<<grid, block, 0, st>>>(view<P64>(rhi), view<P16>(rlo), n, V, sc, partials, count, skip);
       break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int V, CgScalars* sc, double* partials,
+cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int n, int V, CgScalars* sc, double* partials,
                                int use_cond, unsigned long long cond, int block, cudaStream_t st) {
-  const int grid = grid_for(V, block);
+  const int grid = grid_for(n, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
   switch (precw) {
     case SP32:
-      mp_update_p_kernel<P32><<<grid, block, 0, st>>>(view<P32>(p), view<P32>(s), V, sc, partials, use_cond, h);
+      mp_update_p_kernel<P32><<<grid, block, 0, st>>>(view<P32>(p), view<P32>(s), n, V, sc, partials, use_cond, h);
       break;
     case SP16:
-      mp_update_p_kernel<P16><<<grid, block, 0, st>>>(view<P16>(p), view<P16>(s), V, sc, partials, use_cond, h);
+      mp_update_p_kernel<P16><<<grid, block, 0, st>>>(view<P16>(p), view<P16>(s), n, V, sc, partials, use_cond, h);
       break;
     default: return cudaErrorInvalidValue;
   }

@@ -173,4 +173,178 @@ cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------- even-odd (Schur) hopping
+//
+// With all extents even, sites split into parities p = (x + y + z + t) mod 2 and the hopping term
+// H of D = 1 - kappa H only connects opposite parities. An even-odd context stores every field in
+// parity order: site (x, y, z, t) of parity p sits at s = p * V/2 + (x/2 + Lx/2 (y + Ly (z + Lz t))).
+// The half kernel computes, for every site of output parity p,
+//   out = [b -] ([self] + c * H in)           c = sign * kappa (kappa read from device memory)
+// with `in` read on parity 1 - p. M = 1 - kappa^2 H_eo H_oe on the even sites is two launches:
+// t_o = kappa H_oe x_e, then M x_e = x_e - kappa H_eo t_o.
+
+struct EoArgsBase {
+  Geom g;
+  int parity;         // output parity
+  double sign;        // c = sign * kappa
+  const double* kappa_dev;
+  const int* skip;
+  double* partials;
+  unsigned* ticket;
+  double* result;
+};
+
+template <int SP, bool C12>
+struct EoArgs {
+  EoArgsBase e;
+  GaugeRef<typename RealOf<SP>::type, C12> u;
+  SpinorRef<SP> in, out, self, b;
+};
+
+// full coordinates of half index i of parity p
+__device__ __forceinline__ void eo_coords(const Geom& g, int i, int p, int (&c)[4]) {
+  const int lxh = g.L[0] >> 1;
+  int r = i;
+  const int xh = r % lxh;
+  r /= lxh;
+  c[1] = r % g.L[1];
+  r /= g.L[1];
+  c[2] = r % g.L[2];
+  c[3] = r / g.L[2];
+  c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
+}
+
+__device__ __forceinline__ int eo_index(const Geom& g, const int (&c)[4]) {
+  const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+  return par * (g.V >> 1) + (c[0] >> 1) + (g.L[0] >> 1) * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
+}
+
+template <int MU, int SF, int SP, bool C12, typename R>
+__device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int s, const int (&c)[4],
+                                            Cx<R> (&acc)[12]) {
+  const int V = a.e.g.V;
+  {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    const bool wrap = n[MU] == a.e.g.L[MU] - 1;
+    n[MU] = wrap ? 0 : n[MU] + 1;
+    const int nb = eo_index(a.e.g, n);
+    const R k = (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0;
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    load_spinor(a.in, nb, V, psi);
+    spin_project<MU, SF>(psi, h);
+    load_link(a.u, MU, s, V, u);
+    su3_mul(u, h, chi);
+    spin_reconstruct<MU, SF>(acc, chi, k);
+  }
+  {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    const bool wrap = n[MU] == 0;
+    n[MU] = wrap ? a.e.g.L[MU] - 1 : n[MU] - 1;
+    const int nb = eo_index(a.e.g, n);
+    const R k = (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0;
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    load_spinor(a.in, nb, V, psi);
+    spin_project<MU, -SF>(psi, h);
+    load_link(a.u, MU, nb, V, u);
+    su3_dag_mul(u, h, chi);
+    spin_reconstruct<MU, -SF>(acc, chi, k);
+  }
+}
+
+template <int SP, bool C12, bool DAG, bool SELF, bool RESID, bool NORM>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
+    dslash_eo_kernel(const EoArgs<SP, C12> a) {
+  typedef typename RealOf<SP>::type R;
+  if (a.e.skip != nullptr && *a.e.skip != 0) return;
+  const int Vh = a.e.g.V >> 1, V = a.e.g.V;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double n2 = 0.0;
+  if (i < Vh) {
+    const int p = a.e.parity;
+    int c[4];
+    eo_coords(a.e.g, i, p, c);
+    const int s = p * Vh + i;
+    const R k0 = (R)(a.e.sign * *a.e.kappa_dev);
+    Cx<R> acc[12];
+    if (SELF) {
+      load_spinor(a.self, s, V, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[j] = cx<R>(0, 0);
+    }
+    constexpr int SF = DAG ? +1 : -1;
+    eo_hop_pair<0, SF>(a, k0, s, c, acc);
+    eo_hop_pair<1, SF>(a, k0, s, c, acc);
+    eo_hop_pair<2, SF>(a, k0, s, c, acc);
+    eo_hop_pair<3, SF>(a, k0, s, c, acc);
+    if (RESID) {
+      Cx<R> bv[12];
+      load_spinor(a.b, s, V, bv);
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[j] = cx<R>(bv[j].re - acc[j].re, bv[j].im - acc[j].im);
+    }
+    store_spinor(a.out, s, V, acc);
+    if (NORM) n2 = norm2_site(acc);
+  }
+  if (NORM) {
+    double v[1] = {n2}, tot[1];
+    if (grid_reduce<OpSum, 1>(v, a.e.partials, a.e.ticket, tot) && threadIdx.x == 0) *a.e.result = tot[0];
+  }
+}
+
+template <int SP, bool C12, bool DAG, bool SELF, bool RESID>
+static cudaError_t eo_launch_t(const EoCall& c, cudaStream_t st) {
+  EoArgs<SP, C12> a;
+  memcpy(&a.e.g, &c.g, sizeof(Geom));
+  a.e.parity = c.parity;
+  a.e.sign = c.sign;
+  a.e.kappa_dev = c.kappa_dev;
+  a.e.skip = c.skip;
+  a.e.partials = c.red.partials;
+  a.e.ticket = c.red.ticket;
+  a.e.result = c.red.result;
+  a.u.p = reinterpret_cast<decltype(a.u.p)>(c.u.p);
+  a.in.p = reinterpret_cast<decltype(a.in.p)>(c.in.p);
+  a.out.p = reinterpret_cast<decltype(a.out.p)>(c.out.p);
+  a.self.p = reinterpret_cast<decltype(a.self.p)>(c.self.p);
+  a.b.p = reinterpret_cast<decltype(a.b.p)>(c.b.p);
+  if constexpr (SP == P16) {
+    a.in.norm = c.in.norm;
+    a.out.norm = c.out.norm;
+    a.self.norm = c.self.norm;
+    a.b.norm = c.b.norm;
+  }
+  const int grid = grid_for(c.g.V / 2, c.block);
+  if (c.red.result)
+    dslash_eo_kernel<SP, C12, DAG, SELF, RESID, true><<<grid, c.block, 0, st>>>(a);
+  else
+    dslash_eo_kernel<SP, C12, DAG, SELF, RESID, false><<<grid, c.block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int SP, bool C12, bool DAG>
+static cudaError_t eo_launch_d(const EoCall& c, cudaStream_t st) {
+  if (c.use_self) {
+    return c.resid ? eo_launch_t<SP, C12, DAG, true, true>(c, st) : eo_launch_t<SP, C12, DAG, true, false>(c, st);
+  }
+  return c.resid ? eo_launch_t<SP, C12, DAG, false, true>(c, st) : eo_launch_t<SP, C12, DAG, false, false>(c, st);
+}
+
+template <int SP, bool C12>
+static cudaError_t eo_launch_p(const EoCall& c, cudaStream_t st) {
+  return c.dagger ? eo_launch_d<SP, C12, true>(c, st) : eo_launch_d<SP, C12, false>(c, st);
+}
+
+cudaError_t launch_dslash_eo(const EoCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || !c.kappa_dev) return cudaErrorInvalidValue;
+  if (c.in.prec == SP64) {
+    if (c.u.prec != SP64) return cudaErrorInvalidValue;
+    return eo_launch_p<P64, false>(c, st);
+  }
+  if (c.u.prec != SP32) return cudaErrorInvalidValue;
+  if (c.in.prec == SP32) return c.u.c12 ? eo_launch_p<P32, true>(c, st) : eo_launch_p<P32, false>(c, st);
+  if (c.in.prec == SP16) return c.u.c12 ? eo_launch_p<P16, true>(c, st) : eo_launch_p<P16, false>(c, st);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace wdk

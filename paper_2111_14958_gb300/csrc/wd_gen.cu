@@ -185,11 +185,22 @@ __device__ void reunitarise(Cx<double> (&u)[9]) {
 }
 
 // One thread per link i = 4 s + mu: generate, write the device layouts (and the canonical copy).
-__global__ void gen_gauge_kernel(int V, double eps, uint64_t seed, double2* __restrict__ g64, float2* __restrict__ g32,
-                                 float4* __restrict__ g32c, double2* __restrict__ canon) {
+__global__ void gen_gauge_kernel(int V, GeomH eo, int use_eo, double eps, uint64_t seed, double2* __restrict__ g64,
+                                 float2* __restrict__ g32, float4* __restrict__ g32c, double2* __restrict__ canon) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 4 * V) return;
-  const int s = i >> 2, mu = i & 3;
+  const int mu = i & 3;
+  int s = i >> 2;  // canonical site; storage site below
+  if (use_eo) {
+    int r = s;
+    const int x = r % eo.L[0];
+    r /= eo.L[0];
+    const int y = r % eo.L[1];
+    r /= eo.L[1];
+    const int z = r % eo.L[2];
+    const int t = r / eo.L[2];
+    s = ((x + y + z + t) & 1) * (V >> 1) + (x >> 1) + (eo.L[0] >> 1) * (y + eo.L[1] * (z + eo.L[2] * t));
+  }
   double g[18];
   gaussians<18>(seed, (uint64_t)i, 0u, g);
   Cx<double> M[9], Q[9], U[9];
@@ -238,11 +249,14 @@ __global__ void gen_source_kernel(int V, uint64_t seed, double2* __restrict__ ca
   for (int c = 0; c < 12; ++c) canon[(size_t)s * 12 + c] = make_double2(g[c], g[12 + c]);
 }
 
-cudaError_t launch_gen_gauge(int V, double eps, unsigned long long seed, void* g64, void* g32, int c12, double* canon,
-                             cudaStream_t st) {
+cudaError_t launch_gen_gauge(int V, const GeomH* eo, double eps, unsigned long long seed, void* g64, void* g32,
+                             int c12, double* canon, cudaStream_t st) {
   const int block = 128;
   const int grid = (4 * V + block - 1) / block;
-  gen_gauge_kernel<<<grid, block, 0, st>>>(V, eps, (uint64_t)seed, reinterpret_cast<double2*>(g64),
+  GeomH g;
+  memset(&g, 0, sizeof(g));
+  if (eo) g = *eo;
+  gen_gauge_kernel<<<grid, block, 0, st>>>(V, g, eo != nullptr, eps, (uint64_t)seed, reinterpret_cast<double2*>(g64),
                                            c12 ? nullptr : reinterpret_cast<float2*>(g32),
                                            c12 ? reinterpret_cast<float4*>(g32) : nullptr,
                                            reinterpret_cast<double2*>(canon));

@@ -90,34 +90,40 @@ struct DslashCall {
 // Launchers. Each returns cudaGetLastError() after the launch.
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st);
 
+// eo: null for lexicographic storage, else the geometry of a parity-ordered context.
 // canonical complex128 [V][12] -> field; optional |src|^2 into red
-cudaError_t launch_pack(const double* canon, FieldPtr out, int V, Red red, int block, cudaStream_t st);
+cudaError_t launch_pack(const double* canon, FieldPtr out, int V, const GeomH* eo, Red red, int block,
+                        cudaStream_t st);
 // canonical complex64 [V][12] -> P32 field
-cudaError_t launch_pack_c64(const float* canon, FieldPtr out, int V, int block, cudaStream_t st);
+cudaError_t launch_pack_c64(const float* canon, FieldPtr out, int V, const GeomH* eo, int block, cudaStream_t st);
 // field -> canonical complex128
-cudaError_t launch_unpack(FieldPtr in, double* canon, int V, int block, cudaStream_t st);
+cudaError_t launch_unpack(FieldPtr in, double* canon, int V, const GeomH* eo, int block, cudaStream_t st);
 // P32 field -> canonical complex64
-cudaError_t launch_unpack_c64(FieldPtr in, float* canon, int V, int block, cudaStream_t st);
+cudaError_t launch_unpack_c64(FieldPtr in, float* canon, int V, const GeomH* eo, int block, cudaStream_t st);
 // canonical complex128 links [V][4][9] -> gauge field; optional max deviation from SU(3) into red
-cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, Red red, int block, cudaStream_t st);
+cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, const GeomH* eo, Red red, int block,
+                              cudaStream_t st);
 
-// CG pieces (prec = storage precision of all vectors involved)
+// CG pieces (prec = storage precision of all vectors involved); n = sites updated, V = stride of the
+// fields (n = V, or n = V/2 for the even half of a parity-ordered field)
 cudaError_t launch_cg_init(CgScalars* sc, int reset_iter, cudaStream_t st);
 cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond, cudaStream_t st);
 // sms: SM count of the device (sizes the grid of the element-wise FP64/FP32 kernels)
-cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int V, CgScalars* sc, double* partials,
+cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, CgScalars* sc, double* partials,
                                int block, int sms, cudaStream_t st);
-cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int V, CgScalars* sc,
+cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int n, int V, CgScalars* sc,
                                 double* partials, int use_cond, unsigned long long cond, int block, int sms,
                                 cudaStream_t st);
 // Mixed precision (inner W = SP32 or SP16 spinors, x_lo in SP32, outer FP64)
-cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int V, CgScalars* sc,
-                                double* partials, int use_cond, unsigned long long upd, int block, cudaStream_t st);
+cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int n, int V,
+                                CgScalars* sc, double* partials, int use_cond, unsigned long long upd, int block,
+                                cudaStream_t st);
 // skip: pointer to CgScalars::need_update; the kernel runs only when it is non-zero (nullptr = always)
-cudaError_t launch_mp_accumulate(FieldPtr xhi, FieldPtr xlo, int V, const int* skip, int block, cudaStream_t st);
-cudaError_t launch_mp_convert(FieldPtr rhi, FieldPtr rlo, int V, CgScalars* sc, double* partials, int count,
+cudaError_t launch_mp_accumulate(FieldPtr xhi, FieldPtr xlo, int n, int V, const int* skip, int block,
+                                 cudaStream_t st);
+cudaError_t launch_mp_convert(FieldPtr rhi, FieldPtr rlo, int n, int V, CgScalars* sc, double* partials, int count,
                               const int* skip, int block, cudaStream_t st);
-cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int V, CgScalars* sc, double* partials,
+cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int n, int V, CgScalars* sc, double* partials,
                                int use_cond, unsigned long long cond, int block, cudaStream_t st);
 // zero `bytes` (multiple of 16) of device memory with a kernel
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
@@ -178,9 +184,27 @@ cudaError_t launch_mconv(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x, M
 
 // Seeded generation (Philox4x32-10): links into the device layouts (any pointer may be null) and
 // optionally the canonical complex128 copy; Gaussian source in the canonical layout.
-cudaError_t launch_gen_gauge(int V, double eps, unsigned long long seed, void* g64, void* g32, int c12, double* canon,
-                             cudaStream_t st);
+cudaError_t launch_gen_gauge(int V, const GeomH* eo, double eps, unsigned long long seed, void* g64, void* g32,
+                             int c12, double* canon, cudaStream_t st);
 cudaError_t launch_gen_source(int V, unsigned long long seed, double* canon, cudaStream_t st);
+
+// Even-odd half hopping: out = [b -] ([self] + sign * kappa * H in) on the sites of `parity`
+// (fields in parity order, see wd_dslash.cu).
+struct EoCall {
+  GeomH g;
+  GaugePtr u;
+  FieldPtr in, out, self, b;
+  int parity;
+  double sign;
+  int dagger;
+  int use_self;
+  int resid;
+  const double* kappa_dev;
+  const int* skip;
+  Red red;
+  int block;
+};
+cudaError_t launch_dslash_eo(const EoCall& c, cudaStream_t st);
 
 // grid size used by a launcher for V sites at a block size
 inline int grid_for(int V, int block) { return (V + block - 1) / block; }

@@ -43,12 +43,14 @@ long long volume_of(const int d[4]) { return (long long)d[0] * d[1] * d[2] * d[3
 // canonical source and solution buffers of the slot).
 size_t request_bytes(const int d[4], int precision) {
   const size_t V = (size_t)volume_of(d);
+  const size_t extra = (precision & WD_EVEN_ODD) ? V * 192 * 2 : 0;  // odd-site temporaries
+  precision &= ~WD_EVEN_ODD;
   const size_t f64 = V * 192, f32 = V * 96, f16 = V * 52;
   switch (precision) {
-    case WD_PREC_F64: return V * 576 + 9 * f64 + 2 * f64 + (V / 32 + 64) * 8 * 12;
-    case WD_PREC_F32: return V * 288 + 6 * f32 + 2 * f64 + V * 12;
-    case WD_PREC_MIXED_F32: return V * 576 + V * 192 + 5 * f32 + 3 * f64 + 2 * f64 + V * 12;
-    case WD_PREC_MIXED_F16: return V * 576 + V * 192 + 4 * f16 + f32 + 3 * f64 + 2 * f64 + V * 12;
+    case WD_PREC_F64: return extra + V * 576 + 9 * f64 + 2 * f64 + (V / 32 + 64) * 8 * 12;
+    case WD_PREC_F32: return extra + V * 288 + 6 * f32 + 2 * f64 + V * 12;
+    case WD_PREC_MIXED_F32: return extra + V * 576 + V * 192 + 5 * f32 + 3 * f64 + 2 * f64 + V * 12;
+    case WD_PREC_MIXED_F16: return extra + V * 576 + V * 192 + 4 * f16 + f32 + 3 * f64 + 2 * f64 + V * 12;
   }
   return 0;
 }
@@ -150,7 +152,7 @@ void run_job(Slot* s, Job* j) {
   Resident* e = nullptr;
   wd_status st = prepare(s, r, &e);
   const size_t V = (size_t)volume_of(r.dims);
-  if (st == WD_OK) st = wd_generate_gauge(e->ctx, r.eps, r.gauge_seed, r.precision == WD_PREC_F64 ? 0 : 1, nullptr);
+  if (st == WD_OK) st = wd_generate_gauge(e->ctx, r.eps, r.gauge_seed, (r.precision & ~WD_EVEN_ODD) == WD_PREC_F64 ? 0 : 1, nullptr);
   if (st == WD_OK) {
     if (r.src_host) {
       if (cudaMemcpyAsync(e->src, r.src_host, V * 192, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) st = WD_ECUDA;

@@ -40,6 +40,7 @@ WD_PREC_F64 = 64
 WD_PREC_F32 = 32
 WD_PREC_MIXED_F32 = 6432
 WD_PREC_MIXED_F16 = 6416
+WD_EVEN_ODD = 0x10000
 
 WD_OPT_RELIABLE_DELTA = 1
 WD_OPT_USE_GRAPH = 2
