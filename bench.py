@@ -264,6 +264,8 @@ def run_native(args, rank, world):
         out["dslash_sweep"] = _sweep(wd, dev, stream, args.sweep)
         out["mixed_32x64"] = _mixed_32x64(wd, dev, stream)
         out["multi_rhs_24x48"] = _multi_24x48(wd, dev, stream)
+        out["even_odd"] = _even_odd(wd, dev, stream)
+        out["paper_coo_14x4"] = _paper_coo(wd, dev, stream)
         out["serving"] = _serving(wd)
         out["cpu_baseline"] = _cpu_baseline(iters)
     op.close()
@@ -437,6 +439,55 @@ def _multi_24x48(wd, dev, stream):
     out["plain_f64_one_rhs"] = rec
     out["plain_f64_x12_ms"] = 12 * rec["ms"]
     ref.close()
+    return out
+
+
+def _paper_coo(wd, dev, stream):
+    """The paper's COO SpMV (Sec. 2) on this GPU at its largest lattice, 14^4, FP64."""
+    import torch
+    op = wd.WilsonDirac(DIMS, KAPPA, BC, wd.WD_PREC_F64, stream=stream)
+    U = op.generate_gauge(EPS, GAUGE_SEED, return_field=True)
+    row, col, val = wd.wd_coo_build(op.ctx, U)
+    psi = op.generate_source(SOURCE_SEED)
+    out = torch.empty_like(psi)
+    for _ in range(3):
+        wd.wd_coo_spmv(op.ctx, row, col, val, psi, out)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    a.record(stream)
+    for _ in range(reps):
+        wd.wd_coo_spmv(op.ctx, row, col, val, psi, out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    nnz = row.numel()
+    V = int(np.prod(DIMS))
+    stencil_ms = op.time_dslash(False, 100)
+    op.close()
+    return {"workload": "14^4 FP64, D in COO (49 non-zeros per row), one thread per non-zero, atomic adds",
+            "nnz": nnz, "spmv_ms": ms, "gflops_8_per_nonzero": 8 * nnz / (ms * 1e-3) / 1e9,
+            "gflops_1320_per_site": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e9,
+            "stencil_dslash_ms": stencil_ms, "stencil_speedup": ms / stencil_ms,
+            "paper_a100_gflops": 65}
+
+
+def _even_odd(wd, dev, stream):
+    """Even-odd (Schur) preconditioned solves against the unpreconditioned ones."""
+    import torch
+    out = {}
+    for name, dims, kappa, prec in (("14x4_f64", DIMS, KAPPA, wd.WD_PREC_F64),
+                                    ("14x4_mixed_f32", DIMS, KAPPA, wd.WD_PREC_MIXED_F32),
+                                    ("32x64_mixed_f32", (32, 32, 32, 64), 0.124, wd.WD_PREC_MIXED_F32)):
+        rec = {}
+        for tag, flag in (("plain", 0), ("even_odd", wd.WD_EVEN_ODD)):
+            op = wd.WilsonDirac(dims, kappa, BC, prec | flag, stream=stream)
+            op.generate_gauge(EPS, GAUGE_SEED, compress12=prec != wd.WD_PREC_F64)
+            eta = op.generate_source(SOURCE_SEED)
+            _, r = _timed_solve(op, wd, eta, TOL, repeats=2)
+            rec[tag] = r
+            op.close()
+        rec["speedup"] = rec["plain"]["ms"] / rec["even_odd"]["ms"]
+        out[name] = rec
     return out
 
 

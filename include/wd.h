@@ -258,6 +258,21 @@ wd_status wd_server_poll(wd_server* srv, long long id, wd_result* out, int* done
 wd_status wd_server_get_stats(wd_server* srv, wd_server_stats* out);
 void wd_server_destroy(wd_server* srv);
 
+/*
+ * The paper's own method, for comparison on the same GPU (Sec. 2): D in coordinate format and
+ * its sparse matrix-vector product. wd_coo_build writes the 49 * 12 * V non-zeros of D (the
+ * context's kappa and boundary; U = device canonical complex128 links) into device arrays Row,
+ * Col (int32, indices of the canonical vector 12*site + 3*spin + colour) and Val (complex128),
+ * ordered by row; capacity = their length in entries, *nnz receives 49 * 12 * V. wd_coo_spmv
+ * computes out[Row[k]] += Val[k] * in[Col[k]] over k < nnz, one thread per non-zero with atomic
+ * accumulation into the zeroed `out` (canonical complex128; summation order is not fixed).
+ * Errors: WD_EINVAL, WD_ECUDA.
+ */
+wd_status wd_coo_build(wd_ctx* ctx, const double* U, int* row, int* col, double* val, long long capacity,
+                       long long* nnz);
+wd_status wd_coo_spmv(wd_ctx* ctx, long long nnz, const int* row, const int* col, const double* val,
+                      const double* in, double* out);
+
 /* Set an option (WD_OPT_*). Returns WD_EINVAL for an unknown key or a value out of range. */
 wd_status wd_set_option(wd_ctx* ctx, int key, double value);
 

@@ -1449,4 +1449,28 @@ wd_status wd_set_kappa(wd_ctx* c, double kappa) {
   return WD_OK;
 }
 
+wd_status wd_coo_build(wd_ctx* c, const double* U, int* row, int* col, double* val, long long capacity,
+                       long long* nnz) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!U || !row || !col || !val || !nnz) return fail(WD_EINVAL, "null argument");
+  const long long need = 49LL * 12LL * c->V;
+  *nnz = need;
+  if (capacity < need) return fail(WD_EINVAL, "capacity below 49 * 12 * V entries");
+  if (12LL * c->V > 0x7fffffffLL) return fail(WD_EINVAL, "volume too large for 32-bit COO indices");
+  WD_CUDA(launch_coo_build(c->geom, U, c->kappa, row, col, val, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return WD_OK;
+}
+
+wd_status wd_coo_spmv(wd_ctx* c, long long nnz, const int* row, const int* col, const double* val, const double* in,
+                      double* out) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!row || !col || !val || !in || !out || in == out || nnz < 0) return fail(WD_EINVAL, "bad argument");
+  WD_CUDA(launch_coo_spmv(nnz, row, col, val, in, out, 12LL * c->V, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return WD_OK;
+}
+
 }  // extern "C"

@@ -206,6 +206,12 @@ struct EoCall {
 };
 cudaError_t launch_dslash_eo(const EoCall& c, cudaStream_t st);
 
+// The paper's COO representation of D (49 non-zeros per row) and its atomic SpMV (wd_coo.cu).
+cudaError_t launch_coo_build(const GeomH& g, const double* U, double kappa, int* row, int* col, double* val,
+                             cudaStream_t st);
+cudaError_t launch_coo_spmv(long long nnz, const int* row, const int* col, const double* val, const double* in,
+                            double* out, long long nrows, cudaStream_t st);
+
 // grid size used by a launcher for V sites at a block size
 inline int grid_for(int V, int block) { return (V + block - 1) / block; }
 

@@ -105,6 +105,8 @@ _sig = {
     "wd_get_multi_stats": (_I, [_P, ctypes.POINTER(WdMultiStats)]),
     "wd_generate_gauge": (_I, [_P, _D, ctypes.c_ulonglong, _I, _P]),
     "wd_generate_source": (_I, [_P, ctypes.c_ulonglong, _P]),
+    "wd_coo_build": (_I, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+    "wd_coo_spmv": (_I, [_P, ctypes.c_longlong, _P, _P, _P, _P, _P]),
     "wd_dslash_noalloc": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _P, _P, _P, _I, _P, _P]),
     "wd_server_create": (_I, [_D, _I, ctypes.POINTER(_P)]),
     "wd_server_submit": (_I, [_P, ctypes.POINTER(WdRequest), ctypes.POINTER(ctypes.c_longlong)]),
@@ -209,6 +211,26 @@ def wd_generate_source(ctx, seed: int, out: torch.Tensor) -> None:
     if out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous():
         raise ValueError("out must be a contiguous complex128 CUDA tensor")
     _check(_lib.wd_generate_source(_P(ctx), int(seed) & 0xFFFFFFFFFFFFFFFF, _P(_ptr(out))), "wd_generate_source")
+
+
+def wd_coo_build(ctx, U: torch.Tensor):
+    """D in the paper's coordinate format: returns (row int32, col int32, val complex128) device tensors."""
+    if U.dtype != torch.complex128 or not U.is_cuda or not U.is_contiguous():
+        raise ValueError("U must be a contiguous complex128 CUDA tensor")
+    V = U.numel() // 36
+    n = 49 * 12 * V
+    row = torch.empty(n, dtype=torch.int32, device=U.device)
+    col = torch.empty(n, dtype=torch.int32, device=U.device)
+    val = torch.empty(n, dtype=torch.complex128, device=U.device)
+    nnz = ctypes.c_longlong()
+    _check(_lib.wd_coo_build(_P(ctx), _P(_ptr(U)), _P(_ptr(row)), _P(_ptr(col)), _P(_ptr(val)), n,
+                             ctypes.byref(nnz)), "wd_coo_build")
+    return row, col, val
+
+
+def wd_coo_spmv(ctx, row, col, val, inp: torch.Tensor, out: torch.Tensor) -> None:
+    _check(_lib.wd_coo_spmv(_P(ctx), row.numel(), _P(_ptr(row)), _P(_ptr(col)), _P(_ptr(val)), _P(_ptr(inp)),
+                            _P(_ptr(out))), "wd_coo_spmv")
 
 
 def _check_multi(t: torch.Tensor, name: str) -> int:
