@@ -75,7 +75,14 @@ enum {
   WD_OPT_MAX_RESTARTS = 5,   /* max restarts from the true residual (default 5)                  */
   WD_OPT_MULTI_GROUP = 6,    /* multi-RHS: right-hand sides sharing one link load (K, divides
                                 nrhs); 0 (default) = chosen by the autotuner                     */
-  WD_OPT_MULTI_SITES = 7     /* multi-RHS: sites per thread block (K * sites <= 256); 0 = tuned   */
+  WD_OPT_MULTI_SITES = 7,    /* multi-RHS: sites per thread block (K * sites <= 256); 0 = tuned   */
+  WD_OPT_DF_UPDATES = 8,     /* mixed precision: 1 (default) computes the reliable-update residual
+                                and accumulates the solution in double-float arithmetic (pairs of
+                                FP32, ~48 bits, on the FP32 pipes, ~2^-47 relative error per
+                                operation); 0 uses native FP64. The final true residual is always
+                                recomputed in native FP64. Changing it needs a gauge reload.     */
+  WD_OPT_APPLY_DF = 9        /* mixed precision: 1 makes wd_apply use the double-float operator
+                                (complex128 in and out), to check it; 0 (default) native FP64     */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

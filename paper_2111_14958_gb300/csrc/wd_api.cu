@@ -60,6 +60,11 @@ struct wd_ctx {
   int eo;     // fields stored in parity order; CG on the even-site Schur complement
   int nsolve; // sites the Krylov vectors span: V, or V/2 (even half) for even-odd
   FieldPtr t, t64;  // even-odd: odd-site temporaries of the two-step operator
+  // mixed precision: reliable updates in double-float (FP32-pipe) arithmetic
+  int use_df;
+  int apply_df;  // wd_apply on a mixed context uses the double-float operator (for checks)
+  FieldPtr xdf, rdf, etadf, tdf;
+  void* gauge_df;
   FieldPtr x, r, p, q, s, eta;  // plain modes: all in wprec; mixed: r, p, q, s in wprec, x = x_lo (SP32)
   // FP64 operator and outer vectors (FP64 context and mixed modes)
   FieldPtr x64, r64, eta64;
@@ -103,7 +108,7 @@ struct wd_ctx {
   cudaGraphExec_t mexec;
   bool mgraph_ready;
   int force_mK, force_mspb;   // launch shape fixed by options (0 = autotuned)
-  int tuned_block[3];         // autotuned single-RHS dslash block size per storage precision
+  int tuned_block[4];         // autotuned single-RHS dslash block size per storage precision
   wd_multi_stats mstats;
 };
 
@@ -114,6 +119,7 @@ size_t spinor_bytes(int prec, int V) {
     case SP64: return (size_t)V * 12 * 16;
     case SP32: return (size_t)V * 12 * 8;
     case SP16: return (size_t)V * 12 * 4;
+    case SPDF: return (size_t)V * 12 * 16;
   }
   return 0;
 }
@@ -164,13 +170,17 @@ Red no_red() {
 
 int dslash_block(const wd_ctx* c, int prec) {
   if (c->block_dslash > 0) return c->block_dslash;
-  if (prec >= 0 && prec < 3 && c->tuned_block[prec] > 0) return c->tuned_block[prec];
+  if (prec >= 0 && prec < 4 && c->tuned_block[prec] > 0) return c->tuned_block[prec];
   return 256;
 }
 
 GaugePtr gauge_for(const wd_ctx* c, int prec) {
   GaugePtr g;
-  if (prec == SP64) {
+  if (prec == SPDF) {
+    g.p = c->gauge_df;
+    g.prec = SPDF;
+    g.c12 = 0;
+  } else if (prec == SP64) {
     g.p = c->gauge64;
     g.prec = SP64;
     g.c12 = 0;
@@ -235,7 +245,7 @@ cudaError_t op(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, FieldP
                const int* skip, cudaStream_t st) {
   if (!c->eo) return dslash(c, in, out, dagger, epi, b, norm_dst, slot, skip, st);
   cudaError_t e;
-  FieldPtr t = in.prec == SP64 ? c->t64 : c->t;
+  FieldPtr t = in.prec == SP64 ? c->t64 : (in.prec == SPDF ? c->tdf : c->t);
   if ((e = eo_half(c, in, t, 1, +1.0, dagger, nullptr, nullptr, nullptr, 0, skip, st)) != cudaSuccess) return e;
   return eo_half(c, t, out, 0, -1.0, dagger, &in, epi == EPI_RESID ? &b : nullptr, norm_dst, slot, skip, st);
 }
@@ -298,31 +308,43 @@ cudaError_t plain_epilogue(wd_ctx* c, cudaStream_t st) {
 
 // ---------------------------------------------------------------- mixed precision CG
 
+// Reliable-update residual r_hi = eta - A x_hi, in double-float (FP32 pipes) or in FP64.
+cudaError_t mixed_residual(wd_ctx* c, const int* skip, cudaStream_t st) {
+  if (c->use_df) return op(c, c->xdf, c->rdf, 0, EPI_RESID, c->etadf, &c->sc->rr_true, TK_DSLASH_C, skip, st);
+  return op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &c->sc->rr_true, TK_DSLASH_C, skip, st);
+}
+
+cudaError_t mixed_accumulate(wd_ctx* c, const int* skip, cudaStream_t st) {
+  if (c->use_df) return launch_mp_accumulate_df(c->xdf, c->x, c->nsolve, c->V, skip, c->block_blas, st);
+  return launch_mp_accumulate(c->x64, c->x, c->nsolve, c->V, skip, c->block_blas, st);
+}
+
+cudaError_t mixed_convert(wd_ctx* c, int count, const int* skip, cudaStream_t st) {
+  if (c->use_df)
+    return launch_mp_convert_df(c->rdf, c->r, c->nsolve, c->V, c->sc, c->partials, count, skip, c->block_blas, st);
+  return launch_mp_convert(c->r64, c->r, c->nsolve, c->V, c->sc, c->partials, count, skip, c->block_blas, st);
+}
+
 cudaError_t mixed_prologue(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
   cudaError_t e;
   CgScalars* sc = c->sc;
-  const int bb = c->block_blas;
   if ((e = launch_cg_init(sc, 0, st)) != cudaSuccess) return e;
-  // r_hi = eta - D x_hi (FP64); x_lo = 0; r_lo = r_hi
-  if ((e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, nullptr, st)) != cudaSuccess)
-    return e;
+  // r_hi = eta - A x_hi; x_lo = 0; r_lo = r_hi
+  if ((e = mixed_residual(c, nullptr, st)) != cudaSuccess) return e;
   if ((e = launch_zero(c->x.p, spinor_bytes(c->x.prec, c->V), st)) != cudaSuccess) return e;
-  if ((e = launch_mp_convert(c->r64, c->r, c->nsolve, c->V, sc, c->partials, 0, nullptr, bb, st)) != cudaSuccess) return e;
-  // p = D^dag r_lo
+  if ((e = mixed_convert(c, 0, nullptr, st)) != cudaSuccess) return e;
+  // p = A^dag r_lo
   if ((e = op(c, c->r, c->p, 1, EPI_PLAIN, none_field(), &sc->gamma, TK_DSLASH_B, nullptr, st)) != cudaSuccess)
     return e;
   return launch_cg_check(sc, use_cond, cond, st);
 }
 
-// reliable update: x_hi += x_lo; x_lo = 0; r_hi = eta - D x_hi (FP64); r_lo = r_hi
+// reliable update: x_hi += x_lo; x_lo = 0; r_hi = eta - A x_hi; r_lo = r_hi
 cudaError_t mixed_update(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
-  CgScalars* sc = c->sc;
-  const int bb = c->block_blas;
-  if ((e = launch_mp_accumulate(c->x64, c->x, c->nsolve, c->V, nullptr, bb, st)) != cudaSuccess) return e;
-  if ((e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, nullptr, st)) != cudaSuccess)
-    return e;
-  return launch_mp_convert(c->r64, c->r, c->nsolve, c->V, sc, c->partials, 1, nullptr, bb, st);
+  if ((e = mixed_accumulate(c, nullptr, st)) != cudaSuccess) return e;
+  if ((e = mixed_residual(c, nullptr, st)) != cudaSuccess) return e;
+  return mixed_convert(c, 1, nullptr, st);
 }
 
 cudaError_t mixed_body_a(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long upd) {
@@ -330,7 +352,8 @@ cudaError_t mixed_body_a(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long
   CgScalars* sc = c->sc;
   if ((e = op(c, c->p, c->q, 0, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
     return e;
-  return launch_mp_update_rx(c->wprec, c->r, c->q, c->p, c->x, c->nsolve, c->V, sc, c->partials, use_cond, upd, c->block_blas, st);
+  return launch_mp_update_rx(c->wprec, c->r, c->q, c->p, c->x, c->nsolve, c->V, sc, c->partials, use_cond, upd,
+                             c->block_blas, st);
 }
 
 cudaError_t mixed_body_b(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
@@ -342,9 +365,13 @@ cudaError_t mixed_body_b(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long
   return launch_mp_update_p(c->wprec, c->p, c->s, c->nsolve, c->V, sc, c->partials, use_cond, cond, c->block_blas, st);
 }
 
+// Fold the last increment into the solution and recompute the true residual in native FP64
+// (double-float solutions are converted first), then rebuild the odd sites for even-odd.
 cudaError_t mixed_epilogue(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
-  if ((e = launch_mp_accumulate(c->x64, c->x, c->nsolve, c->V, nullptr, c->block_blas, st)) != cudaSuccess) return e;
+  if ((e = mixed_accumulate(c, nullptr, st)) != cudaSuccess) return e;
+  if (c->use_df && (e = launch_convert_f64_df(c->xdf, c->x64, c->V, c->V, 0, c->block_blas, st)) != cudaSuccess)
+    return e;
   e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &c->sc->rr_true, TK_DSLASH_C, nullptr, st);
   if (e != cudaSuccess || !c->eo) return e;
   return eo_half(c, c->x64, c->x64, 1, +1.0, 0, &c->eta64, nullptr, nullptr, 0, nullptr, st);
@@ -354,12 +381,9 @@ cudaError_t mixed_epilogue(wd_ctx* c, cudaStream_t st) {
 cudaError_t mixed_update_flagged(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
   CgScalars* sc = c->sc;
-  const int bb = c->block_blas;
-  if ((e = launch_mp_accumulate(c->x64, c->x, c->nsolve, c->V, &sc->need_update, bb, st)) != cudaSuccess) return e;
-  if ((e = op(c, c->x64, c->r64, 0, EPI_RESID, c->eta64, &sc->rr_true, TK_DSLASH_C, &sc->no_update, st)) !=
-      cudaSuccess)
-    return e;
-  return launch_mp_convert(c->r64, c->r, c->nsolve, c->V, sc, c->partials, 1, &sc->need_update, bb, st);
+  if ((e = mixed_accumulate(c, &sc->need_update, st)) != cudaSuccess) return e;
+  if ((e = mixed_residual(c, &sc->no_update, st)) != cudaSuccess) return e;
+  return mixed_convert(c, 1, &sc->need_update, st);
 }
 
 // ---------------------------------------------------------------- graph construction
@@ -516,11 +540,11 @@ __global__ void set_params_kernel(CgScalars* sc, double tol2, double delta2, int
 // size is timed per context and precision on first use (CUDA events, the context's own fields).
 wd_status autotune_single(wd_ctx* c) {
   if (c->block_dslash > 0) return WD_OK;
-  const int precs[2] = {c->wprec, (is_mixed(c->precision) ? SP64 : -1)};
+  const int precs[3] = {c->wprec, (is_mixed(c->precision) ? SP64 : -1), (c->use_df ? SPDF : -1)};
   for (int prec : precs) {
     if (prec < 0 || c->tuned_block[prec] > 0) continue;
-    FieldPtr in = prec == c->wprec ? c->p : c->x64;
-    FieldPtr out = prec == c->wprec ? c->q : c->r64;
+    FieldPtr in = prec == c->wprec ? c->p : (prec == SPDF ? c->xdf : c->x64);
+    FieldPtr out = prec == c->wprec ? c->q : (prec == SPDF ? c->rdf : c->r64);
     const int cands[] = {64, 128, 256};
     float best = 1e30f;
     int best_b = 256;
@@ -892,8 +916,16 @@ wd_status ensure_gauge_buffers(wd_ctx* c, int compress12, bool* need64, bool* ne
     c->mexec = nullptr;
     c->mgraph = nullptr;
     c->mgraph_ready = false;
-    c->tuned_block[0] = c->tuned_block[1] = c->tuned_block[2] = 0;
+    c->tuned_block[0] = c->tuned_block[1] = c->tuned_block[2] = c->tuned_block[3] = 0;
     c->mK = c->mK64 = 0;
+  }
+  if (is_mixed(c->precision) && c->use_df && !c->gauge_df) {
+    destroy_graph(c);
+    if (cudaMalloc(&c->gauge_df, (size_t)c->V * 4 * 9 * 16) != cudaSuccess) {
+      cudaGetLastError();
+      c->gauge_df = nullptr;
+      return fail(WD_ENOMEM, "cudaMalloc of the double-float gauge field failed");
+    }
   }
   if (*need64 && !c->gauge64) {
     if (cudaMalloc(&c->gauge64, (size_t)c->V * 4 * 9 * 16) != cudaSuccess) {
@@ -1020,6 +1052,13 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
     if ((st = alloc_field(c, &c->r64, SP64)) != WD_OK) return bail(st);
     if ((st = alloc_field(c, &c->eta64, SP64)) != WD_OK) return bail(st);
   }
+  if (mixed) {
+    c->use_df = 1;
+    if ((st = alloc_field(c, &c->xdf, SPDF)) != WD_OK) return bail(st);
+    if ((st = alloc_field(c, &c->rdf, SPDF)) != WD_OK) return bail(st);
+    if ((st = alloc_field(c, &c->etadf, SPDF)) != WD_OK) return bail(st);
+    if (eo && (st = alloc_field(c, &c->tdf, SPDF)) != WD_OK) return bail(st);
+  }
   if (eo) {
     if ((st = alloc_field(c, &c->t, wprec)) != WD_OK) return bail(st);
     if (mixed && (st = alloc_field(c, &c->t64, SP64)) != WD_OK) return bail(st);
@@ -1062,6 +1101,11 @@ void wd_destroy(wd_ctx* c) {
   if (c->t64.p == c->t.p) c->t64.p = nullptr;
   free_field(&c->t);
   free_field(&c->t64);
+  free_field(&c->xdf);
+  free_field(&c->rdf);
+  free_field(&c->etadf);
+  free_field(&c->tdf);
+  if (c->gauge_df) cudaFree(c->gauge_df);
   if (c->gauge64) cudaFree(c->gauge64);
   if (c->gauge32) cudaFree(c->gauge32);
   if (c->staging) cudaFree(c->staging);
@@ -1094,7 +1138,7 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
         return fail(WD_EINVAL, "block size must be 0 or a multiple of 32 in [32, 256] (dslash) / [32, 1024] (BLAS)");
       if (key == WD_OPT_BLOCK_DSLASH) {
         c->block_dslash = b;
-        c->tuned_block[0] = c->tuned_block[1] = c->tuned_block[2] = 0;
+        c->tuned_block[0] = c->tuned_block[1] = c->tuned_block[2] = c->tuned_block[3] = 0;
       } else
         c->block_blas = b ? b : 256;
       destroy_graph(c);  // launch shapes are baked into the graph
@@ -1116,6 +1160,21 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       c->mgraph_ready = false;
       return WD_OK;
     }
+    case WD_OPT_DF_UPDATES: {
+      if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float updates apply to mixed-precision contexts");
+      const int v = value != 0.0;
+      if (v && (!c->xdf.p || !c->rdf.p || !c->etadf.p)) return fail(WD_EINVAL, "context has no double-float workspace");
+      if (v != c->use_df) {
+        c->use_df = v;
+        destroy_graph(c);
+        if (v && c->gauge_loaded && !c->gauge_df) c->gauge_loaded = false;  // needs a reload
+      }
+      return WD_OK;
+    }
+    case WD_OPT_APPLY_DF:
+      if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float operator exists on mixed-precision contexts");
+      c->apply_df = value != 0.0;
+      return WD_OK;
     case WD_OPT_MAX_RESTARTS:
       if (!(value >= 0 && value <= 100)) return fail(WD_EINVAL, "max restarts must be in [0, 100]");
       c->max_restarts = (int)value;
@@ -1158,6 +1217,14 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
     if (launch_gauge_load(src, g, c->V, eo_geom(c), red_to(c, TK_GAUGE, &c->sc->max_dev), gb, c->stream) != cudaSuccess)
       return fail(WD_ECUDA, "gauge load kernel failed to launch");
   }
+  if (c->gauge_df) {
+    GaugePtr g;
+    g.p = c->gauge_df;
+    g.prec = SPDF;
+    g.c12 = 0;
+    if (launch_gauge_load(src, g, c->V, eo_geom(c), no_red(), gb, c->stream) != cudaSuccess)
+      return fail(WD_ECUDA, "gauge load kernel failed to launch");
+  }
   if (need32) {
     GaugePtr g;
     g.p = c->gauge32;
@@ -1195,7 +1262,13 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
     FieldPtr a = c->wprec == SP64 ? c->q : c->x64;
     FieldPtr b = c->wprec == SP64 ? c->s : c->r64;
     WD_CUDA(launch_pack((const double*)in, a, c->V, eo_geom(c), no_red(), bb, c->stream));
-    WD_CUDA(full_D(c, a, b, dagger ? 1 : 0, c->stream));
+    if (c->apply_df && c->gauge_df) {
+      WD_CUDA(launch_convert_f64_df(a, c->xdf, c->V, c->V, 1, bb, c->stream));
+      WD_CUDA(full_D(c, c->xdf, c->rdf, dagger ? 1 : 0, c->stream));
+      WD_CUDA(launch_convert_f64_df(c->rdf, b, c->V, c->V, 0, bb, c->stream));
+    } else {
+      WD_CUDA(full_D(c, a, b, dagger ? 1 : 0, c->stream));
+    }
     WD_CUDA(launch_unpack(b, (double*)out, c->V, eo_geom(c), bb, c->stream));
   }
   WD_CUDA(cudaStreamSynchronize(c->stream));
@@ -1224,6 +1297,10 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
     // Schur source on the even sites, in place: b_e = eta_e + kappa H_eo eta_o (eta_o is kept for
     // the reconstruction x_o = eta_o + kappa H_oe x_e)
     WD_CUDA(eo_half(c, eta, eta, 0, +1.0, 0, &eta, nullptr, nullptr, 0, nullptr, c->stream));
+  }
+  if (mixed && c->use_df) {
+    WD_CUDA(launch_convert_f64_df(c->eta64, c->etadf, c->V, c->V, 1, bb, c->stream));
+    WD_CUDA(launch_convert_f64_df(c->x64, c->xdf, c->V, c->V, 1, bb, c->stream));
   }
   if ((st = autotune_single(c)) != WD_OK) return st;
   if (c->use_graph) {
@@ -1421,7 +1498,7 @@ wd_status wd_generate_gauge(wd_ctx* c, double eps, unsigned long long seed, int 
   bool need64 = false, need32 = false;
   int c12 = 0;
   if ((st = ensure_gauge_buffers(c, compress12, &need64, &need32, &c12)) != WD_OK) return st;
-  WD_CUDA(launch_gen_gauge(c->V, eo_geom(c), eps, seed, need64 ? c->gauge64 : nullptr, need32 ? c->gauge32 : nullptr, c12, U_out,
+  WD_CUDA(launch_gen_gauge(c->V, eo_geom(c), eps, seed, need64 ? c->gauge64 : nullptr, need32 ? c->gauge32 : nullptr, c12, U_out, c->gauge_df,
                            c->stream));
   WD_CUDA(cudaStreamSynchronize(c->stream));
   c->gauge_loaded = true;

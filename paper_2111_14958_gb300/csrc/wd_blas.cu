@@ -117,6 +117,14 @@ SpinorRef<P16> view<P16>(FieldPtr f) {
   return r;
 }
 
+// double-float fields need the stride V to find the lo half
+static SpinorRef<PDF> view_df(FieldPtr f, int V) {
+  SpinorRef<PDF> r;
+  r.hi = reinterpret_cast<float4*>(f.p);
+  r.lo = reinterpret_cast<float4*>(f.p) + (size_t)6 * V;
+  return r;
+}
+
 static SiteMap site_map(const GeomH* eo) {
   SiteMap m;
   m.eo = eo != nullptr;
@@ -224,6 +232,15 @@ __global__ void gauge_load_kernel(const double2* __restrict__ canon, void* out, 
       double2* o = reinterpret_cast<double2*>(out) + (size_t)mu * 9 * V + s;
 #pragma unroll
       for (int k = 0; k < 9; ++k) o[(size_t)k * V] = make_double2(u[k].re, u[k].im);
+    } else if (GP == PDF) {
+      float2* hi = reinterpret_cast<float2*>(out) + (size_t)mu * 9 * V + s;
+      float2* lo = hi + (size_t)36 * V;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float hr = __double2float_rn(u[k].re), hm = __double2float_rn(u[k].im);
+        hi[(size_t)k * V] = make_float2(hr, hm);
+        lo[(size_t)k * V] = make_float2(__double2float_rn(u[k].re - (double)hr), __double2float_rn(u[k].im - (double)hm));
+      }
     } else if (!C12) {
       float2* o = reinterpret_cast<float2*>(out) + (size_t)mu * 9 * V + s;
 #pragma unroll
@@ -258,6 +275,8 @@ cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, const Ge
   } while (0)
   if (out.prec == SP64)
     WD_GL(P64, false);
+  else if (out.prec == SPDF)
+    WD_GL(PDF, false);
   else if (out.c12)
     WD_GL(P32, true);
   else
@@ -640,6 +659,115 @@ cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int n, int V, 
       break;
     case SP16:
       mp_update_p_kernel<P16><<<grid, block, 0, st>>>(view<P16>(p), view<P16>(s), n, V, sc, partials, use_cond, h);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- double-float helpers
+
+// FP64 -> double-float (hi = rn(x), lo = rn(x - hi)) and back (hi + lo in FP64)
+__global__ void f64_to_df_kernel(SpinorRef<P64> in, SpinorRef<PDF> out, int n, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  Cx<double> v[12];
+  load_spinor(in, s, V, v);
+  Cx<dfloat> w[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) w[c] = cx(dfloat(v[c].re), dfloat(v[c].im));
+  store_spinor(out, s, V, w);
+}
+
+__global__ void df_to_f64_kernel(SpinorRef<PDF> in, SpinorRef<P64> out, int n, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  Cx<dfloat> w[12];
+  load_spinor(in, s, V, w);
+  Cx<double> v[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) v[c] = cx((double)w[c].re, (double)w[c].im);
+  store_spinor(out, s, V, v);
+}
+
+// x_hi += x_lo in double-float (TwoSum of the hi parts), x_lo = 0
+__global__ void mp_accumulate_df_kernel(SpinorRef<PDF> xhi, SpinorRef<P32> xlo, int n, int V, const int* skip) {
+  if (skip != nullptr && *skip == 0) return;  // runs only when an update is pending
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  Cx<dfloat> xh[12];
+  Cx<float> xl[12];
+  load_spinor(xhi, s, V, xh);
+  load_spinor(xlo, s, V, xl);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    xh[c].re = xh[c].re + dfloat(xl[c].re, 0.f);
+    xh[c].im = xh[c].im + dfloat(xl[c].im, 0.f);
+    xl[c] = cx(0.f, 0.f);
+  }
+  store_spinor(xhi, s, V, xh);
+  store_spinor(xlo, s, V, xl);
+}
+
+// r_lo = r_hi from a double-float residual (its hi part), then the same bookkeeping as
+// mp_convert_kernel
+template <int SPW>
+__global__ void mp_convert_df_kernel(SpinorRef<PDF> rhi, SpinorRef<SPW> rlo, int n, int V, CgScalars* sc,
+                                     double* partials, int count, const int* skip) {
+  if (skip != nullptr && *skip == 0) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) {
+    Cx<dfloat> h[12];
+    Cx<float> l[12];
+    load_spinor(rhi, s, V, h);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) l[c] = cx(h[c].re.hi, h[c].im.hi);
+    store_spinor(rlo, s, V, l);
+  }
+  double v[1] = {0.0}, tot[1];
+  if (grid_reduce<OpSum, 1>(v, partials, &sc->ticket[TK_UPD_REL], tot) && threadIdx.x == 0) {
+    const double rr = sc->rr_true;
+    sc->rr = rr;
+    sc->rr_ref = rr;
+    sc->need_update = 0;
+    sc->no_update = 1;
+    if (count) sc->updates += 1;
+    if (!isfinite(rr))
+      sc->status = ST_BREAKDOWN;
+    else if (rr <= sc->tol2 * sc->eta2)
+      sc->status = ST_CONVERGED;
+  }
+}
+
+cudaError_t launch_convert_f64_df(FieldPtr in, FieldPtr out, int n, int V, int to_df, int block, cudaStream_t st) {
+  const int grid = grid_for(n, block);
+  if (to_df) {
+    if (in.prec != SP64 || out.prec != SPDF) return cudaErrorInvalidValue;
+    f64_to_df_kernel<<<grid, block, 0, st>>>(view<P64>(in), view_df(out, V), n, V);
+  } else {
+    if (in.prec != SPDF || out.prec != SP64) return cudaErrorInvalidValue;
+    df_to_f64_kernel<<<grid, block, 0, st>>>(view_df(in, V), view<P64>(out), n, V);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mp_accumulate_df(FieldPtr xhi, FieldPtr xlo, int n, int V, const int* skip, int block,
+                                    cudaStream_t st) {
+  if (xhi.prec != SPDF || xlo.prec != SP32) return cudaErrorInvalidValue;
+  mp_accumulate_df_kernel<<<grid_for(n, block), block, 0, st>>>(view_df(xhi, V), view<P32>(xlo), n, V, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mp_convert_df(FieldPtr rhi, FieldPtr rlo, int n, int V, CgScalars* sc, double* partials, int count,
+                                 const int* skip, int block, cudaStream_t st) {
+  const int grid = grid_for(n, block);
+  if (rhi.prec != SPDF) return cudaErrorInvalidValue;
+  switch (rlo.prec) {
+    case SP32:
+      mp_convert_df_kernel<P32><<<grid, block, 0, st>>>(view_df(rhi, V), view<P32>(rlo), n, V, sc, partials, count, skip);
+      break;
+    case SP16:
+      mp_convert_df_kernel<P16><<<grid, block, 0, st>>>(view_df(rhi, V), view<P16>(rlo), n, V, sc, partials, count, skip);
       break;
     default: return cudaErrorInvalidValue;
   }

@@ -9,8 +9,68 @@
 
 namespace wdk {
 
-// Storage precisions of spinor fields.
-enum { P64 = 0, P32 = 1, P16 = 2 };
+// Storage precisions of spinor fields. PDF: double-float, two FP32 arrays (hi, lo) whose sum
+// carries about 48 significant bits; arithmetic on the FP32 pipes (see dfloat below).
+enum { P64 = 0, P32 = 1, P16 = 2, PDF = 3 };
+
+// ---------------------------------------------------------------- double-float arithmetic
+//
+// A value is hi + lo with |lo| <= ulp(hi)/2, hi and lo FP32. Sums and products use the
+// error-free transformations of Knuth (TwoSum), Dekker/FMA (TwoProduct) and the renormalisation
+// FastTwoSum (Dekker 1971; see also Hida, Li, Bailey, "Library for double-double and quad-double
+// arithmetic", 2000, for the "sloppy" double-double add used here). Every step uses the _rn
+// intrinsics, which the compiler never fuses into FMAs, so each transformation stays exact.
+// Relative error per operation ~2^-47; used where FP64 accuracy is needed but the FP64 pipe
+// (1/58 of the FP32 rate on GB300) would be the bottleneck.
+struct dfloat {
+  float hi, lo;
+  __device__ __forceinline__ dfloat() {}
+  __device__ __forceinline__ dfloat(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit dfloat(double d) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+  }
+  __device__ __forceinline__ dfloat(int i) : hi((float)i), lo(0.f) {}
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dfloat(s, e);
+}
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
+  dfloat s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
+__device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+// a * b + c. The templates below call madd for every precision (not fma, whose double overload a
+// dfloat one would hide inside this namespace).
+__device__ __forceinline__ double madd(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ dfloat madd(dfloat a, dfloat b, dfloat c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  dfloat s = df_two_sum(c.hi, p);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(c.lo, e)));
+}
 
 // Lattice geometry. Site index s = x + Lx*(y + Ly*(z + Lz*t)); stride[mu] = step of s along mu.
 struct Geom {
@@ -63,6 +123,31 @@ struct SpinorRef<P16> {
   float* norm;
   typedef float real;
 };
+
+// PDF: hi and lo arrays, each float4 [6][V] (the FP32 layout)
+template <>
+struct SpinorRef<PDF> {
+  float4* hi;
+  float4* lo;
+  typedef dfloat real;
+};
+
+__device__ __forceinline__ void load_spinor(const SpinorRef<PDF>& f, int s, int V, Cx<dfloat> (&v)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float4 h = __ldg(f.hi + (size_t)j * V + s), l = __ldg(f.lo + (size_t)j * V + s);
+    v[2 * j] = cx(dfloat(h.x, l.x), dfloat(h.y, l.y));
+    v[2 * j + 1] = cx(dfloat(h.z, l.z), dfloat(h.w, l.w));
+  }
+}
+
+__device__ __forceinline__ void store_spinor(const SpinorRef<PDF>& f, int s, int V, const Cx<dfloat> (&v)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    f.hi[(size_t)j * V + s] = make_float4(v[2 * j].re.hi, v[2 * j].im.hi, v[2 * j + 1].re.hi, v[2 * j + 1].im.hi);
+    f.lo[(size_t)j * V + s] = make_float4(v[2 * j].re.lo, v[2 * j].im.lo, v[2 * j + 1].re.lo, v[2 * j + 1].im.lo);
+  }
+}
 
 __device__ __forceinline__ void load_spinor(const SpinorRef<P64>& f, int s, int V, Cx<double> (&v)[12]) {
 #pragma unroll
@@ -149,6 +234,12 @@ struct GaugeRef<float, true> {
   const float4* p;
 };
 
+// double-float links: hi and lo arrays, each float2 [4][9][V]
+template <>
+struct GaugeRef<dfloat, false> {
+  const float2* p;  // hi; lo follows at p + 36 V
+};
+
 template <typename R>
 __device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
   return cx<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
@@ -187,6 +278,17 @@ __device__ __forceinline__ void load_link(const GaugeRef<float, false>& g, int m
   for (int k = 0; k < 9; ++k) {
     const float2 d = __ldg(base + (size_t)k * V);
     u[k] = cx(d.x, d.y);
+  }
+}
+
+__device__ __forceinline__ void load_link(const GaugeRef<dfloat, false>& g, int mu, int s, int V,
+                                          Cx<dfloat> (&u)[9]) {
+  const float2* hi = g.p + (size_t)mu * 9 * V + s;
+  const float2* lo = hi + (size_t)36 * V;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float2 h = __ldg(hi + (size_t)k * V), l = __ldg(lo + (size_t)k * V);
+    u[k] = cx(dfloat(h.x, l.x), dfloat(h.y, l.y));
   }
 }
 
@@ -243,10 +345,10 @@ __device__ __forceinline__ void spin_reconstruct(Cx<R> (&acc)[12], const Cx<R> (
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const Cx<R> c0 = chi[c], c1 = chi[3 + c];
-    acc[c].re = fma(k, c0.re, acc[c].re);
-    acc[c].im = fma(k, c0.im, acc[c].im);
-    acc[3 + c].re = fma(k, c1.re, acc[3 + c].re);
-    acc[3 + c].im = fma(k, c1.im, acc[3 + c].im);
+    acc[c].re = madd(k, c0.re, acc[c].re);
+    acc[c].im = madd(k, c0.im, acc[c].im);
+    acc[3 + c].re = madd(k, c1.re, acc[3 + c].re);
+    acc[3 + c].im = madd(k, c1.im, acc[3 + c].im);
     Cx<R> l0, l1;
     if (MU == 0) {  // B^dag chi = (i c1, i c0)
       l0 = cx<R>(-c1.im, c1.re);
@@ -261,10 +363,76 @@ __device__ __forceinline__ void spin_reconstruct(Cx<R> (&acc)[12], const Cx<R> (
       l0 = c0;
       l1 = c1;
     }
-    acc[6 + c].re = fma(k, sg<S>(l0.re), acc[6 + c].re);
-    acc[6 + c].im = fma(k, sg<S>(l0.im), acc[6 + c].im);
-    acc[9 + c].re = fma(k, sg<S>(l1.re), acc[9 + c].re);
-    acc[9 + c].im = fma(k, sg<S>(l1.im), acc[9 + c].im);
+    acc[6 + c].re = madd(k, sg<S>(l0.re), acc[6 + c].re);
+    acc[6 + c].im = madd(k, sg<S>(l0.im), acc[6 + c].im);
+    acc[9 + c].re = madd(k, sg<S>(l1.re), acc[9 + c].re);
+    acc[9 + c].im = madd(k, sg<S>(l1.im), acc[9 + c].im);
+  }
+}
+
+// ---------------------------------------------------------------- runtime hop (compact code)
+//
+// The same spin algebra as spin_project / spin_reconstruct, driven by small tables instead of
+// template parameters, so one copy of the code serves all 8 hops. Used where the per-hop code is
+// long (double-float): fully unrolled, such a kernel no longer fits the instruction cache.
+// B_mu row r has its single non-zero at column bcol(mu, r) with phase i^bph(mu, r):
+// B_x = [[0,-i],[-i,0]], B_y = [[0,-1],[1,0]], B_z = diag(-i, i), B_t = 1.
+__device__ __forceinline__ int bcol(int mu, int r) { return mu < 2 ? 1 - r : r; }
+__device__ __forceinline__ int bph(int mu, int r) {
+  return mu == 0 ? 3 : (mu == 1 ? (r ? 0 : 2) : (mu == 2 ? (r ? 1 : 3) : 0));
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> mul_ipow(Cx<R> z, int k) {  // z * i^k
+  switch (k & 3) {
+    case 0: return z;
+    case 1: return cx<R>(-z.im, z.re);
+    case 2: return cx<R>(-z.re, -z.im);
+    default: return cx<R>(z.im, -z.re);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) {
+  return cx<R>(a.re + b.re, a.im + b.im);
+}
+
+// h = psi_u + S B_mu psi_l
+template <typename R>
+__device__ __forceinline__ void spin_project_rt(int mu, int S, const Cx<R> (&psi)[12], Cx<R> (&h)[6]) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int col = bcol(mu, r), ph = bph(mu, r) + (S < 0 ? 2 : 0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const Cx<R> l = col == 0 ? psi[6 + c] : psi[9 + c];  // selects: no dynamic register indexing
+      h[3 * r + c] = cadd(psi[3 * r + c], mul_ipow(l, ph));
+    }
+  }
+}
+
+// acc_u += k chi;  acc_l += k S B_mu^dag chi  ((B^dag)[col][r] = conj(B[r][col]))
+template <typename R>
+__device__ __forceinline__ void spin_reconstruct_rt(int mu, int S, Cx<R> (&acc)[12], const Cx<R> (&chi)[6], R k) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    acc[i].re = madd(k, chi[i].re, acc[i].re);
+    acc[i].im = madd(k, chi[i].im, acc[i].im);
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int col = bcol(mu, r), ph = (4 - bph(mu, r)) + (S < 0 ? 2 : 0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const Cx<R> l = mul_ipow(chi[3 * r + c], ph);
+      if (col == 0) {  // both branches index statically
+        acc[6 + c].re = madd(k, l.re, acc[6 + c].re);
+        acc[6 + c].im = madd(k, l.im, acc[6 + c].im);
+      } else {
+        acc[9 + c].re = madd(k, l.re, acc[9 + c].re);
+        acc[9 + c].im = madd(k, l.im, acc[9 + c].im);
+      }
+    }
   }
 }
 
@@ -278,17 +446,17 @@ __device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6]
       const Cx<R> u0 = u[3 * a], u1 = u[3 * a + 1], u2 = u[3 * a + 2];
       const Cx<R> h0 = h[3 * sp], h1 = h[3 * sp + 1], h2 = h[3 * sp + 2];
       R re = u0.re * h0.re;
-      re = fma(-u0.im, h0.im, re);
-      re = fma(u1.re, h1.re, re);
-      re = fma(-u1.im, h1.im, re);
-      re = fma(u2.re, h2.re, re);
-      re = fma(-u2.im, h2.im, re);
+      re = madd(-u0.im, h0.im, re);
+      re = madd(u1.re, h1.re, re);
+      re = madd(-u1.im, h1.im, re);
+      re = madd(u2.re, h2.re, re);
+      re = madd(-u2.im, h2.im, re);
       R im = u0.re * h0.im;
-      im = fma(u0.im, h0.re, im);
-      im = fma(u1.re, h1.im, im);
-      im = fma(u1.im, h1.re, im);
-      im = fma(u2.re, h2.im, im);
-      im = fma(u2.im, h2.re, im);
+      im = madd(u0.im, h0.re, im);
+      im = madd(u1.re, h1.im, im);
+      im = madd(u1.im, h1.re, im);
+      im = madd(u2.re, h2.im, im);
+      im = madd(u2.im, h2.re, im);
       chi[3 * sp + a] = cx<R>(re, im);
     }
   }
@@ -304,17 +472,17 @@ __device__ __forceinline__ void su3_dag_mul(const Cx<R> (&u)[9], const Cx<R> (&h
       const Cx<R> u0 = u[a], u1 = u[3 + a], u2 = u[6 + a];
       const Cx<R> h0 = h[3 * sp], h1 = h[3 * sp + 1], h2 = h[3 * sp + 2];
       R re = u0.re * h0.re;
-      re = fma(u0.im, h0.im, re);
-      re = fma(u1.re, h1.re, re);
-      re = fma(u1.im, h1.im, re);
-      re = fma(u2.re, h2.re, re);
-      re = fma(u2.im, h2.im, re);
+      re = madd(u0.im, h0.im, re);
+      re = madd(u1.re, h1.re, re);
+      re = madd(u1.im, h1.im, re);
+      re = madd(u2.re, h2.re, re);
+      re = madd(u2.im, h2.im, re);
       R im = u0.re * h0.im;
-      im = fma(-u0.im, h0.re, im);
-      im = fma(u1.re, h1.im, im);
-      im = fma(-u1.im, h1.re, im);
-      im = fma(u2.re, h2.im, im);
-      im = fma(-u2.im, h2.re, im);
+      im = madd(-u0.im, h0.re, im);
+      im = madd(u1.re, h1.im, im);
+      im = madd(-u1.im, h1.re, im);
+      im = madd(u2.re, h2.im, im);
+      im = madd(-u2.im, h2.re, im);
       chi[3 * sp + a] = cx<R>(re, im);
     }
   }
@@ -397,13 +565,23 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[N], double* partials, un
   return true;
 }
 
+__device__ __forceinline__ double norm2_site(const Cx<dfloat> (&v)[12]) {
+  float a = 0.f;  // the norm steers the solver only: the hi parts suffice
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    a = fmaf(v[c].re.hi, v[c].re.hi, a);
+    a = fmaf(v[c].im.hi, v[c].im.hi, a);
+  }
+  return (double)a;
+}
+
 template <typename R>
 __device__ __forceinline__ double norm2_site(const Cx<R> (&v)[12]) {
   R a = 0;
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
-    a = fma(v[c].re, v[c].re, a);
-    a = fma(v[c].im, v[c].im, a);
+    a = madd(v[c].re, v[c].re, a);
+    a = madd(v[c].im, v[c].im, a);
   }
   return (double)a;
 }

@@ -23,6 +23,24 @@ template <>
 struct RealOf<P64> {
   typedef double type;
 };
+template <>
+struct RealOf<PDF> {
+  typedef dfloat type;
+};
+
+// device view of a field (hi/lo halves for double-float)
+template <int SP>
+__host__ SpinorRef<SP> make_ref(FieldPtr f, int V) {
+  SpinorRef<SP> r;
+  if constexpr (SP == PDF) {
+    r.hi = reinterpret_cast<float4*>(f.p);
+    r.lo = f.p ? reinterpret_cast<float4*>(f.p) + (size_t)6 * V : nullptr;
+  } else {
+    r.p = reinterpret_cast<decltype(r.p)>(f.p);
+    if constexpr (SP == P16) r.norm = f.norm;
+  }
+  return r;
+}
 
 template <int SP, bool C12>
 struct DslashArgs {
@@ -73,13 +91,39 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int
   }
 }
 
+// All 8 hops in a runtime loop (one copy of the per-hop code): for double-float arithmetic, whose
+// unrolled form overflows the instruction cache.
+template <int SF, int SP, bool C12, typename R>
+__device__ __forceinline__ void hops_rt(const DslashArgs<SP, C12>& a, R mk, int s, const int (&c)[4], Cx<R> (&acc)[12]) {
+  const int V = a.g.V;
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int mu = hop >> 1, dir = hop & 1;
+    const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+    const int L = a.g.L[mu], st = a.g.stride[mu];
+    const bool wrap = dir == 0 ? cm == L - 1 : cm == 0;
+    const int nb = dir == 0 ? (wrap ? s - (L - 1) * st : s + st) : (wrap ? s + (L - 1) * st : s - st);
+    const R k = (wrap && a.g.bc[mu] < 0) ? -mk : mk;
+    const int S = dir == 0 ? SF : -SF;
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    load_spinor(a.in, nb, V, psi);
+    spin_project_rt(mu, S, psi, h);
+    load_link(a.u, mu, dir == 0 ? s : nb, V, u);
+    if (dir == 0)
+      su3_mul(u, h, chi);
+    else
+      su3_dag_mul(u, h, chi);
+    spin_reconstruct_rt(mu, S, acc, chi, k);
+  }
+}
+
 // Occupancy: the kernel is latency-bound at large volumes (memory-level parallelism comes from
 // resident warps), so registers are capped for 3 blocks of 256 threads per SM in FP32/FP16
 // (24 warps) and 2 in FP64 (whose FP64 pipe saturates with few warps).
 constexpr int kDslashMaxThreads = 256;
 template <int SP>
 struct DslashMinBlocks {
-  static constexpr int value = SP == P64 ? 2 : 3;
+  static constexpr int value = SP == P64 ? 2 : (SP == PDF ? 1 : 3);
 };
 
 template <int SP, bool C12, bool DAG, int EPI, bool NORM>
@@ -106,10 +150,14 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
     load_spinor(a.in, s, V, acc);
     // D: forward (1 - gamma), backward (1 + gamma); D^dagger: the reverse
     constexpr int SF = DAG ? +1 : -1;
-    hop_pair<0, SF>(a, mk, s, c, acc);
-    hop_pair<1, SF>(a, mk, s, c, acc);
-    hop_pair<2, SF>(a, mk, s, c, acc);
-    hop_pair<3, SF>(a, mk, s, c, acc);
+    if constexpr (SP == PDF) {
+      hops_rt<SF>(a, mk, s, c, acc);
+    } else {
+      hop_pair<0, SF>(a, mk, s, c, acc);
+      hop_pair<1, SF>(a, mk, s, c, acc);
+      hop_pair<2, SF>(a, mk, s, c, acc);
+      hop_pair<3, SF>(a, mk, s, c, acc);
+    }
     if (EPI == EPI_RESID) {
       Cx<R> bv[12];
       load_spinor(a.b, s, V, bv);
@@ -131,14 +179,9 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   static_assert(sizeof(GeomH) == sizeof(Geom), "geometry mirror");
   memcpy(&a.g, &c.g, sizeof(Geom));
   a.u.p = reinterpret_cast<decltype(a.u.p)>(c.u.p);
-  a.in.p = reinterpret_cast<decltype(a.in.p)>(c.in.p);
-  a.out.p = reinterpret_cast<decltype(a.out.p)>(c.out.p);
-  a.b.p = reinterpret_cast<decltype(a.b.p)>(c.b.p);
-  if constexpr (SP == P16) {
-    a.in.norm = c.in.norm;
-    a.out.norm = c.out.norm;
-    a.b.norm = c.b.norm;
-  }
+  a.in = make_ref<SP>(c.in, c.g.V);
+  a.out = make_ref<SP>(c.out, c.g.V);
+  a.b = make_ref<SP>(c.b, c.g.V);
   a.mkappa = (typename RealOf<SP>::type)(-c.kappa);
   a.kappa_dev = c.kappa_dev;
   a.skip = c.skip;
@@ -163,6 +206,10 @@ static cudaError_t launch_p(const DslashCall& c, cudaStream_t st) {
 
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32) return cudaErrorInvalidValue;
+  if (c.in.prec == SPDF) {
+    if (c.u.prec != SPDF) return cudaErrorInvalidValue;
+    return launch_p<PDF, false>(c, st);
+  }
   if (c.in.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;
     return launch_p<P64, false>(c, st);
@@ -251,6 +298,34 @@ __device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int 
   }
 }
 
+template <int SF, int SP, bool C12, typename R>
+__device__ __forceinline__ void eo_hops_rt(const EoArgs<SP, C12>& a, R k0, int s, const int (&c)[4],
+                                           Cx<R> (&acc)[12]) {
+  const int V = a.e.g.V;
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int mu = hop >> 1, dir = hop & 1;
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    const int L = a.e.g.L[mu];
+    const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+    const bool wrap = dir == 0 ? cm == L - 1 : cm == 0;
+    const int nm = dir == 0 ? (wrap ? 0 : cm + 1) : (wrap ? L - 1 : cm - 1);
+    if (mu == 0) n[0] = nm; else if (mu == 1) n[1] = nm; else if (mu == 2) n[2] = nm; else n[3] = nm;
+    const int nb = eo_index(a.e.g, n);
+    const R k = (wrap && a.e.g.bc[mu] < 0) ? -k0 : k0;
+    const int S = dir == 0 ? SF : -SF;
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    load_spinor(a.in, nb, V, psi);
+    spin_project_rt(mu, S, psi, h);
+    load_link(a.u, mu, dir == 0 ? s : nb, V, u);
+    if (dir == 0)
+      su3_mul(u, h, chi);
+    else
+      su3_dag_mul(u, h, chi);
+    spin_reconstruct_rt(mu, S, acc, chi, k);
+  }
+}
+
 template <int SP, bool C12, bool DAG, bool SELF, bool RESID, bool NORM>
 __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
     dslash_eo_kernel(const EoArgs<SP, C12> a) {
@@ -273,10 +348,14 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
       for (int j = 0; j < 12; ++j) acc[j] = cx<R>(0, 0);
     }
     constexpr int SF = DAG ? +1 : -1;
-    eo_hop_pair<0, SF>(a, k0, s, c, acc);
-    eo_hop_pair<1, SF>(a, k0, s, c, acc);
-    eo_hop_pair<2, SF>(a, k0, s, c, acc);
-    eo_hop_pair<3, SF>(a, k0, s, c, acc);
+    if constexpr (SP == PDF) {
+      eo_hops_rt<SF>(a, k0, s, c, acc);
+    } else {
+      eo_hop_pair<0, SF>(a, k0, s, c, acc);
+      eo_hop_pair<1, SF>(a, k0, s, c, acc);
+      eo_hop_pair<2, SF>(a, k0, s, c, acc);
+      eo_hop_pair<3, SF>(a, k0, s, c, acc);
+    }
     if (RESID) {
       Cx<R> bv[12];
       load_spinor(a.b, s, V, bv);
@@ -304,16 +383,10 @@ static cudaError_t eo_launch_t(const EoCall& c, cudaStream_t st) {
   a.e.ticket = c.red.ticket;
   a.e.result = c.red.result;
   a.u.p = reinterpret_cast<decltype(a.u.p)>(c.u.p);
-  a.in.p = reinterpret_cast<decltype(a.in.p)>(c.in.p);
-  a.out.p = reinterpret_cast<decltype(a.out.p)>(c.out.p);
-  a.self.p = reinterpret_cast<decltype(a.self.p)>(c.self.p);
-  a.b.p = reinterpret_cast<decltype(a.b.p)>(c.b.p);
-  if constexpr (SP == P16) {
-    a.in.norm = c.in.norm;
-    a.out.norm = c.out.norm;
-    a.self.norm = c.self.norm;
-    a.b.norm = c.b.norm;
-  }
+  a.in = make_ref<SP>(c.in, c.g.V);
+  a.out = make_ref<SP>(c.out, c.g.V);
+  a.self = make_ref<SP>(c.self, c.g.V);
+  a.b = make_ref<SP>(c.b, c.g.V);
   const int grid = grid_for(c.g.V / 2, c.block);
   if (c.red.result)
     dslash_eo_kernel<SP, C12, DAG, SELF, RESID, true><<<grid, c.block, 0, st>>>(a);
@@ -337,6 +410,10 @@ static cudaError_t eo_launch_p(const EoCall& c, cudaStream_t st) {
 
 cudaError_t launch_dslash_eo(const EoCall& c, cudaStream_t st) {
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || !c.kappa_dev) return cudaErrorInvalidValue;
+  if (c.in.prec == SPDF) {
+    if (c.u.prec != SPDF) return cudaErrorInvalidValue;
+    return eo_launch_p<PDF, false>(c, st);
+  }
   if (c.in.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;
     return eo_launch_p<P64, false>(c, st);

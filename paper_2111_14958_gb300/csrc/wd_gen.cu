@@ -186,7 +186,8 @@ __device__ void reunitarise(Cx<double> (&u)[9]) {
 
 // One thread per link i = 4 s + mu: generate, write the device layouts (and the canonical copy).
 __global__ void gen_gauge_kernel(int V, GeomH eo, int use_eo, double eps, uint64_t seed, double2* __restrict__ g64,
-                                 float2* __restrict__ g32, float4* __restrict__ g32c, double2* __restrict__ canon) {
+                                 float2* __restrict__ g32, float4* __restrict__ g32c, double2* __restrict__ canon,
+                                 float2* __restrict__ gdf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 4 * V) return;
   const int mu = i & 3;
@@ -231,6 +232,15 @@ __global__ void gen_gauge_kernel(int V, GeomH eo, int use_eo, double eps, uint64
 #pragma unroll
     for (int k = 0; k < 9; ++k) g32[((size_t)mu * 9 + k) * V + s] = make_float2((float)U[k].re, (float)U[k].im);
   }
+  if (gdf) {  // double-float copy: hi [4][9][V], lo [4][9][V]
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float hr = __double2float_rn(U[k].re), hm = __double2float_rn(U[k].im);
+      gdf[((size_t)mu * 9 + k) * V + s] = make_float2(hr, hm);
+      gdf[((size_t)36 + mu * 9 + k) * V + s] =
+          make_float2(__double2float_rn(U[k].re - (double)hr), __double2float_rn(U[k].im - (double)hm));
+    }
+  }
   if (g32c) {
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -250,7 +260,7 @@ __global__ void gen_source_kernel(int V, uint64_t seed, double2* __restrict__ ca
 }
 
 cudaError_t launch_gen_gauge(int V, const GeomH* eo, double eps, unsigned long long seed, void* g64, void* g32,
-                             int c12, double* canon, cudaStream_t st) {
+                             int c12, double* canon, void* gdf, cudaStream_t st) {
   const int block = 128;
   const int grid = (4 * V + block - 1) / block;
   GeomH g;
@@ -259,7 +269,7 @@ cudaError_t launch_gen_gauge(int V, const GeomH* eo, double eps, unsigned long l
   gen_gauge_kernel<<<grid, block, 0, st>>>(V, g, eo != nullptr, eps, (uint64_t)seed, reinterpret_cast<double2*>(g64),
                                            c12 ? nullptr : reinterpret_cast<float2*>(g32),
                                            c12 ? reinterpret_cast<float4*>(g32) : nullptr,
-                                           reinterpret_cast<double2*>(canon));
+                                           reinterpret_cast<double2*>(canon), reinterpret_cast<float2*>(gdf));
   return cudaGetLastError();
 }
 

@@ -17,7 +17,9 @@ struct GeomH {
   int bc[4];
 };
 
-enum { SP64 = 0, SP32 = 1, SP16 = 2 };  // spinor storage precisions (match wd_device.cuh)
+enum { SP64 = 0, SP32 = 1, SP16 = 2, SPDF = 3 };  // spinor storage precisions (match wd_device.cuh)
+// SPDF fields: float4 hi [6][V] followed by float4 lo [6][V] in one allocation; SPDF links: float2 hi
+// [4][9][V] followed by float2 lo [4][9][V].
 
 // A spinor field in the device layout.
 struct FieldPtr {
@@ -29,7 +31,7 @@ struct FieldPtr {
 // A gauge field in the device layout.
 struct GaugePtr {
   const void* p;
-  int prec;  // SP64 (18 reals) or SP32
+  int prec;  // SP64 (18 reals), SP32, or SPDF (18 reals, double-float)
   int c12;   // SP32 only: 1 = 12 reals
 };
 
@@ -185,7 +187,7 @@ cudaError_t launch_mconv(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x, M
 // Seeded generation (Philox4x32-10): links into the device layouts (any pointer may be null) and
 // optionally the canonical complex128 copy; Gaussian source in the canonical layout.
 cudaError_t launch_gen_gauge(int V, const GeomH* eo, double eps, unsigned long long seed, void* g64, void* g32,
-                             int c12, double* canon, cudaStream_t st);
+                             int c12, double* canon, void* gdf, cudaStream_t st);
 cudaError_t launch_gen_source(int V, unsigned long long seed, double* canon, cudaStream_t st);
 
 // Even-odd half hopping: out = [b -] ([self] + sign * kappa * H in) on the sites of `parity`
@@ -211,6 +213,14 @@ cudaError_t launch_coo_build(const GeomH& g, const double* U, double kappa, int*
                              cudaStream_t st);
 cudaError_t launch_coo_spmv(long long nnz, const int* row, const int* col, const double* val, const double* in,
                             double* out, long long nrows, cudaStream_t st);
+
+// Double-float support: FP64 <-> double-float fields (to_df = 1: FP64 -> df), x_hi += x_lo with a
+// double-float x_hi, and r_lo = hi part of a double-float residual (+ reliable-update bookkeeping).
+cudaError_t launch_convert_f64_df(FieldPtr in, FieldPtr out, int n, int V, int to_df, int block, cudaStream_t st);
+cudaError_t launch_mp_accumulate_df(FieldPtr xhi, FieldPtr xlo, int n, int V, const int* skip, int block,
+                                    cudaStream_t st);
+cudaError_t launch_mp_convert_df(FieldPtr rhi, FieldPtr rlo, int n, int V, CgScalars* sc, double* partials, int count,
+                                 const int* skip, int block, cudaStream_t st);
 
 // grid size used by a launcher for V sites at a block size
 inline int grid_for(int V, int block) { return (V + block - 1) / block; }

@@ -43,14 +43,15 @@ long long volume_of(const int d[4]) { return (long long)d[0] * d[1] * d[2] * d[3
 // canonical source and solution buffers of the slot).
 size_t request_bytes(const int d[4], int precision) {
   const size_t V = (size_t)volume_of(d);
-  const size_t extra = (precision & WD_EVEN_ODD) ? V * 192 * 2 : 0;  // odd-site temporaries
+  const size_t extra = (precision & WD_EVEN_ODD) ? V * 192 * 3 : 0;  // odd-site temporaries
   precision &= ~WD_EVEN_ODD;
   const size_t f64 = V * 192, f32 = V * 96, f16 = V * 52;
   switch (precision) {
     case WD_PREC_F64: return extra + V * 576 + 9 * f64 + 2 * f64 + (V / 32 + 64) * 8 * 12;
     case WD_PREC_F32: return extra + V * 288 + 6 * f32 + 2 * f64 + V * 12;
-    case WD_PREC_MIXED_F32: return extra + V * 576 + V * 192 + 5 * f32 + 3 * f64 + 2 * f64 + V * 12;
-    case WD_PREC_MIXED_F16: return extra + V * 576 + V * 192 + 4 * f16 + f32 + 3 * f64 + 2 * f64 + V * 12;
+    // mixed: + double-float solution, residual, source (3 x 192 B) and links (576 B) per site
+    case WD_PREC_MIXED_F32: return extra + V * 576 + V * 192 + 5 * f32 + 3 * f64 + 2 * f64 + V * 12 + V * 1152;
+    case WD_PREC_MIXED_F16: return extra + V * 576 + V * 192 + 4 * f16 + f32 + 3 * f64 + 2 * f64 + V * 12 + V * 1152;
   }
   return 0;
 }

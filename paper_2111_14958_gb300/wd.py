@@ -51,6 +51,8 @@ WD_OPT_MAX_RESTARTS = 5
 
 WD_OPT_MULTI_GROUP = 6
 WD_OPT_MULTI_SITES = 7
+WD_OPT_DF_UPDATES = 8
+WD_OPT_APPLY_DF = 9
 
 
 class WdMultiStats(ctypes.Structure):
