@@ -98,6 +98,7 @@ struct wd_ctx {
   int mN;
   FieldPtr mx, mr, mp, mq, ms, meta;  // working precision (mixed: mx = x_lo in FP32, meta unused)
   FieldPtr mx64, mr64, meta64;        // FP64 (F64 context: unused; mixed: outer solution/residual)
+  FieldPtr mxdf, mrdf, metadf;        // mixed with double-float updates: outer solution, residual, source
   MCgScalars* msc;
   MCgScalars* msc_host;
   double* mpartials;
@@ -577,7 +578,8 @@ void free_multi(wd_ctx* c) {
   c->mexec = nullptr;
   c->mgraph = nullptr;
   c->mgraph_ready = false;
-  FieldPtr* fs[] = {&c->mx, &c->mr, &c->mp, &c->mq, &c->ms, &c->meta, &c->mx64, &c->mr64, &c->meta64};
+  FieldPtr* fs[] = {&c->mx,   &c->mr,   &c->mp,   &c->mq,   &c->ms,     &c->meta,
+                    &c->mx64, &c->mr64, &c->meta64, &c->mxdf, &c->mrdf, &c->metadf};
   for (FieldPtr* f : fs) free_field(f);
   if (c->mpartials) cudaFree(c->mpartials);
   if (c->msc) cudaFree(c->msc);
@@ -633,6 +635,11 @@ wd_status ensure_multi(wd_ctx* c, int N) {
     if ((st = alloc_mfield(c, &c->mx64, SP64, N)) != WD_OK) return st;
     if ((st = alloc_mfield(c, &c->mr64, SP64, N)) != WD_OK) return st;
     if ((st = alloc_mfield(c, &c->meta64, SP64, N)) != WD_OK) return st;
+    if (c->use_df) {
+      if ((st = alloc_mfield(c, &c->mxdf, SPDF, N)) != WD_OK) return st;
+      if ((st = alloc_mfield(c, &c->mrdf, SPDF, N)) != WD_OK) return st;
+      if ((st = alloc_mfield(c, &c->metadf, SPDF, N)) != WD_OK) return st;
+    }
   }
   // partials: N per block for grids up to sms * 16 blocks
   c->mpartials_len = (size_t)N * (size_t)c->sms * 16 + 64;
@@ -665,7 +672,7 @@ MDslashCall mcall(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fie
   d.dagger = dagger;
   d.epi = epi;
   d.nrhs = c->mN;
-  const bool f64 = in.prec == SP64 && c->wprec != SP64;
+  const bool f64 = (in.prec == SP64 || in.prec == SPDF) && c->wprec != SP64;
   d.group = f64 ? c->mK64 : c->mK;
   d.sites_per_block = f64 ? c->mspb64 : c->mspb;
   d.grid_x = f64 ? c->mgrid64 : c->mgrid;
@@ -737,7 +744,8 @@ wd_status ensure_multi_tuned(wd_ctx* c) {
     if ((st = autotune_multi(c, c->mp, c->mq, false)) != WD_OK) return st;
   }
   if (is_mixed(c->precision) && !c->mK64) {
-    if ((st = autotune_multi(c, c->mx64, c->mr64, true)) != WD_OK) return st;
+    const bool df = c->use_df && c->mxdf.p;
+    if ((st = autotune_multi(c, df ? c->mxdf : c->mx64, df ? c->mrdf : c->mr64, true)) != WD_OK) return st;
   }
   c->mstats.group = c->mK;
   c->mstats.sites_per_block = c->mspb;
@@ -773,9 +781,18 @@ cudaError_t mplain_epilogue(wd_ctx* c, cudaStream_t st) {
   return mdslash(c, c->mx, c->mq, 0, EPI_RESID, c->meta, c->msc->rr_true, TKM_DSLASH_C, nullptr, st);
 }
 
+bool mdf(const wd_ctx* c) { return c->use_df && c->mxdf.p != nullptr; }
+
 cudaError_t mmixed_update(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
   MCgScalars* sc = c->msc;
+  if (mdf(c)) {
+    if ((e = launch_macc_df(c->mxdf, c->mx, c->V, c->mN, c->mgrid, st)) != cudaSuccess) return e;
+    if ((e = mdslash(c, c->mxdf, c->mrdf, 0, EPI_RESID, c->metadf, sc->rr_true, TKM_DSLASH_C, sc->status, st)) !=
+        cudaSuccess)
+      return e;
+    return launch_mconv_df(c->mrdf, c->mr, c->V, c->mN, c->mgrid, sc, 1, st);
+  }
   if ((e = launch_macc(c->mx64, c->mx, c->V, c->mN, c->mgrid, st)) != cudaSuccess) return e;
   if ((e = mdslash(c, c->mx64, c->mr64, 0, EPI_RESID, c->meta64, sc->rr_true, TKM_DSLASH_C, sc->status, st)) !=
       cudaSuccess)
@@ -787,11 +804,20 @@ cudaError_t mmixed_prologue(wd_ctx* c, cudaStream_t st, int use_cond, unsigned l
   cudaError_t e;
   MCgScalars* sc = c->msc;
   if ((e = launch_mcg_init(sc, st)) != cudaSuccess) return e;
-  if ((e = mdslash(c, c->mx64, c->mr64, 0, EPI_RESID, c->meta64, sc->rr_true, TKM_DSLASH_C, nullptr, st)) !=
-      cudaSuccess)
+  if (mdf(c)) {
+    if ((e = mdslash(c, c->mxdf, c->mrdf, 0, EPI_RESID, c->metadf, sc->rr_true, TKM_DSLASH_C, nullptr, st)) !=
+        cudaSuccess)
+      return e;
+  } else if ((e = mdslash(c, c->mx64, c->mr64, 0, EPI_RESID, c->meta64, sc->rr_true, TKM_DSLASH_C, nullptr, st)) !=
+             cudaSuccess) {
     return e;
+  }
   if ((e = launch_zero(c->mx.p, spinor_bytes(SP32, c->V) * (size_t)c->mN, st)) != cudaSuccess) return e;
-  if ((e = launch_mconv(c->mr64, c->mr, c->V, c->mN, c->mgrid, sc, 0, st)) != cudaSuccess) return e;
+  if (mdf(c)) {
+    if ((e = launch_mconv_df(c->mrdf, c->mr, c->V, c->mN, c->mgrid, sc, 0, st)) != cudaSuccess) return e;
+  } else if ((e = launch_mconv(c->mr64, c->mr, c->V, c->mN, c->mgrid, sc, 0, st)) != cudaSuccess) {
+    return e;
+  }
   if ((e = mdslash(c, c->mr, c->mp, 1, EPI_PLAIN, none_field(), sc->gamma, TKM_DSLASH_B, nullptr, st)) != cudaSuccess)
     return e;
   return launch_mcg_check(sc, use_cond, cond, st);
@@ -818,7 +844,12 @@ cudaError_t mmixed_body_b(wd_ctx* c, cudaStream_t st, int use_cond, unsigned lon
 
 cudaError_t mmixed_epilogue(wd_ctx* c, cudaStream_t st) {
   cudaError_t e;
-  if ((e = launch_macc(c->mx64, c->mx, c->V, c->mN, c->mgrid, st)) != cudaSuccess) return e;
+  if (mdf(c)) {
+    if ((e = launch_macc_df(c->mxdf, c->mx, c->V, c->mN, c->mgrid, st)) != cudaSuccess) return e;
+    if ((e = launch_mconvert_df(c->mx64, c->mxdf, c->V, c->mN, c->mgrid, 0, st)) != cudaSuccess) return e;
+  } else if ((e = launch_macc(c->mx64, c->mx, c->V, c->mN, c->mgrid, st)) != cudaSuccess) {
+    return e;
+  }
   return mdslash(c, c->mx64, c->mr64, 0, EPI_RESID, c->meta64, c->msc->rr_true, TKM_DSLASH_C, nullptr, st);
 }
 
@@ -1167,6 +1198,7 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (v != c->use_df) {
         c->use_df = v;
         destroy_graph(c);
+        free_multi(c);  // multi-RHS workspace is rebuilt with the matching fields on next use
         if (v && c->gauge_loaded && !c->gauge_df) c->gauge_loaded = false;  // needs a reload
       }
       return WD_OK;
@@ -1428,6 +1460,10 @@ wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, doub
   WD_CUDA(cudaGetLastError());
   WD_CUDA(launch_mpack(src, eta, c->V, nrhs, c->mgrid, c->mpartials, &sc->ticket[TKM_PACK], sc->eta2, c->stream));
   WD_CUDA(launch_mpack(x, xs, c->V, nrhs, c->mgrid, nullptr, nullptr, nullptr, c->stream));
+  if (mixed && mdf(c)) {
+    WD_CUDA(launch_mconvert_df(c->meta64, c->metadf, c->V, nrhs, c->mgrid, 1, c->stream));
+    WD_CUDA(launch_mconvert_df(c->mx64, c->mxdf, c->V, nrhs, c->mgrid, 1, c->stream));
+  }
   if (c->use_graph) {
     if ((st = build_mgraph(c)) != WD_OK) {
       abort_capture(c->cap);

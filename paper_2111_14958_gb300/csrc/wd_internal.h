@@ -222,6 +222,12 @@ cudaError_t launch_mp_accumulate_df(FieldPtr xhi, FieldPtr xlo, int n, int V, co
 cudaError_t launch_mp_convert_df(FieldPtr rhi, FieldPtr rlo, int n, int V, CgScalars* sc, double* partials, int count,
                                  const int* skip, int block, cudaStream_t st);
 
+// multi-RHS double-float: FP64 <-> df conversion (to_df = 1: FP64 -> df), x_hi += x_lo, r_lo = hi(r_hi)
+cudaError_t launch_mconvert_df(FieldPtr f64, FieldPtr df, int V, int N, int grid_x, int to_df, cudaStream_t st);
+cudaError_t launch_macc_df(FieldPtr xhi, FieldPtr xlo, int V, int N, int grid_x, cudaStream_t st);
+cudaError_t launch_mconv_df(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x, MCgScalars* sc, int count,
+                            cudaStream_t st);
+
 // grid size used by a launcher for V sites at a block size
 inline int grid_for(int V, int block) { return (V + block - 1) / block; }
 

@@ -35,6 +35,33 @@ struct MSpinor<P16> {
   typedef float real;
 };
 
+// double-float: hi float4 [6][V][N], then lo float4 [6][V][N]
+template <>
+struct MSpinor<PDF> {
+  float4* hi;
+  float4* lo;
+  typedef dfloat real;
+};
+
+__device__ __forceinline__ void mload(const MSpinor<PDF>& f, int s, int r, int V, int N, Cx<dfloat> (&v)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const size_t i = ((size_t)j * V + s) * N + r;
+    const float4 h = __ldg(f.hi + i), l = __ldg(f.lo + i);
+    v[2 * j] = cx(dfloat(h.x, l.x), dfloat(h.y, l.y));
+    v[2 * j + 1] = cx(dfloat(h.z, l.z), dfloat(h.w, l.w));
+  }
+}
+
+__device__ __forceinline__ void mstore(const MSpinor<PDF>& f, int s, int r, int V, int N, const Cx<dfloat> (&v)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const size_t i = ((size_t)j * V + s) * N + r;
+    f.hi[i] = make_float4(v[2 * j].re.hi, v[2 * j].im.hi, v[2 * j + 1].re.hi, v[2 * j + 1].im.hi);
+    f.lo[i] = make_float4(v[2 * j].re.lo, v[2 * j].im.lo, v[2 * j + 1].re.lo, v[2 * j + 1].im.lo);
+  }
+}
+
 __device__ __forceinline__ void mload(const MSpinor<P64>& f, int s, int r, int V, int N, Cx<double> (&v)[12]) {
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
@@ -94,6 +121,14 @@ __device__ __forceinline__ void mstore(const MSpinor<P16>& f, int s, int r, int 
 
 template <int SP>
 static MSpinor<SP> mview(FieldPtr f);
+
+// double-float multi-RHS fields need V and N to find the lo half
+static MSpinor<PDF> mview_df(FieldPtr f, int V, int N) {
+  MSpinor<PDF> r;
+  r.hi = reinterpret_cast<float4*>(f.p);
+  r.lo = reinterpret_cast<float4*>(f.p) + (size_t)6 * V * N;
+  return r;
+}
 template <>
 MSpinor<P64> mview<P64>(FieldPtr f) {
   MSpinor<P64> r;
@@ -121,6 +156,10 @@ struct MReal {
 template <>
 struct MReal<P64> {
   typedef double type;
+};
+template <>
+struct MReal<PDF> {
+  typedef dfloat type;
 };
 
 // ---------------------------------------------------------------- per-RHS deterministic reduction
@@ -217,9 +256,35 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r
   }
 }
 
+// 8 hops in a runtime loop (compact code for double-float, see wd_dslash.cu)
+template <int SF, int SP, bool C12, typename R>
+__device__ __forceinline__ void mhops_rt(const MArgs<SP, C12>& a, R mk, int s, int r, const int (&c)[4],
+                                         Cx<R> (&acc)[12]) {
+  const int V = a.g.V, N = a.N;
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int mu = hop >> 1, dir = hop & 1;
+    const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+    const int L = a.g.L[mu], st = a.g.stride[mu];
+    const bool wrap = dir == 0 ? cm == L - 1 : cm == 0;
+    const int nb = dir == 0 ? (wrap ? s - (L - 1) * st : s + st) : (wrap ? s + (L - 1) * st : s - st);
+    const R k = (wrap && a.g.bc[mu] < 0) ? -mk : mk;
+    const int S = dir == 0 ? SF : -SF;
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    mload(a.in, nb, r, V, N, psi);
+    spin_project_rt(mu, S, psi, h);
+    load_link(a.u, mu, dir == 0 ? s : nb, V, u);
+    if (dir == 0)
+      su3_mul(u, h, chi);
+    else
+      su3_dag_mul(u, h, chi);
+    spin_reconstruct_rt(mu, S, acc, chi, k);
+  }
+}
+
 template <int SP>
 struct MMinBlocks {
-  static constexpr int value = SP == P64 ? 2 : 3;
+  static constexpr int value = SP == P64 ? 2 : (SP == PDF ? 1 : 3);
 };
 
 template <int SP, bool C12, bool DAG, int EPI, bool NORM>
@@ -246,10 +311,14 @@ __global__ void __launch_bounds__(256, MMinBlocks<SP>::value) dslash_multi_kerne
       Cx<R> acc[12];
       mload(a.in, s, r, V, a.N, acc);
       constexpr int SF = DAG ? +1 : -1;
-      mhop<0, SF>(a, mk, s, r, c, acc);
-      mhop<1, SF>(a, mk, s, r, c, acc);
-      mhop<2, SF>(a, mk, s, r, c, acc);
-      mhop<3, SF>(a, mk, s, r, c, acc);
+      if constexpr (SP == PDF) {
+        mhops_rt<SF>(a, mk, s, r, c, acc);
+      } else {
+        mhop<0, SF>(a, mk, s, r, c, acc);
+        mhop<1, SF>(a, mk, s, r, c, acc);
+        mhop<2, SF>(a, mk, s, r, c, acc);
+        mhop<3, SF>(a, mk, s, r, c, acc);
+      }
       if (EPI == EPI_RESID) {
         Cx<R> bv[12];
         mload(a.b, s, r, V, a.N, bv);
@@ -274,9 +343,15 @@ static cudaError_t mlaunch_t(const MDslashCall& c, cudaStream_t st) {
   MArgs<SP, C12> a;
   memcpy(&a.g, &c.g, sizeof(Geom));
   a.u.p = reinterpret_cast<decltype(a.u.p)>(c.u.p);
-  a.in = mview<SP>(c.in);
-  a.out = mview<SP>(c.out);
-  a.b = mview<SP>(c.b);
+  if constexpr (SP == PDF) {
+    a.in = mview_df(c.in, c.g.V, c.nrhs);
+    a.out = mview_df(c.out, c.g.V, c.nrhs);
+    a.b = mview_df(c.b, c.g.V, c.nrhs);
+  } else {
+    a.in = mview<SP>(c.in);
+    a.out = mview<SP>(c.out);
+    a.b = mview<SP>(c.b);
+  }
   a.mkappa = (typename MReal<SP>::type)(-c.kappa);
   a.kappa_dev = c.kappa_dev;
   a.N = c.nrhs;
@@ -307,6 +382,10 @@ cudaError_t launch_dslash_multi(const MDslashCall& c, cudaStream_t st) {
   if (c.nrhs < 1 || c.nrhs > kMaxRhs || c.group < 1 || c.nrhs % c.group || c.sites_per_block < 1 ||
       c.group * c.sites_per_block > 256 || c.grid_x < 1)
     return cudaErrorInvalidValue;
+  if (c.in.prec == SPDF) {
+    if (c.u.prec != SPDF) return cudaErrorInvalidValue;
+    return mlaunch_p<PDF, false>(c, st);
+  }
   if (c.in.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;
     return mlaunch_p<P64, false>(c, st);
@@ -724,6 +803,95 @@ cudaError_t launch_mconv(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x, M
   switch (rlo.prec) {
     case SP32: mconv_kernel<P32><<<grid_x, mblock(N), 0, st>>>(mview<P64>(rhi), mview<P32>(rlo), V, sc, count); break;
     case SP16: mconv_kernel<P16><<<grid_x, mblock(N), 0, st>>>(mview<P64>(rhi), mview<P16>(rlo), V, sc, count); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  mconv_finish_kernel<<<1, 32, 0, st>>>(sc, count);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- multi-RHS double-float helpers
+
+// FP64 multi field (double2 [12][V][N]) <-> double-float multi field (float4 hi/lo [6][V][N])
+__global__ void mconvert_kernel(MSpinor<P64> a, MSpinor<PDF> b, int V, int N, int to_df) {
+  const int rl = threadIdx.x % N, sl = threadIdx.x / N, spb = blockDim.x / N;
+  if (sl >= spb) return;
+  for (int s = blockIdx.x * spb + sl; s < V; s += gridDim.x * spb) {
+    if (to_df) {
+      Cx<double> v[12];
+      Cx<dfloat> w[12];
+      mload(a, s, rl, V, N, v);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) w[c] = cx(dfloat(v[c].re), dfloat(v[c].im));
+      mstore(b, s, rl, V, N, w);
+    } else {
+      Cx<double> v[12];
+      Cx<dfloat> w[12];
+      mload(b, s, rl, V, N, w);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) v[c] = cx((double)w[c].re, (double)w[c].im);
+      mstore(a, s, rl, V, N, v);
+    }
+  }
+}
+
+// x_hi += x_lo in double-float, x_lo = 0 (all right-hand sides)
+__global__ void macc_df_kernel(MSpinor<PDF> xhi, MSpinor<P32> xlo, int V, int N) {
+  const int rl = threadIdx.x % N, sl = threadIdx.x / N, spb = blockDim.x / N;
+  if (sl >= spb) return;
+  for (int s = blockIdx.x * spb + sl; s < V; s += gridDim.x * spb) {
+    Cx<dfloat> xh[12];
+    Cx<float> xl[12];
+    mload(xhi, s, rl, V, N, xh);
+    mload(xlo, s, rl, V, N, xl);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      xh[c].re = xh[c].re + dfloat(xl[c].re, 0.f);
+      xh[c].im = xh[c].im + dfloat(xl[c].im, 0.f);
+      xl[c] = cx(0.f, 0.f);
+    }
+    mstore(xhi, s, rl, V, N, xh);
+    mstore(xlo, s, rl, V, N, xl);
+  }
+}
+
+// r_lo = hi part of the double-float residual, for every right-hand side still running
+template <int SPW>
+__global__ void mconv_df_kernel(MSpinor<PDF> rhi, MSpinor<SPW> rlo, int V, MCgScalars* sc) {
+  const int N = sc->nrhs;
+  const int rl = threadIdx.x % N, sl = threadIdx.x / N, spb = blockDim.x / N;
+  if (sl < spb && sc->status[rl] == ST_RUNNING) {
+    for (int s = blockIdx.x * spb + sl; s < V; s += gridDim.x * spb) {
+      Cx<dfloat> h[12];
+      Cx<float> l[12];
+      mload(rhi, s, rl, V, N, h);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) l[c] = cx(h[c].re.hi, h[c].im.hi);
+      mstore(rlo, s, rl, V, N, l);
+    }
+  }
+}
+
+cudaError_t launch_mconvert_df(FieldPtr f64, FieldPtr df, int V, int N, int grid_x, int to_df, cudaStream_t st) {
+  if (f64.prec != SP64 || df.prec != SPDF) return cudaErrorInvalidValue;
+  mconvert_kernel<<<grid_x, mblock(N), 0, st>>>(mview<P64>(f64), mview_df(df, V, N), V, N, to_df);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_macc_df(FieldPtr xhi, FieldPtr xlo, int V, int N, int grid_x, cudaStream_t st) {
+  if (xhi.prec != SPDF || xlo.prec != SP32) return cudaErrorInvalidValue;
+  macc_df_kernel<<<grid_x, mblock(N), 0, st>>>(mview_df(xhi, V, N), mview<P32>(xlo), V, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mconv_df(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x, MCgScalars* sc, int count,
+                            cudaStream_t st) {
+  if (rhi.prec != SPDF) return cudaErrorInvalidValue;
+  switch (rlo.prec) {
+    case SP32: mconv_df_kernel<P32><<<grid_x, mblock(N), 0, st>>>(mview_df(rhi, V, N), mview<P32>(rlo), V, sc); break;
+    case SP16: mconv_df_kernel<P16><<<grid_x, mblock(N), 0, st>>>(mview_df(rhi, V, N), mview<P16>(rlo), V, sc); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();

@@ -166,3 +166,20 @@ def test_graph_and_host_loop_agree_multi():
         op.close()
     assert outs[0][1] == outs[1][1]
     assert torch.equal(outs[0][0], outs[1][0])
+
+
+def test_solve_multi_mixed_with_fp64_updates():
+    wd = require_gpu()
+    dims = (6, 4, 4, 8)
+    U = synthetic.gauge_field(dims, 0.4, 1)
+    eta = _sources(dims, 3)
+    for df in (0, 1):
+        op = wd.WilsonDirac(dims, 0.124, BC, wd.WD_PREC_MIXED_F16)
+        op.set_option(wd.WD_OPT_DF_UPDATES, df)
+        op.load_gauge(to_dev(U), compress12=True)
+        x, iters, res, status = op.solve_multi(to_dev(eta), tol=1e-10)
+        assert status == wd.WD_OK
+        x = to_np(x)
+        for r in range(3):
+            assert ocg.true_residual(U, eta[r], x[r], 0.124) <= 1e-10
+        op.close()
