@@ -4,6 +4,8 @@ Examples:
   python -m paper_2111_14958_gb300.profile_case --prec 64 --dims 14,14,14,14 --launches 5
   python -m paper_2111_14958_gb300.profile_case --prec 32 --c12 --dims 32,32,32,32 --launches 3
   python -m paper_2111_14958_gb300.profile_case --prec 64 --dims 14,14,14,14 --solve
+  python -m paper_2111_14958_gb300.profile_case --prec 6432 --c12 --dims 16,16,16,16 --launches 0 \
+      --apply 3 --apply-df        # the double-float dslash (through wd_apply)
 
 Fields come from the seeded generators (links exp(i 0.4 H), Gaussian source); the program prints
 the timing of the dslash as the solver launches it (CUDA events) and, with --solve, one CG solve.
@@ -30,6 +32,10 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--kappa", type=float, default=0.12)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--apply", type=int, default=0, help="wd_apply calls on a Gaussian field")
+    ap.add_argument("--apply-df", action="store_true",
+                    help="mixed-precision contexts: wd_apply through the double-float operator")
+    ap.add_argument("--even-odd", action="store_true")
     args = ap.parse_args(argv)
 
     import torch
@@ -39,13 +45,28 @@ def main(argv=None):
 
     dims = tuple(int(v) for v in args.dims.split(","))
     U = torch.from_numpy(synthetic.gauge_field(dims, 0.4, 1)).cuda()
-    op = wd.WilsonDirac(dims, args.kappa, (1, 1, 1, -1), args.prec)
+    prec = args.prec | (wd.WD_EVEN_ODD if args.even_odd else 0)
+    op = wd.WilsonDirac(dims, args.kappa, (1, 1, 1, -1), prec)
     op.load_gauge(U, compress12=args.c12)
     if args.block:
         op.set_option(wd.WD_OPT_BLOCK_DSLASH, args.block)
     if args.launches:
         ms = op.time_dslash(args.dagger, args.launches)
         print(f"dslash dims={dims} prec={args.prec} c12={args.c12}: {ms * 1e3:.2f} us per launch")
+    if args.apply:
+        if args.apply_df:
+            op.set_option(wd.WD_OPT_APPLY_DF, 1)
+        psi = torch.from_numpy(synthetic.gaussian_source(dims, 3)).cuda()
+        if args.prec == wd.WD_PREC_F32:
+            psi = psi.to(torch.complex64)
+        out = torch.empty_like(psi)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.apply):
+            op.apply(psi, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        print(f"wd_apply x{args.apply}: {a.elapsed_time(b) / args.apply * 1e3:.2f} us per call (with packing)")
     if args.solve:
         eta = torch.from_numpy(synthetic.gaussian_source(dims, 2)).cuda()
         x, iters, res, status = op.solve(eta, tol=args.tol, maxit=4000)
