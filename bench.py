@@ -175,6 +175,16 @@ def _config():
 
 # ---------------------------------------------------------------------------- native arm
 
+def max_over_ranks(ms, world, device):
+    """The slowest replica's time: every rank solves its own system (weak scaling)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_native(args, rank, world):
     import torch
     from paper_2111_14958_gb300 import wd
@@ -219,11 +229,7 @@ def run_native(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), world, dev)
     stats = op.stats()
     iters = iters_seen[-1]
     # our kernels per step: gauge load 1, parameter set 1, pack 2, prologue 4, 4 per iteration,
@@ -259,6 +265,9 @@ def run_native(args, rank, world):
     if rank == 0 and not args.quick:
         out["e2e"] = _e2e(args, op, U, eta, dev, stream)
         out["fp32_cg"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_F32, 1e-6, c12=True)
+        # the paper's own CG form (on D D^dag, Sec. 2) with the same kernels and stopping rule
+        out["paper_cg_form_f64"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_F64, TOL, c12=False,
+                                            options={wd.WD_OPT_CG_FORM: 1})
         out["mixed_f32"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_MIXED_F32, TOL, c12=True)
         out["mixed_f16"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_MIXED_F16, TOL, c12=True)
         out["dslash_sweep"] = _sweep(wd, dev, stream, args.sweep)
@@ -314,10 +323,12 @@ def _e2e(args, op, U, eta, dev, stream):
             "h2d_bytes_per_step": U.nbytes + eta.nbytes, "d2h_bytes_per_step": eta.nbytes}
 
 
-def _variant(wd, U, eta, dev, stream, prec, tol, c12):
+def _variant(wd, U, eta, dev, stream, prec, tol, c12, options=None):
     import torch
     op = wd.WilsonDirac(DIMS, KAPPA, BC, prec, stream=stream)
     op.load_gauge(torch.from_numpy(U).to(dev), compress12=c12)
+    for k, v in (options or {}).items():
+        op.set_option(k, v)
     etad = torch.from_numpy(eta).to(dev)
     x = torch.zeros_like(etad)
     for _ in range(3):

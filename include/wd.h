@@ -81,8 +81,14 @@ enum {
                                 FP32, ~48 bits, on the FP32 pipes, ~2^-47 relative error per
                                 operation); 0 uses native FP64. The final true residual is always
                                 recomputed in native FP64. Changing it needs a gauge reload.     */
-  WD_OPT_APPLY_DF = 9        /* mixed precision: 1 makes wd_apply use the double-float operator
+  WD_OPT_APPLY_DF = 9,       /* mixed precision: 1 makes wd_apply use the double-float operator
                                 (complex128 in and out), to check it; 0 (default) native FP64     */
+  WD_OPT_CG_FORM = 10        /* plain FP64 / FP32 contexts, single right-hand side: 0 (default)
+                                CG on D^dag D x = D^dag eta (CGLS arrangement); 1 the paper's
+                                form (Sec. 2): CG on D D^dag y = eta with x = D^dag y, carried in
+                                x directly (x += alpha D^dag p), so x on input is the initial
+                                guess in both forms. Same two operator applications, stopping
+                                rule and true residual; mixed-precision contexts reject 1.       */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

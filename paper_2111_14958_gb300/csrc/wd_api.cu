@@ -6,10 +6,13 @@
 // kernel sets the loop condition, so the host never polls inside a solve), and an epilogue that
 // recomputes the true residual. The host launches the graph, waits once, and relaunches only if
 // the recomputed residual has not reached the tolerance (a restart from the true residual).
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "../../include/wd.h"
@@ -84,6 +87,7 @@ struct wd_ctx {
   int block_dslash;
   int block_blas;
   int max_restarts;
+  int cg_form;  // 0: CGLS on D^dag D; 1: the paper's CG on D D^dag, carried in x
 
   // graph
   cudaGraph_t graph;
@@ -269,19 +273,53 @@ FieldPtr none_field() {
 
 // ---------------------------------------------------------------- plain CG (one precision)
 
+// dst = src (a whole field of the context's volume, norms included)
+cudaError_t copy_field(const wd_ctx* c, FieldPtr src, FieldPtr dst, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(dst.p, src.p, spinor_bytes(src.prec, c->V), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess || src.prec != SP16) return e;
+  return cudaMemcpyAsync(dst.norm, src.norm, sizeof(float) * (size_t)c->V, cudaMemcpyDeviceToDevice, st);
+}
+
 cudaError_t plain_prologue(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
   cudaError_t e;
   CgScalars* sc = c->sc;
   if ((e = launch_cg_init(sc, 0, st)) != cudaSuccess) return e;
   // r = eta - D x
   if ((e = op(c, c->x, c->r, 0, EPI_RESID, c->eta, &sc->rr, TK_DSLASH_A, nullptr, st)) != cudaSuccess) return e;
+  if (c->cg_form) {
+    // the paper's form (CG on D D^dag y = eta, x = D^dag y): p = r, gamma = |r|^2
+    if ((e = copy_field(c, c->r, c->p, st)) != cudaSuccess) return e;
+    return launch_cg_check(sc, use_cond, cond, st, 1);
+  }
   // p = D^dag r, gamma = |p|^2
   if ((e = op(c, c->r, c->p, 1, EPI_PLAIN, none_field(), &sc->gamma, TK_DSLASH_B, nullptr, st)) != cudaSuccess)
     return e;
   return launch_cg_check(sc, use_cond, cond, st);
 }
 
+// The paper's iteration (Sec. 2) with x = D^dag y carried directly: s = D^dag p; alpha =
+// gamma / |s|^2; x += alpha s; r -= alpha D s; gamma' = |r|^2; p = r + (gamma' / gamma) p.
+cudaError_t paper_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
+  cudaError_t e;
+  CgScalars* sc = c->sc;
+  const int bb = c->block_blas;
+  // s = D^dag p, |s|^2 (in the slot the CGLS arrangement uses for |q|^2)
+  if ((e = op(c, c->p, c->s, 1, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
+    return e;
+  // q = D s
+  if ((e = op(c, c->s, c->q, 0, EPI_PLAIN, none_field(), nullptr, TK_DSLASH_B, &sc->status, st)) != cudaSuccess)
+    return e;
+  // alpha; r -= alpha q; gamma' = |r|^2
+  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->nsolve, c->V, sc, c->partials, bb, c->sms, st, 1)) !=
+      cudaSuccess)
+    return e;
+  // x += alpha s; p = r + beta p; loop condition
+  return launch_cg_update_xp(c->wprec, c->x, c->s, c->p, c->r, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb,
+                             c->sms, st);
+}
+
 cudaError_t plain_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
+  if (c->cg_form) return paper_body(c, st, use_cond, cond);
   cudaError_t e;
   CgScalars* sc = c->sc;
   const int bb = c->block_blas;
@@ -295,7 +333,8 @@ cudaError_t plain_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long l
       cudaSuccess)
     return e;
   // x += alpha p; p = s + beta p; loop condition
-  return launch_cg_update_xp(c->wprec, c->x, c->p, c->s, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb, c->sms, st);
+  return launch_cg_update_xp(c->wprec, c->x, c->p, c->p, c->s, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb,
+                             c->sms, st);
 }
 
 cudaError_t plain_epilogue(wd_ctx* c, cudaStream_t st) {
@@ -537,13 +576,45 @@ __global__ void set_params_kernel(CgScalars* sc, double tol2, double delta2, int
   }
 }
 
+// Launch shapes chosen by timing are remembered for the life of the process, per device and
+// problem shape. The block partials of the fused reductions follow the launch shape, so without
+// this two contexts of the same problem (a served request and the same solve alone, say) could
+// time their way to different shapes and differ in the last bits; with it they agree bitwise.
+using TuneKey = std::array<int, 11>;  // device, kind, storage precision, L[4], eo, c12, nrhs, forced
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 2>> g_tune;
+
+TuneKey tune_key(const wd_ctx* c, int kind, int prec, int nrhs, int forced) {
+  return TuneKey{c->device, kind, prec, c->dims[0], c->dims[1], c->dims[2], c->dims[3], c->eo, c->c12, nrhs, forced};
+}
+
+bool tune_lookup(const TuneKey& k, int* a, int* b) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *a = it->second[0];
+  if (b) *b = it->second[1];
+  return true;
+}
+
+// First writer wins: a context that tuned concurrently with another adopts the stored choice.
+void tune_store(const TuneKey& k, int* a, int* b) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto ins = g_tune.emplace(k, std::array<int, 2>{*a, b ? *b : 0});
+  *a = ins.first->second[0];
+  if (b) *b = ins.first->second[1];
+}
+
 // The paper tunes the SYCL workgroup size per device (Sec. 3.1, Fig. 1); here the dslash block
-// size is timed per context and precision on first use (CUDA events, the context's own fields).
+// size is timed per problem shape and precision on first use (CUDA events, the context's own
+// fields) and shared with later contexts of the same shape.
 wd_status autotune_single(wd_ctx* c) {
   if (c->block_dslash > 0) return WD_OK;
   const int precs[3] = {c->wprec, (is_mixed(c->precision) ? SP64 : -1), (c->use_df ? SPDF : -1)};
   for (int prec : precs) {
     if (prec < 0 || c->tuned_block[prec] > 0) continue;
+    const TuneKey key = tune_key(c, 0, prec, 0, 0);
+    if (tune_lookup(key, &c->tuned_block[prec], nullptr)) continue;
     FieldPtr in = prec == c->wprec ? c->p : (prec == SPDF ? c->xdf : c->x64);
     FieldPtr out = prec == c->wprec ? c->q : (prec == SPDF ? c->rdf : c->r64);
     const int cands[] = {64, 128, 256};
@@ -565,6 +636,7 @@ wd_status autotune_single(wd_ctx* c) {
         best_b = b;
       }
     }
+    tune_store(key, &best_b, nullptr);
     c->tuned_block[prec] = best_b;
   }
   return WD_OK;
@@ -689,42 +761,56 @@ cudaError_t mdslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, F
   return launch_dslash_multi(mcall(c, in, out, dagger, epi, b, result, slot, status), st);
 }
 
-// Time candidate launch shapes of the multi-RHS dslash on the context's fields; keep the fastest.
+// Mean time of one multi-RHS dslash launch of shape (K, spb) on the context's fields.
+wd_status time_multi_shape(wd_ctx* c, FieldPtr in, FieldPtr out, int K, int spb, int reps, float* ms) {
+  MDslashCall d = mcall(c, in, out, 0, EPI_PLAIN, none_field(), nullptr, TKM_MISC, nullptr);
+  d.group = K;
+  d.sites_per_block = spb;
+  d.grid_x = mgrid_for(c, spb);
+  WD_CUDA(launch_dslash_multi(d, c->stream));  // warm-up
+  WD_CUDA(cudaEventRecord(c->ev0, c->stream));
+  for (int i = 0; i < reps; ++i) WD_CUDA(launch_dslash_multi(d, c->stream));
+  WD_CUDA(cudaEventRecord(c->ev1, c->stream));
+  WD_CUDA(cudaEventSynchronize(c->ev1));
+  WD_CUDA(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+  *ms /= reps;
+  return WD_OK;
+}
+
+// Time candidate launch shapes of the multi-RHS dslash on the context's fields; keep the fastest
+// (shared with later contexts of the same problem shape, like the single-RHS block size).
 wd_status autotune_multi(wd_ctx* c, FieldPtr in, FieldPtr out, bool f64) {
   const int N = c->mN;
   int bestK = N, bestS = 256 / N;
   float best = 1e30f;
   const int fixK = c->force_mK, fixS = c->force_mspb;
-  for (int K = 1; K <= N; ++K) {
-    if (N % K) continue;
-    if (fixK && K != fixK) continue;
-    if (f64 && K != N && !fixK) continue;  // FP64 is ALU-bound: only the full group is tried
-    const int spbs[] = {4, 8, 16, 32, 64, 128};
-    for (int spb : spbs) {
-      if (fixS && spb != fixS) continue;
-      const int block = K * spb;
-      if (block > 256 || block < 64) continue;
-      MDslashCall d = mcall(c, in, out, 0, EPI_PLAIN, none_field(), nullptr, TKM_MISC, nullptr);
-      d.group = K;
-      d.sites_per_block = spb;
-      d.grid_x = mgrid_for(c, spb);
-      WD_CUDA(launch_dslash_multi(d, c->stream));  // warm-up
-      WD_CUDA(cudaEventRecord(c->ev0, c->stream));
-      const int reps = f64 ? 1 : 3;
-      for (int i = 0; i < reps; ++i) WD_CUDA(launch_dslash_multi(d, c->stream));
-      WD_CUDA(cudaEventRecord(c->ev1, c->stream));
-      WD_CUDA(cudaEventSynchronize(c->ev1));
-      float ms = 0.f;
-      WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-      ms /= reps;
-      if (ms < best) {
-        best = ms;
-        bestK = K;
-        bestS = spb;
+  const int reps = f64 ? 1 : 3;
+  wd_status st;
+  const TuneKey key = tune_key(c, 1, in.prec, N, fixK * 1024 + fixS);
+  if (tune_lookup(key, &bestK, &bestS)) {
+    if (!f64 && (st = time_multi_shape(c, in, out, bestK, bestS, reps, &best)) != WD_OK) return st;
+  } else {
+    for (int K = 1; K <= N; ++K) {
+      if (N % K) continue;
+      if (fixK && K != fixK) continue;
+      if (f64 && K != N && !fixK) continue;  // FP64 is ALU-bound: only the full group is tried
+      const int spbs[] = {4, 8, 16, 32, 64, 128};
+      for (int spb : spbs) {
+        if (fixS && spb != fixS) continue;
+        const int block = K * spb;
+        if (block > 256 || block < 64) continue;
+        float ms = 0.f;
+        if ((st = time_multi_shape(c, in, out, K, spb, reps, &ms)) != WD_OK) return st;
+        if (ms < best) {
+          best = ms;
+          bestK = K;
+          bestS = spb;
+        }
       }
     }
+    if (best >= 1e29f) return fail(WD_EINVAL, "no valid multi-RHS launch shape for this nrhs and options");
+    tune_store(key, &bestK, &bestS);
   }
-  if (best >= 1e29f) return fail(WD_EINVAL, "no valid multi-RHS launch shape for this nrhs and options");
   if (f64) {
     c->mK64 = bestK;
     c->mspb64 = bestS;
@@ -1207,6 +1293,17 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float operator exists on mixed-precision contexts");
       c->apply_df = value != 0.0;
       return WD_OK;
+    case WD_OPT_CG_FORM: {
+      const int v = (int)value;
+      if (value != (double)v || v < 0 || v > 1) return fail(WD_EINVAL, "CG form must be 0 or 1");
+      if (v && is_mixed(c->precision))
+        return fail(WD_EINVAL, "the paper's CG form is available on plain FP64 / FP32 contexts");
+      if (v != c->cg_form) {
+        c->cg_form = v;
+        destroy_graph(c);
+      }
+      return WD_OK;
+    }
     case WD_OPT_MAX_RESTARTS:
       if (!(value >= 0 && value <= 100)) return fail(WD_EINVAL, "max restarts must be in [0, 100]");
       c->max_restarts = (int)value;
@@ -1448,6 +1545,7 @@ wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, doub
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(WD_EINVAL, "tol must be a positive finite number");
   if (maxit < 0 || maxit > 10000000) return fail(WD_EINVAL, "maxit must be in [0, 10^7]");
   if (c->eo) return fail(WD_EINVAL, "multi-RHS calls need a context without WD_EVEN_ODD");
+  if (c->cg_form) return fail(WD_EINVAL, "the paper's CG form (WD_OPT_CG_FORM = 1) solves one right-hand side");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
   const auto t0 = std::chrono::steady_clock::now();
   if ((st = ensure_multi(c, nrhs)) != WD_OK) return st;

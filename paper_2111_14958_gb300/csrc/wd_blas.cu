@@ -299,10 +299,11 @@ __global__ void cg_init_kernel(CgScalars* sc, int reset_iter) {
   }
 }
 
-// After r = eta - D x and p = D^dag r: decide whether the loop has work to do.
-__global__ void cg_check_kernel(CgScalars* sc, int use_cond, cudaGraphConditionalHandle cond) {
+// After r = eta - D x and p = D^dag r (or p = r): decide whether the loop has work to do.
+__global__ void cg_check_kernel(CgScalars* sc, int use_cond, cudaGraphConditionalHandle cond, int gamma_from_rr) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int st = ST_RUNNING;
+    if (gamma_from_rr) sc->gamma = sc->rr;
     const double eta2 = sc->eta2, rr = sc->rr, g = sc->gamma;
     if (!isfinite(eta2) || !isfinite(rr) || !isfinite(g))
       st = ST_BREAKDOWN;
@@ -320,7 +321,8 @@ __global__ void cg_check_kernel(CgScalars* sc, int use_cond, cudaGraphConditiona
 
 // alpha = gamma / ||q||^2; r -= alpha q; ||r||^2. Converged or breakdown is decided here.
 template <int SP>
-__global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int V, CgScalars* sc, double* partials) {
+__global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int V, CgScalars* sc, double* partials,
+                                   int gamma_from_rr) {
   typedef typename Work<SP>::R R;
   if (sc->status != ST_RUNNING) return;  // uniform
   const double qq = sc->qq, gamma = sc->gamma;
@@ -345,6 +347,7 @@ __global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int 
   if (grid_reduce<OpSum, 1>(v, partials, &sc->ticket[TK_UPD_R], tot) && threadIdx.x == 0) {
     sc->alpha = alpha;
     sc->rr = tot[0];
+    if (gamma_from_rr) sc->gamma_new = tot[0];
     if (!ok || !isfinite(tot[0]))
       sc->status = ST_BREAKDOWN;
     else if (tot[0] <= sc->tol2 * sc->eta2)
@@ -352,12 +355,13 @@ __global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int 
   }
 }
 
-// x += alpha p; p = s + beta p (beta = gamma_new / gamma). The last block advances the iteration,
-// applies the iteration limit and sets the loop condition. Every block always takes a ticket, so
-// the condition is set on every pass: the loop cannot run on without an update.
+// x += alpha d; p = s + beta p (beta = gamma_new / gamma; d is p itself in the CGLS arrangement).
+// The last block advances the iteration, applies the iteration limit and sets the loop condition.
+// Every block always takes a ticket, so the condition is set on every pass: the loop cannot run
+// on without an update.
 template <int SP>
-__global__ void cg_update_xp_kernel(SpinorRef<SP> x, SpinorRef<SP> p, SpinorRef<SP> sv, int n, int V, CgScalars* sc,
-                                    double* partials, int use_cond, cudaGraphConditionalHandle cond) {
+__global__ void cg_update_xp_kernel(SpinorRef<SP> x, SpinorRef<SP> d, SpinorRef<SP> p, SpinorRef<SP> sv, int n, int V,
+                                    CgScalars* sc, double* partials, int use_cond, cudaGraphConditionalHandle cond) {
   typedef typename Work<SP>::R R;
   const int st0 = sc->status;  // uniform: only this kernel's last block changes it below
   const double alpha = sc->alpha;
@@ -370,11 +374,22 @@ __global__ void cg_update_xp_kernel(SpinorRef<SP> x, SpinorRef<SP> p, SpinorRef<
   if (s < n && do_x) {
     Cx<R> xv[12], pv[12];
     load_spinor(x, s, V, xv);
-    load_spinor(p, s, V, pv);
+    if (d.p != p.p) {  // uniform
+      Cx<R> dv[12];
+      load_spinor(d, s, V, dv);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      xv[c].re = fma(a, pv[c].re, xv[c].re);
-      xv[c].im = fma(a, pv[c].im, xv[c].im);
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fma(a, dv[c].re, xv[c].re);
+        xv[c].im = fma(a, dv[c].im, xv[c].im);
+      }
+      if (do_p) load_spinor(p, s, V, pv);
+    } else {
+      load_spinor(p, s, V, pv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fma(a, pv[c].re, xv[c].re);
+        xv[c].im = fma(a, pv[c].im, xv[c].im);
+      }
     }
     store_spinor(x, s, V, xv);
     if (do_p) {
@@ -411,42 +426,44 @@ cudaError_t launch_cg_init(CgScalars* sc, int reset_iter, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond, cudaStream_t st) {
-  cg_check_kernel<<<1, 32, 0, st>>>(sc, use_cond, (cudaGraphConditionalHandle)cond);
+cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond, cudaStream_t st,
+                            int gamma_from_rr) {
+  cg_check_kernel<<<1, 32, 0, st>>>(sc, use_cond, (cudaGraphConditionalHandle)cond, gamma_from_rr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, CgScalars* sc, double* partials,
-                               int block, int sms, cudaStream_t st) {
+                               int block, int sms, cudaStream_t st, int gamma_from_rr) {
   const int grid = grid_for(n, block);
+  const int g = gamma_from_rr;
   (void)sms;
   switch (prec) {
-    case SP64: cg_update_r_kernel<P64><<<grid, block, 0, st>>>(view<P64>(r), view<P64>(q), n, V, sc, partials); break;
-    case SP32: cg_update_r_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), n, V, sc, partials); break;
-    case SP16: cg_update_r_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), n, V, sc, partials); break;
+    case SP64: cg_update_r_kernel<P64><<<grid, block, 0, st>>>(view<P64>(r), view<P64>(q), n, V, sc, partials, g); break;
+    case SP32: cg_update_r_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), n, V, sc, partials, g); break;
+    case SP16: cg_update_r_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), n, V, sc, partials, g); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int n, int V, CgScalars* sc,
-                                double* partials, int use_cond, unsigned long long cond, int block, int sms,
-                                cudaStream_t st) {
+cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr d, FieldPtr p, FieldPtr s, int n, int V,
+                                CgScalars* sc, double* partials, int use_cond, unsigned long long cond, int block,
+                                int sms, cudaStream_t st) {
   const int grid = grid_for(n, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
   (void)sms;
   switch (prec) {
     case SP64:
-      cg_update_xp_kernel<P64><<<grid, block, 0, st>>>(view<P64>(x), view<P64>(p), view<P64>(s), n, V, sc, partials,
-                                                       use_cond, h);
+      cg_update_xp_kernel<P64><<<grid, block, 0, st>>>(view<P64>(x), view<P64>(d), view<P64>(p), view<P64>(s), n, V,
+                                                       sc, partials, use_cond, h);
       break;
     case SP32:
-      cg_update_xp_kernel<P32><<<grid, block, 0, st>>>(view<P32>(x), view<P32>(p), view<P32>(s), n, V, sc, partials,
-                                                       use_cond, h);
+      cg_update_xp_kernel<P32><<<grid, block, 0, st>>>(view<P32>(x), view<P32>(d), view<P32>(p), view<P32>(s), n, V,
+                                                       sc, partials, use_cond, h);
       break;
     case SP16:
-      cg_update_xp_kernel<P16><<<grid, block, 0, st>>>(view<P16>(x), view<P16>(p), view<P16>(s), n, V, sc, partials,
-                                                       use_cond, h);
+      cg_update_xp_kernel<P16><<<grid, block, 0, st>>>(view<P16>(x), view<P16>(d), view<P16>(p), view<P16>(s), n, V,
+                                                       sc, partials, use_cond, h);
       break;
     default: return cudaErrorInvalidValue;
   }

@@ -53,6 +53,7 @@ WD_OPT_MULTI_GROUP = 6
 WD_OPT_MULTI_SITES = 7
 WD_OPT_DF_UPDATES = 8
 WD_OPT_APPLY_DF = 9
+WD_OPT_CG_FORM = 10
 
 
 class WdMultiStats(ctypes.Structure):

@@ -180,3 +180,87 @@ def test_repeated_solves_are_bitwise_identical():
     b = op.solve(to_dev(eta), tol=1e-10)[0]
     assert torch.equal(a, b)
     op.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed16"])
+def test_separate_contexts_agree_bitwise(prec):
+    """Launch shapes are tuned once per problem shape, so a second context repeats the first."""
+    wd = require_gpu()
+    dims = (8, 8, 8, 12)
+    U, eta = fields(dims)
+    p = wd.WD_PREC_F64 if prec == "f64" else wd.WD_PREC_MIXED_F16
+    xs = []
+    for _ in range(2):
+        op = wd.WilsonDirac(dims, 0.12, BC, p)
+        op.load_gauge(to_dev(U), compress12=prec != "f64")
+        x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+        assert st == wd.WD_OK
+        xs.append((x, iters, res))
+        op.close()
+    assert xs[0][1] == xs[1][1] and xs[0][2] == xs[1][2]
+    assert torch.equal(xs[0][0], xs[1][0])
+
+
+# ---------------------------------------------------------------- the paper's CG form (Sec. 2)
+
+@pytest.mark.parametrize("dims,kappa", [((4, 4, 4, 4), 0.12), ((6, 4, 4, 8), 0.124)])
+def test_paper_form_fp64_matches_the_oracle_paper_cg(dims, kappa):
+    wd = require_gpu()
+    x, iters, res, status, stats, U, eta = _solve(wd, dims, kappa, wd.WD_PREC_F64, 1e-10,
+                                                  options={wd.WD_OPT_CG_FORM: 1})
+    assert status == wd.WD_OK
+    xo, io, ro, hist = ocg.cg_paper(U, eta, kappa, 1e-10, 4000)
+    assert ocg.true_residual(U, eta, x, kappa) <= 1e-10
+    assert abs(res - ocg.true_residual(U, eta, x, kappa)) < 1e-12
+    assert abs(iters - io) <= 2
+    # both meet 1e-10 on the same non-singular system: they agree to its conditioning
+    assert rel(x, xo) < 1e-8
+
+
+def test_paper_form_fp32_and_even_odd():
+    wd = require_gpu()
+    dims = (8, 8, 8, 8)
+    U, eta = fields(dims)
+    x, iters, res, status, _, _, _ = _solve(wd, dims, 0.12, wd.WD_PREC_F32, 1e-6, U=U, eta=eta, c12=True,
+                                            options={wd.WD_OPT_CG_FORM: 1})
+    assert status == wd.WD_OK and ocg.true_residual(U, eta, x, 0.12) <= 1e-6 * 1.05
+    xe, ie, re_, se, _, _, _ = _solve(wd, dims, 0.12, wd.WD_PREC_F64 | wd.WD_EVEN_ODD, 1e-10, U=U, eta=eta,
+                                      options={wd.WD_OPT_CG_FORM: 1})
+    assert se == wd.WD_OK and ocg.true_residual(U, eta, xe, 0.12) <= 1e-10
+    _, ifull, _, _, _, _, _ = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta,
+                                     options={wd.WD_OPT_CG_FORM: 1})
+    assert ie < 0.75 * ifull
+
+
+def test_paper_form_graph_and_host_loop_agree_bitwise():
+    wd = require_gpu()
+    dims = (4, 4, 4, 8)
+    U, eta = fields(dims)
+    a = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, options={wd.WD_OPT_CG_FORM: 1})
+    b = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=False, options={wd.WD_OPT_CG_FORM: 1})
+    assert a[1] == b[1] and np.array_equal(a[0], b[0])
+
+
+def test_paper_form_uses_the_initial_guess_and_is_rejected_where_unsupported():
+    wd = require_gpu()
+    dims = (4, 4, 4, 4)
+    U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_F64)
+    op.load_gauge(to_dev(U))
+    op.set_option(wd.WD_OPT_CG_FORM, 1)
+    x1, it1, _, st1 = op.solve(to_dev(eta), tol=1e-5)
+    x2, it2, r2, st2 = op.solve(to_dev(eta), x0=x1, tol=1e-10)
+    x3, it3, _, st3 = op.solve(to_dev(eta), tol=1e-10)
+    assert st1 == st2 == st3 == wd.WD_OK
+    assert it2 < it3 and ocg.true_residual(U, eta, to_np(x2), 0.12) <= 1e-10
+    with pytest.raises(wd.WdError) as e:
+        op.solve_multi(to_dev(np.stack([eta, eta])), tol=1e-8)
+    assert e.value.status == wd.WD_EINVAL
+    with pytest.raises(wd.WdError):
+        op.set_option(wd.WD_OPT_CG_FORM, 2)
+    op.close()
+    mixed = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_MIXED_F32)
+    with pytest.raises(wd.WdError) as e:
+        mixed.set_option(wd.WD_OPT_CG_FORM, 1)
+    assert e.value.status == wd.WD_EINVAL
+    mixed.close()

@@ -59,8 +59,10 @@ def test_mixed_requests_match_solves_alone():
         assert ocg.true_residual(U, eta, xs, q["kappa"]) <= q["tol"] * 1.01
         xa, ia, ra, sa = _alone(wd, q)
         assert sa == wd.WD_OK
-        # both solve the same system to tol: they agree to the conditioning of D times tol
-        assert rel(xs, xa) < 200 * q["tol"]
+        # same problem, same launch shapes (tuned once per shape in the process), fixed
+        # reduction trees: the served result is the solve alone, bit for bit
+        assert ia == r["iterations"] and ra == r["true_rel_residual"], q
+        assert np.array_equal(xs, xa), q
 
 
 def test_budget_limits_residency_and_oversize_is_rejected():
