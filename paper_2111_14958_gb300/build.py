@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library ``libwdcg.so`` for sm_103a (GB300).
 
-The three translation units compile in parallel with nvcc, then link into one shared library next
+The translation units compile in parallel with nvcc, then link into one shared library next
 to this file. CUDA runtime is linked statically, so the library needs only the NVIDIA driver at
 run time. Usage: ``python -m paper_2111_14958_gb300.build`` or ``build()`` from Python.
 """

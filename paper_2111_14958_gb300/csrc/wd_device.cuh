@@ -549,12 +549,24 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[N], double* partials, un
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
+  // The last block sums the partials in a fixed order: eight independent loads per step (so the
+  // L2 latency is paid once per eight partials, not once per partial), combined as a fixed tree.
   double w[N];
+  const int G = (int)gridDim.x, S = (int)blockDim.x;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
+    const double* p = partials + (size_t)i * G;
     w[i] = Op::identity();
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      w[i] = Op::apply(w[i], __ldcg(partials + (size_t)i * gridDim.x + b));
+    int b = threadIdx.x;
+    for (; b + 7 * S < G; b += 8 * S) {
+      double x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = __ldcg(p + b + k * S);
+      const double lo = Op::apply(Op::apply(x[0], x[1]), Op::apply(x[2], x[3]));
+      const double hi = Op::apply(Op::apply(x[4], x[5]), Op::apply(x[6], x[7]));
+      w[i] = Op::apply(w[i], Op::apply(lo, hi));
+    }
+    for (; b < G; b += S) w[i] = Op::apply(w[i], __ldcg(p + b));
   }
   block_reduce<Op, N>(w, smem);
   if (threadIdx.x == 0) {

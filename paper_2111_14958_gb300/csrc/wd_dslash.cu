@@ -10,6 +10,10 @@
 // Arithmetic per site: 8 x (12 projection adds + 72 SU(3) FMA/MUL + 24 reconstruction FMA)
 // = 864 FP instructions for 1320 hopping flops + 48 diagonal flops (the usual convention counts
 // 1320). Bytes per site at minimum: 1 spinor in + 1 out + 4 links.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "wd_device.cuh"
 #include "wd_internal.h"
 
@@ -132,9 +136,10 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
   typedef typename RealOf<SP>::type R;
   if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
   const int V = a.g.V;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double n2 = 0.0;
-  if (s < V) {
+  // grid-stride over sites: the launch is one wave of resident blocks, so the fused norm has one
+  // partial per resident block and no block waits in a queue
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
     int c[4];
     {
       int r = s;
@@ -165,12 +170,37 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
       for (int i = 0; i < 12; ++i) acc[i] = cx<R>(bv[i].re - acc[i].re, bv[i].im - acc[i].im);
     }
     store_spinor(a.out, s, V, acc);
-    if (NORM) n2 = norm2_site(acc);
+    if (NORM) n2 += norm2_site(acc);
   }
   if (NORM) {
     double v[1] = {n2}, tot[1];
     if (grid_reduce<OpSum, 1>(v, a.partials, a.ticket, tot) && threadIdx.x == 0) *a.result = tot[0];
   }
+}
+
+// Blocks of `block` threads of kernel `fn` resident on the whole device at once (occupancy of
+// the instantiation, cached per kernel and block size).
+static int resident_grid(const void* fn, int block, int sms) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find({fn, block});
+  if (it == cache.end()) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess || nb < 1) {
+      cudaGetLastError();
+      nb = 1;
+    }
+    it = cache.emplace(std::make_pair(fn, block), nb).first;
+  }
+  return it->second * (sms > 0 ? sms : 1);
+}
+
+template <typename K>
+static int stride_grid(K kernel, int sites, int block, int sms) {
+  const int need = grid_for(sites, block);
+  const int res = resident_grid(reinterpret_cast<const void*>(kernel), block, sms);
+  return need < res ? need : res;
 }
 
 template <int SP, bool C12, bool DAG, int EPI>
@@ -188,11 +218,13 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   a.partials = c.red.partials;
   a.ticket = c.red.ticket;
   a.result = c.red.result;
-  const int grid = grid_for(c.g.V, c.block);
-  if (c.red.result)
-    dslash_kernel<SP, C12, DAG, EPI, true><<<grid, c.block, 0, st>>>(a);
-  else
-    dslash_kernel<SP, C12, DAG, EPI, false><<<grid, c.block, 0, st>>>(a);
+  if (c.red.result) {
+    auto k = dslash_kernel<SP, C12, DAG, EPI, true>;
+    k<<<stride_grid(k, c.g.V, c.block, c.sms), c.block, 0, st>>>(a);
+  } else {
+    auto k = dslash_kernel<SP, C12, DAG, EPI, false>;
+    k<<<stride_grid(k, c.g.V, c.block, c.sms), c.block, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -332,9 +364,8 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
   typedef typename RealOf<SP>::type R;
   if (a.e.skip != nullptr && *a.e.skip != 0) return;
   const int Vh = a.e.g.V >> 1, V = a.e.g.V;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double n2 = 0.0;
-  if (i < Vh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     const int p = a.e.parity;
     int c[4];
     eo_coords(a.e.g, i, p, c);
@@ -363,7 +394,7 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
       for (int j = 0; j < 12; ++j) acc[j] = cx<R>(bv[j].re - acc[j].re, bv[j].im - acc[j].im);
     }
     store_spinor(a.out, s, V, acc);
-    if (NORM) n2 = norm2_site(acc);
+    if (NORM) n2 += norm2_site(acc);
   }
   if (NORM) {
     double v[1] = {n2}, tot[1];
@@ -387,11 +418,13 @@ static cudaError_t eo_launch_t(const EoCall& c, cudaStream_t st) {
   a.out = make_ref<SP>(c.out, c.g.V);
   a.self = make_ref<SP>(c.self, c.g.V);
   a.b = make_ref<SP>(c.b, c.g.V);
-  const int grid = grid_for(c.g.V / 2, c.block);
-  if (c.red.result)
-    dslash_eo_kernel<SP, C12, DAG, SELF, RESID, true><<<grid, c.block, 0, st>>>(a);
-  else
-    dslash_eo_kernel<SP, C12, DAG, SELF, RESID, false><<<grid, c.block, 0, st>>>(a);
+  if (c.red.result) {
+    auto k = dslash_eo_kernel<SP, C12, DAG, SELF, RESID, true>;
+    k<<<stride_grid(k, c.g.V / 2, c.block, c.sms), c.block, 0, st>>>(a);
+  } else {
+    auto k = dslash_eo_kernel<SP, C12, DAG, SELF, RESID, false>;
+    k<<<stride_grid(k, c.g.V / 2, c.block, c.sms), c.block, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -87,6 +87,7 @@ struct DslashCall {
   Red red;          // optional |out|^2
   int block;
   const double* kappa_dev;  // optional: kappa read from device memory (overrides `kappa`)
+  int sms;                  // SM count of the device (the grid is one wave of resident blocks)
 };
 
 // Launchers. Each returns cudaGetLastError() after the launch.
@@ -209,6 +210,7 @@ struct EoCall {
   const int* skip;
   Red red;
   int block;
+  int sms;  // SM count of the device
 };
 cudaError_t launch_dslash_eo(const EoCall& c, cudaStream_t st);
 
