@@ -213,7 +213,6 @@ cudaError_t dslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fi
   d.red = norm_dst ? red_to(c, slot, norm_dst) : no_red();
   d.block = dslash_block(c, in.prec);
   d.kappa_dev = &c->sc->kappa;
-  d.sms = c->sms;
   return launch_dslash(d, st);
 }
 
@@ -239,7 +238,6 @@ cudaError_t eo_half(wd_ctx* c, FieldPtr in, FieldPtr out, int parity, double sig
   e.skip = skip;
   e.red = norm_dst ? red_to(c, slot, norm_dst) : no_red();
   e.block = dslash_block(c, in.prec);
-  e.sms = c->sms;
   return launch_dslash_eo(e, st);
 }
 

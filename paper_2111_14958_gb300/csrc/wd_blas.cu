@@ -329,9 +329,8 @@ __global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int 
   const bool ok = qq > 0.0 && isfinite(qq) && isfinite(gamma);
   const double alpha = ok ? gamma / qq : 0.0;
   const R a = (R)alpha;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double n2 = 0.0;
-  if (ok && s < n) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; ok && s < n; s += gridDim.x * blockDim.x) {
     Cx<R> rv[12], qv[12];
     load_spinor(r, s, V, rv);
     load_spinor(q, s, V, qv);
@@ -341,7 +340,7 @@ __global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int 
       rv[c].im = fma(-a, qv[c].im, rv[c].im);
     }
     store_spinor(r, s, V, rv);
-    n2 = norm2_site(rv);
+    n2 += norm2_site(rv);
   }
   double v[1] = {n2}, tot[1];
   if (grid_reduce<OpSum, 1>(v, partials, &sc->ticket[TK_UPD_R], tot) && threadIdx.x == 0) {
@@ -370,8 +369,7 @@ __global__ void cg_update_xp_kernel(SpinorRef<SP> x, SpinorRef<SP> d, SpinorRef<
   const bool do_p = st0 == ST_RUNNING && isfinite(gnew) && gold > 0.0;
   const double beta = do_p ? gnew / gold : 0.0;
   const R a = (R)alpha, b = (R)beta;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n && do_x) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; do_x && s < n; s += gridDim.x * blockDim.x) {
     Cx<R> xv[12], pv[12];
     load_spinor(x, s, V, xv);
     if (d.p != p.p) {  // uniform
@@ -432,15 +430,16 @@ cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond
   return cudaGetLastError();
 }
 
+#define WD_STRIDE(K) K<<<stride_grid(K, n, block), block, 0, st>>>
+
 cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, CgScalars* sc, double* partials,
                                int block, int sms, cudaStream_t st, int gamma_from_rr) {
-  const int grid = grid_for(n, block);
   const int g = gamma_from_rr;
   (void)sms;
   switch (prec) {
-    case SP64: cg_update_r_kernel<P64><<<grid, block, 0, st>>>(view<P64>(r), view<P64>(q), n, V, sc, partials, g); break;
-    case SP32: cg_update_r_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), n, V, sc, partials, g); break;
-    case SP16: cg_update_r_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), n, V, sc, partials, g); break;
+    case SP64: WD_STRIDE(cg_update_r_kernel<P64>)(view<P64>(r), view<P64>(q), n, V, sc, partials, g); break;
+    case SP32: WD_STRIDE(cg_update_r_kernel<P32>)(view<P32>(r), view<P32>(q), n, V, sc, partials, g); break;
+    case SP16: WD_STRIDE(cg_update_r_kernel<P16>)(view<P16>(r), view<P16>(q), n, V, sc, partials, g); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -449,21 +448,20 @@ cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, C
 cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr d, FieldPtr p, FieldPtr s, int n, int V,
                                 CgScalars* sc, double* partials, int use_cond, unsigned long long cond, int block,
                                 int sms, cudaStream_t st) {
-  const int grid = grid_for(n, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
   (void)sms;
   switch (prec) {
     case SP64:
-      cg_update_xp_kernel<P64><<<grid, block, 0, st>>>(view<P64>(x), view<P64>(d), view<P64>(p), view<P64>(s), n, V,
-                                                       sc, partials, use_cond, h);
+      WD_STRIDE(cg_update_xp_kernel<P64>)(view<P64>(x), view<P64>(d), view<P64>(p), view<P64>(s), n, V, sc, partials,
+                                          use_cond, h);
       break;
     case SP32:
-      cg_update_xp_kernel<P32><<<grid, block, 0, st>>>(view<P32>(x), view<P32>(d), view<P32>(p), view<P32>(s), n, V,
-                                                       sc, partials, use_cond, h);
+      WD_STRIDE(cg_update_xp_kernel<P32>)(view<P32>(x), view<P32>(d), view<P32>(p), view<P32>(s), n, V, sc, partials,
+                                          use_cond, h);
       break;
     case SP16:
-      cg_update_xp_kernel<P16><<<grid, block, 0, st>>>(view<P16>(x), view<P16>(d), view<P16>(p), view<P16>(s), n, V,
-                                                       sc, partials, use_cond, h);
+      WD_STRIDE(cg_update_xp_kernel<P16>)(view<P16>(x), view<P16>(d), view<P16>(p), view<P16>(s), n, V, sc, partials,
+                                          use_cond, h);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -488,9 +486,8 @@ __global__ void mp_update_rx_kernel(SpinorRef<SPW> r, SpinorRef<SPW> q, SpinorRe
   const bool ok = st0 == ST_RUNNING && qq > 0.0 && isfinite(qq) && isfinite(gamma);
   const double alpha = ok ? gamma / qq : 0.0;
   const R a = (R)alpha;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double n2 = 0.0;
-  if (ok && s < n) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; ok && s < n; s += gridDim.x * blockDim.x) {
     Cx<R> rv[12], qv[12], pv[12], xv[12];
     load_spinor(r, s, V, rv);
     load_spinor(q, s, V, qv);
@@ -500,7 +497,7 @@ __global__ void mp_update_rx_kernel(SpinorRef<SPW> r, SpinorRef<SPW> q, SpinorRe
       rv[c].im = fma(-a, qv[c].im, rv[c].im);
     }
     store_spinor(r, s, V, rv);
-    n2 = norm2_site(rv);
+    n2 += norm2_site(rv);
     load_spinor(p, s, V, pv);
     load_spinor(xlo, s, V, xv);
 #pragma unroll
@@ -587,8 +584,7 @@ __global__ void mp_update_p_kernel(SpinorRef<SPW> p, SpinorRef<SPW> sv, int n, i
   const bool do_p = st0 == ST_RUNNING && isfinite(gnew) && gold > 0.0;
   const double beta = do_p ? gnew / gold : 0.0;
   const R b = (R)beta;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (do_p && s < n) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; do_p && s < n; s += gridDim.x * blockDim.x) {
     Cx<R> pv[12], svv[12];
     load_spinor(p, s, V, pv);
     load_spinor(sv, s, V, svv);
@@ -626,17 +622,16 @@ __global__ void zero_kernel(float4* p, size_t n4) {
 cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int n, int V,
                                 CgScalars* sc, double* partials, int use_cond, unsigned long long upd, int block,
                                 cudaStream_t st) {
-  const int grid = grid_for(n, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)upd;
   if (xlo.prec != SP32) return cudaErrorInvalidValue;
   switch (precw) {
     case SP32:
-      mp_update_rx_kernel<P32><<<grid, block, 0, st>>>(view<P32>(r), view<P32>(q), view<P32>(p), view<P32>(xlo), n, V, sc,
-                                                       partials, use_cond, h);
+      WD_STRIDE(mp_update_rx_kernel<P32>)(view<P32>(r), view<P32>(q), view<P32>(p), view<P32>(xlo), n, V, sc, partials,
+                                          use_cond, h);
       break;
     case SP16:
-      mp_update_rx_kernel<P16><<<grid, block, 0, st>>>(view<P16>(r), view<P16>(q), view<P16>(p), view<P32>(xlo), n, V, sc,
-                                                       partials, use_cond, h);
+      WD_STRIDE(mp_update_rx_kernel<P16>)(view<P16>(r), view<P16>(q), view<P16>(p), view<P32>(xlo), n, V, sc, partials,
+                                          use_cond, h);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -668,14 +663,13 @@ cudaError_t launch_mp_convert(FieldPtr rhi, FieldPtr rlo, int n, int V, CgScalar
 
 cudaError_t launch_mp_update_p(int precw, FieldPtr p, FieldPtr s, int n, int V, CgScalars* sc, double* partials,
                                int use_cond, unsigned long long cond, int block, cudaStream_t st) {
-  const int grid = grid_for(n, block);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
   switch (precw) {
     case SP32:
-      mp_update_p_kernel<P32><<<grid, block, 0, st>>>(view<P32>(p), view<P32>(s), n, V, sc, partials, use_cond, h);
+      WD_STRIDE(mp_update_p_kernel<P32>)(view<P32>(p), view<P32>(s), n, V, sc, partials, use_cond, h);
       break;
     case SP16:
-      mp_update_p_kernel<P16><<<grid, block, 0, st>>>(view<P16>(p), view<P16>(s), n, V, sc, partials, use_cond, h);
+      WD_STRIDE(mp_update_p_kernel<P16>)(view<P16>(p), view<P16>(s), n, V, sc, partials, use_cond, h);
       break;
     default: return cudaErrorInvalidValue;
   }

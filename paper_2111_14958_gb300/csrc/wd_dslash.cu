@@ -10,10 +10,6 @@
 // Arithmetic per site: 8 x (12 projection adds + 72 SU(3) FMA/MUL + 24 reconstruction FMA)
 // = 864 FP instructions for 1320 hopping flops + 48 diagonal flops (the usual convention counts
 // 1320). Bytes per site at minimum: 1 spinor in + 1 out + 4 links.
-#include <map>
-#include <mutex>
-#include <utility>
-
 #include "wd_device.cuh"
 #include "wd_internal.h"
 
@@ -178,31 +174,6 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
   }
 }
 
-// Blocks of `block` threads of kernel `fn` resident on the whole device at once (occupancy of
-// the instantiation, cached per kernel and block size).
-static int resident_grid(const void* fn, int block, int sms) {
-  static std::mutex mu;
-  static std::map<std::pair<const void*, int>, int> cache;
-  std::lock_guard<std::mutex> g(mu);
-  auto it = cache.find({fn, block});
-  if (it == cache.end()) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess || nb < 1) {
-      cudaGetLastError();
-      nb = 1;
-    }
-    it = cache.emplace(std::make_pair(fn, block), nb).first;
-  }
-  return it->second * (sms > 0 ? sms : 1);
-}
-
-template <typename K>
-static int stride_grid(K kernel, int sites, int block, int sms) {
-  const int need = grid_for(sites, block);
-  const int res = resident_grid(reinterpret_cast<const void*>(kernel), block, sms);
-  return need < res ? need : res;
-}
-
 template <int SP, bool C12, bool DAG, int EPI>
 static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   DslashArgs<SP, C12> a;
@@ -220,10 +191,10 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   a.result = c.red.result;
   if (c.red.result) {
     auto k = dslash_kernel<SP, C12, DAG, EPI, true>;
-    k<<<stride_grid(k, c.g.V, c.block, c.sms), c.block, 0, st>>>(a);
+    k<<<stride_grid(k, c.g.V, c.block), c.block, 0, st>>>(a);
   } else {
     auto k = dslash_kernel<SP, C12, DAG, EPI, false>;
-    k<<<stride_grid(k, c.g.V, c.block, c.sms), c.block, 0, st>>>(a);
+    k<<<stride_grid(k, c.g.V, c.block), c.block, 0, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -420,10 +391,10 @@ static cudaError_t eo_launch_t(const EoCall& c, cudaStream_t st) {
   a.b = make_ref<SP>(c.b, c.g.V);
   if (c.red.result) {
     auto k = dslash_eo_kernel<SP, C12, DAG, SELF, RESID, true>;
-    k<<<stride_grid(k, c.g.V / 2, c.block, c.sms), c.block, 0, st>>>(a);
+    k<<<stride_grid(k, c.g.V / 2, c.block), c.block, 0, st>>>(a);
   } else {
     auto k = dslash_eo_kernel<SP, C12, DAG, SELF, RESID, false>;
-    k<<<stride_grid(k, c.g.V / 2, c.block, c.sms), c.block, 0, st>>>(a);
+    k<<<stride_grid(k, c.g.V / 2, c.block), c.block, 0, st>>>(a);
   }
   return cudaGetLastError();
 }

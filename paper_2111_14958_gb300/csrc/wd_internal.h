@@ -3,6 +3,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <stdint.h>
 
 namespace wdk {
@@ -87,7 +91,6 @@ struct DslashCall {
   Red red;          // optional |out|^2
   int block;
   const double* kappa_dev;  // optional: kappa read from device memory (overrides `kappa`)
-  int sms;                  // SM count of the device (the grid is one wave of resident blocks)
 };
 
 // Launchers. Each returns cudaGetLastError() after the launch.
@@ -210,7 +213,6 @@ struct EoCall {
   const int* skip;
   Red red;
   int block;
-  int sms;  // SM count of the device
 };
 cudaError_t launch_dslash_eo(const EoCall& c, cudaStream_t st);
 
@@ -236,5 +238,37 @@ cudaError_t launch_mconv_df(FieldPtr rhi, FieldPtr rlo, int V, int N, int grid_x
 
 // grid size used by a launcher for V sites at a block size
 inline int grid_for(int V, int block) { return (V + block - 1) / block; }
+
+// Blocks of `block` threads of kernel `fn` resident on the current device at once (occupancy of
+// the instantiation times the SM count; cached per device, kernel and block size).
+inline int resident_blocks(const void* fn, int block) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple(dev, fn, block);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    int nb = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    cudaGetLastError();
+    it = cache.emplace(key, nb * sms).first;
+  }
+  return it->second;
+}
+
+// Grid of a grid-stride launch over `sites`: one wave of resident blocks, or fewer when the
+// sites do not fill it.
+template <typename K>
+inline int stride_grid(K kernel, int sites, int block) {
+  const int need = grid_for(sites, block);
+  const int res = resident_blocks(reinterpret_cast<const void*>(kernel), block);
+  return need < res ? need : res;
+}
 
 }  // namespace wdk
