@@ -686,7 +686,8 @@ wd_status alloc_mfield(wd_ctx* c, FieldPtr* f, int prec, int N) {
 
 int mgrid_for(const wd_ctx* c, int spb) {
   const long long need = ((long long)c->V + spb - 1) / spb;
-  const long long cap = (long long)c->sms * 16;
+  long long cap = (long long)c->sms * 16;
+  if (cap > kMaxMultiGrid) cap = kMaxMultiGrid;
   return (int)(need < cap ? need : cap);
 }
 
@@ -713,13 +714,14 @@ wd_status ensure_multi(wd_ctx* c, int N) {
       if ((st = alloc_mfield(c, &c->metadf, SPDF, N)) != WD_OK) return st;
     }
   }
-  // partials: N per block for grids up to sms * 16 blocks
-  c->mpartials_len = (size_t)N * (size_t)c->sms * 16 + 64;
+  // reduction workspace (block and run partials, run tickets that must start at zero)
+  c->mpartials_len = kMultiPartials;
   if (cudaMalloc(&c->mpartials, sizeof(double) * c->mpartials_len) != cudaSuccess ||
       cudaMalloc(&c->msc, sizeof(MCgScalars)) != cudaSuccess) {
     cudaGetLastError();
     return fail(WD_ENOMEM, "cudaMalloc of the multi-RHS reduction workspace failed");
   }
+  WD_CUDA(cudaMemsetAsync(c->mpartials, 0, sizeof(double) * c->mpartials_len, c->stream));
   if (cudaMallocHost(&c->msc_host, sizeof(MCgScalars)) != cudaSuccess) {
     cudaGetLastError();
     return fail(WD_ENOMEM, "pinned host allocation failed");

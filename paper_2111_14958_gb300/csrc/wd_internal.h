@@ -143,6 +143,14 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 constexpr int kMaxRhs = 16;
 
 // Per-RHS solver scalars for the multi-RHS CG (one per context).
+// Multi-RHS reductions: at most kMaxMultiGrid blocks per right-hand-side group, summed in runs of
+// kRedGroup blocks (see mreduce); the partials buffer holds kMultiPartials doubles.
+constexpr int kMaxMultiGrid = 4096;
+constexpr int kRedGroup = 32;
+constexpr int kMaxMultiRuns = kMaxMultiGrid / kRedGroup;
+constexpr size_t kMultiPartials =
+    (size_t)kMaxRhs * kMaxMultiGrid + (size_t)kMaxRhs * kMaxMultiRuns + (size_t)kMaxRhs * kMaxMultiRuns / 2;
+
 struct MCgScalars {
   double eta2[kMaxRhs], rr[kMaxRhs], qq[kMaxRhs], gamma[kMaxRhs], gamma_new[kMaxRhs];
   double alpha[kMaxRhs], rr_true[kMaxRhs], rr_ref[kMaxRhs];

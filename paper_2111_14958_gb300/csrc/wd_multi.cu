@@ -164,51 +164,80 @@ struct MReal<PDF> {
 
 // ---------------------------------------------------------------- per-RHS deterministic reduction
 //
-// Thread (sl, rl) of a block holds one value for right-hand side rl of its group. The block sums
-// the values of each rl in a fixed order into partials[r * gridDim.x + blockIdx.x]; the block that
-// draws the last ticket of its group (blockIdx.y) sums each RHS's partials in a fixed order.
-// Returns true in the finishing block; out[rl] (in shared memory) then holds the group's totals
-// for rl < K, valid after the function returns (it ends with a barrier).
+// Thread (sl, rl) of a block holds one value for right-hand side rl of its group (blockIdx.y).
+// Two levels, each in a fixed order, so the result does not depend on block timing:
+//  1. every block sums its values per rl into a block partial; the block that draws the last
+//     ticket of its run of kRedGroup consecutive blocks sums that run's partials per rl;
+//  2. the run that finishes last sums the run partials per rl, spread over the whole block.
+// Either level loads its operands together, so the tail of the reduction costs two L2 round
+// trips instead of one per block partial. Returns true in the finishing block; out[rl] (in shared
+// memory) then holds the group's totals for rl < K, valid after the function returns (it ends
+// with a barrier). Layout of `partials` (fixed offsets): block partials [r][gridDim.x], run
+// partials [kMaxRhs][kMaxMultiRuns], run tickets [kMaxRhs][kMaxMultiRuns] (zero between launches).
 __device__ bool mreduce(double v, int K, double* partials, unsigned* tickets, double* sh /* >= blockDim + 2*kMaxRhs */,
                         double* out) {
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, nt = blockDim.x, G = gridDim.x, y = blockIdx.y, b = blockIdx.x;
+  double* p1 = partials;
+  double* p2 = partials + (size_t)kMaxRhs * kMaxMultiGrid;
+  unsigned* t1 = reinterpret_cast<unsigned*>(p2 + (size_t)kMaxRhs * kMaxMultiRuns);
+  const int nruns = (G + kRedGroup - 1) / kRedGroup, run = b / kRedGroup;
+  const int rsize = min(kRedGroup, G - run * kRedGroup);
+  __shared__ int flag;
   sh[t] = v;
   __syncthreads();
-  __shared__ int is_last;
   if (t < K) {
     double a = 0.0;
-    for (int i = t; i < (int)blockDim.x; i += K) a += sh[i];
-    const int r = blockIdx.y * K + t;
-    partials[(size_t)r * gridDim.x + blockIdx.x] = a;
+    for (int i = t; i < nt; i += K) a += sh[i];
+    p1[(size_t)(y * K + t) * G + b] = a;
     __threadfence();  // each writer publishes its partial before the ticket is taken
   }
   __syncthreads();
   if (t == 0) {
     __threadfence();
-    const unsigned k = atomicAdd(&tickets[blockIdx.y], 1u);
-    is_last = (k % gridDim.x) == gridDim.x - 1;
+    flag = atomicAdd(&t1[y * kMaxMultiRuns + run], 1u) == (unsigned)(rsize - 1);
   }
   __syncthreads();
-  if (!is_last) return false;
+  if (!flag) return false;
   __threadfence();
-  // each RHS of the group: threads stride over the partials, then a fixed-order block tree
-  for (int rl = 0; rl < K; ++rl) {
-    const int r = blockIdx.y * K + rl;
+  // level 1: the partials of this run, eight loads in flight per step, summed in order
+  if (t < K) {
+    const double* q = p1 + (size_t)(y * K + t) * G + run * kRedGroup;
     double a = 0.0;
-    for (int b = t; b < (int)gridDim.x; b += blockDim.x) a += __ldcg(partials + (size_t)r * gridDim.x + b);
-    __syncthreads();
-    sh[t] = a;
-    __syncthreads();
-    for (int n = blockDim.x; n > 1;) {  // fixed pairwise tree, any block size
-      const int h = (n + 1) >> 1;
-      if (t + h < n) sh[t] += sh[t + h];
-      __syncthreads();
-      n = h;
+    for (int i0 = 0; i0 < rsize; i0 += 8) {
+      double x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = i0 + k < rsize ? __ldcg(q + i0 + k) : 0.0;
+      a += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
     }
-    if (t == 0) out[rl] = sh[0];
-    __syncthreads();
+    p2[(size_t)(y * K + t) * kMaxMultiRuns + run] = a;
+    __threadfence();
   }
-  if (t == 0) atomicExch(&tickets[blockIdx.y], 0u);
+  __syncthreads();
+  if (t == 0) {
+    t1[y * kMaxMultiRuns + run] = 0u;  // every block of the run has taken its ticket
+    __threadfence();
+    flag = atomicAdd(&tickets[y], 1u) == (unsigned)(nruns - 1);
+  }
+  __syncthreads();
+  if (!flag) return false;
+  __threadfence();
+  // level 2: thread (j, rl) sums runs j, j + J, ... of rl; then rl sums its J values in order
+  const int J = nt / K, rl = t % K, j = t / K;
+  double a = 0.0;
+  if (j < J) {
+    const double* q = p2 + (size_t)(y * K + rl) * kMaxMultiRuns;
+#pragma unroll 4
+    for (int r = j; r < nruns; r += J) a += __ldcg(q + r);
+  }
+  __syncthreads();
+  sh[t] = a;
+  __syncthreads();
+  if (t < K) {
+    double tot = 0.0;
+    for (int jj = 0; jj < J; ++jj) tot += sh[jj * K + t];
+    out[t] = tot;
+  }
+  if (t == 0) tickets[y] = 0u;
   __syncthreads();
   return true;
 }
@@ -379,6 +408,7 @@ static cudaError_t mlaunch_p(const MDslashCall& c, cudaStream_t st) {
 }
 
 cudaError_t launch_dslash_multi(const MDslashCall& c, cudaStream_t st) {
+  if (c.grid_x < 1 || c.grid_x > kMaxMultiGrid) return cudaErrorInvalidValue;  // reduction workspace bound
   if (c.nrhs < 1 || c.nrhs > kMaxRhs || c.group < 1 || c.nrhs % c.group || c.sites_per_block < 1 ||
       c.group * c.sites_per_block > 256 || c.grid_x < 1)
     return cudaErrorInvalidValue;
@@ -444,6 +474,7 @@ static int mblock(int N) { return N * (256 / N); }
 
 cudaError_t launch_mpack(const double* canon, FieldPtr out, int V, int N, int grid_x, double* partials,
                          unsigned* tickets, double* result, cudaStream_t st) {
+  if (grid_x < 1 || grid_x > kMaxMultiGrid) return cudaErrorInvalidValue;  // reduction workspace bound
   const int block = mblock(N);
   const size_t smem = sizeof(double) * (block + 32);
   const double2* c2 = reinterpret_cast<const double2*>(canon);
@@ -745,6 +776,7 @@ static cudaError_t mupd_r(FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int 
 cudaError_t launch_mcg_update_r(int prec, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int V, MCgScalars* sc,
                                 double* partials, int N, int K, int spb, int grid_x, int mixed, int use_cond,
                                 unsigned long long upd, cudaStream_t st) {
+  if (grid_x < 1 || grid_x > kMaxMultiGrid) return cudaErrorInvalidValue;  // reduction workspace bound
   switch (prec) {
     case SP64: return mixed ? cudaErrorInvalidValue : mupd_r<P64>(r, q, p, xlo, V, sc, partials, N, K, spb, grid_x, 0, use_cond, upd, st);
     case SP32: return mupd_r<P32>(r, q, p, xlo, V, sc, partials, N, K, spb, grid_x, mixed, use_cond, upd, st);
@@ -773,6 +805,7 @@ static cudaError_t mupd_xp(FieldPtr x, FieldPtr p, FieldPtr s, int V, MCgScalars
 cudaError_t launch_mcg_update_xp(int prec, FieldPtr x, FieldPtr p, FieldPtr s, int V, MCgScalars* sc, double* partials,
                                  int N, int K, int spb, int grid_x, int mixed, int use_cond, unsigned long long cond,
                                  cudaStream_t st) {
+  if (grid_x < 1 || grid_x > kMaxMultiGrid) return cudaErrorInvalidValue;  // reduction workspace bound
   switch (prec) {
     case SP64: return mupd_xp<P64>(x, p, s, V, sc, partials, N, K, spb, grid_x, mixed, use_cond, cond, st);
     case SP32: return mupd_xp<P32>(x, p, s, V, sc, partials, N, K, spb, grid_x, mixed, use_cond, cond, st);

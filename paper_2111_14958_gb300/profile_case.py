@@ -6,6 +6,8 @@ Examples:
   python -m paper_2111_14958_gb300.profile_case --prec 64 --dims 14,14,14,14 --solve
   python -m paper_2111_14958_gb300.profile_case --prec 6432 --c12 --dims 16,16,16,16 --launches 0 \
       --apply 3 --apply-df        # the double-float dslash (through wd_apply)
+  python -m paper_2111_14958_gb300.profile_case --prec 6432 --c12 --dims 16,16,16,32 --launches 0 \
+      --multi 12                  # the multi-RHS dslash (through wd_apply_multi)
 
 Fields come from the seeded generators (links exp(i 0.4 H), Gaussian source); the program prints
 the timing of the dslash as the solver launches it (CUDA events) and, with --solve, one CG solve.
@@ -36,6 +38,9 @@ def main(argv=None):
     ap.add_argument("--apply-df", action="store_true",
                     help="mixed-precision contexts: wd_apply through the double-float operator")
     ap.add_argument("--even-odd", action="store_true")
+    ap.add_argument("--multi", type=int, default=0, help="wd_apply_multi calls on this many Gaussian fields")
+    ap.add_argument("--mgroup", type=int, default=0, help="multi-RHS group size K (0 = tuned)")
+    ap.add_argument("--msites", type=int, default=0, help="multi-RHS sites per block (0 = tuned)")
     args = ap.parse_args(argv)
 
     import torch
@@ -67,6 +72,22 @@ def main(argv=None):
         b.record()
         torch.cuda.synchronize()
         print(f"wd_apply x{args.apply}: {a.elapsed_time(b) / args.apply * 1e3:.2f} us per call (with packing)")
+    if args.multi:
+        if args.mgroup:
+            op.set_option(wd.WD_OPT_MULTI_GROUP, args.mgroup)
+        if args.msites:
+            op.set_option(wd.WD_OPT_MULTI_SITES, args.msites)
+        psi = torch.stack([torch.from_numpy(synthetic.gaussian_source(dims, 10 + i)) for i in range(args.multi)]).cuda()
+        out = op.apply_multi(psi)  # tunes the launch shape
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            out = op.apply_multi(psi)
+        b.record()
+        torch.cuda.synchronize()
+        st = op.multi_stats()
+        print(f"wd_apply_multi x3 ({args.multi} RHS): {a.elapsed_time(b) / 3 * 1e3:.1f} us per call with packing; "
+              f"tuned group {st['group']} sites/block {st['sites_per_block']} dslash {st['dslash_ms'] * 1e3:.1f} us")
     if args.solve:
         eta = torch.from_numpy(synthetic.gaussian_source(dims, 2)).cuda()
         x, iters, res, status = op.solve(eta, tol=args.tol, maxit=4000)
