@@ -507,8 +507,8 @@ def _serving(wd, n_req=60, rate=200.0, seed=7):
 
     Sizes uniform over {8^4, 12^4, 16^4, 16^3x32, 24^3x48, 32^3x64}, kappa U[0.115, 0.124], tol in
     {1e-8, 1e-10}, eps U[0.3, 0.5], a seeded gauge field and source per request, 150 GB budget.
-    Mixed precision on 4 concurrent slots against plain FP64 one request at a time (1 slot), same
-    requests and arrival times. One untimed request per size first warms the resident contexts.
+    Mixed precision on 4 concurrent slots (also with even-odd preconditioning) against plain FP64 one
+    request at a time (1 slot), same requests and arrival times. One untimed request per size first warms the resident contexts.
     """
     rng = np.random.default_rng(seed)
     sizes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (24, 24, 24, 48), (32, 32, 32, 64)]
@@ -549,6 +549,7 @@ def _serving(wd, n_req=60, rate=200.0, seed=7):
     out = {"workload": f"{n_req} requests, Poisson arrivals at {rate:g}/s (offered), sizes 8^4..32^3x64, "
                        "kappa U[0.115,0.124], tol {1e-8,1e-10}, eps U[0.3,0.5], 150 GB budget"}
     out["mixed_f32_4_slots"] = run(wd.WD_PREC_MIXED_F32, 4)
+    out["mixed_f32_even_odd_4_slots"] = run(wd.WD_PREC_MIXED_F32 | wd.WD_EVEN_ODD, 4)
     out["plain_f64_one_at_a_time"] = run(wd.WD_PREC_F64, 1)
     return out
 
