@@ -83,12 +83,17 @@ enum {
                                 recomputed in native FP64. Changing it needs a gauge reload.     */
   WD_OPT_APPLY_DF = 9,       /* mixed precision: 1 makes wd_apply use the double-float operator
                                 (complex128 in and out), to check it; 0 (default) native FP64     */
-  WD_OPT_CG_FORM = 10        /* plain FP64 / FP32 contexts, single right-hand side: 0 (default)
+  WD_OPT_CG_FORM = 10,       /* plain FP64 / FP32 contexts, single right-hand side: 0 (default)
                                 CG on D^dag D x = D^dag eta (CGLS arrangement); 1 the paper's
                                 form (Sec. 2): CG on D D^dag y = eta with x = D^dag y, carried in
                                 x directly (x += alpha D^dag p), so x on input is the initial
                                 guess in both forms. Same two operator applications, stopping
                                 rule and true residual; mixed-precision contexts reject 1.       */
+  WD_OPT_DSLASH_VARIANT = 11 /* FP64 single-RHS dslash (FP64 contexts, and the reliable updates
+                                of mixed ones): 0 (default) chosen with the block size on first
+                                use; 1 one thread per site; 2 two threads per site (each owns one
+                                half-spinor row). Lexicographic layout only: even-odd contexts
+                                ignore it.                                                       */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

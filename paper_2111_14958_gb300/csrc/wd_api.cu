@@ -114,6 +114,8 @@ struct wd_ctx {
   bool mgraph_ready;
   int force_mK, force_mspb;   // launch shape fixed by options (0 = autotuned)
   int tuned_block[4];         // autotuned single-RHS dslash block size per storage precision
+  int tuned_var[4];           // ... and kernel variant (FP64: 1 = two threads per site)
+  int force_var;              // WD_OPT_DSLASH_VARIANT: 0 tuned, 1 one thread per site, 2 two (FP64)
   wd_multi_stats mstats;
 };
 
@@ -179,6 +181,14 @@ int dslash_block(const wd_ctx* c, int prec) {
   return 256;
 }
 
+// FP64 single-RHS dslash: one (0) or two (1) threads per site
+int dslash_variant(const wd_ctx* c, int prec) {
+  if (prec != SP64) return 0;
+  if (c->force_var) return c->force_var - 1;
+  if (c->block_dslash > 0) return 0;
+  return c->tuned_block[SP64] > 0 ? c->tuned_var[SP64] : 0;
+}
+
 GaugePtr gauge_for(const wd_ctx* c, int prec) {
   GaugePtr g;
   if (prec == SPDF) {
@@ -212,6 +222,7 @@ cudaError_t dslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fi
   d.skip = skip;
   d.red = norm_dst ? red_to(c, slot, norm_dst) : no_red();
   d.block = dslash_block(c, in.prec);
+  d.variant = dslash_variant(c, in.prec);
   d.kappa_dev = &c->sc->kappa;
   return launch_dslash(d, st);
 }
@@ -614,15 +625,20 @@ wd_status autotune_single(wd_ctx* c) {
   for (int prec : precs) {
     if (prec < 0 || c->tuned_block[prec] > 0) continue;
     const TuneKey key = tune_key(c, 0, prec, 0, 0);
-    if (tune_lookup(key, &c->tuned_block[prec], nullptr)) continue;
+    if (tune_lookup(key, &c->tuned_block[prec], &c->tuned_var[prec])) continue;
     FieldPtr in = prec == c->wprec ? c->p : (prec == SPDF ? c->xdf : c->x64);
     FieldPtr out = prec == c->wprec ? c->q : (prec == SPDF ? c->rdf : c->r64);
-    const int cands[] = {64, 128, 256};
+    // (block, variant); FP64 on the lexicographic layout also tries two threads per site
+    const int cands[6][2] = {{64, 0}, {128, 0}, {256, 0}, {64, 1}, {128, 1}, {256, 1}};
+    const int nc = prec == SP64 && !c->eo ? 6 : 3;
+    const int saved_force = c->force_var;
+    c->force_var = 0;
     float best = 1e30f;
-    int best_b = 256;
+    int best_b = 256, best_v = 0;
     const int reps = prec == SP64 ? 2 : 4;
-    for (int b : cands) {
-      c->tuned_block[prec] = b;
+    for (int k = 0; k < nc; ++k) {
+      c->tuned_block[prec] = cands[k][0];
+      c->tuned_var[prec] = cands[k][1];
       WD_CUDA(op(c, in, out, 0, EPI_PLAIN, none_field(), &c->sc->scratch[1], TK_MISC, nullptr, c->stream));
       WD_CUDA(cudaEventRecord(c->ev0, c->stream));
       for (int i = 0; i < reps; ++i)
@@ -633,11 +649,14 @@ wd_status autotune_single(wd_ctx* c) {
       WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
       if (ms < best) {
         best = ms;
-        best_b = b;
+        best_b = cands[k][0];
+        best_v = cands[k][1];
       }
     }
-    tune_store(key, &best_b, nullptr);
+    c->force_var = saved_force;
+    tune_store(key, &best_b, &best_v);
     c->tuned_block[prec] = best_b;
+    c->tuned_var[prec] = best_v;
   }
   return WD_OK;
 }
@@ -1295,6 +1314,15 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float operator exists on mixed-precision contexts");
       c->apply_df = value != 0.0;
       return WD_OK;
+    case WD_OPT_DSLASH_VARIANT: {
+      const int v = (int)value;
+      if (value != (double)v || v < 0 || v > 2) return fail(WD_EINVAL, "dslash variant must be 0, 1 or 2");
+      if (v == 2 && !(c->precision == WD_PREC_F64 || is_mixed(c->precision)))
+        return fail(WD_EINVAL, "two threads per site is an FP64 dslash variant");
+      c->force_var = v;
+      destroy_graph(c);
+      return WD_OK;
+    }
     case WD_OPT_CG_FORM: {
       const int v = (int)value;
       if (value != (double)v || v < 0 || v > 1) return fail(WD_EINVAL, "CG form must be 0 or 1");

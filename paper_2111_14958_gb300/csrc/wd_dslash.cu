@@ -174,6 +174,174 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
   }
 }
 
+// ---------------------------------------------------------------- FP64: two threads per site
+//
+// The FP64 dslash is bound by the FP64 pipe. At the paper's volumes (14^4 = 38,416 sites) one
+// thread per site leaves 8 warps per SM, too few to keep that pipe fed through the load and
+// dependency latencies. Here lanes 2i and 2i+1 share a site: lane h projects only the half-spinor
+// row h, multiplies it by the link and reconstructs it, so both lanes run the same instructions
+// (no divergence) and together execute the same FP64 operations as one thread of dslash_kernel.
+// Row h of (1 -/+ gamma_mu) pairs upper spin h with lower spin 2 + pi(h), pi(h) = 1 - h for x, y
+// (B_mu off-diagonal) and h for z, t, with the coefficient B_mu[h][pi(h)] = sigma * i^e; the
+// reconstructed row feeds upper spin h and lower spin 2 + pi(h) with S conj(B_mu[h][pi(h)]).
+// Lane h accumulates its upper spin, its own lower spin 2 + h (z, t hops) and the partner's
+// lower spin (x, y hops), which the lanes exchange with one shuffle at the end.
+
+__device__ __forceinline__ Cx<double> shfl_xor_cx(Cx<double> z, int m) {
+  return cx(__shfl_xor_sync(0xffffffffu, z.re, m), __shfl_xor_sync(0xffffffffu, z.im, m));
+}
+
+template <int MU, int DIR, int SF, bool C12>
+__device__ __forceinline__ void pair_hop(const DslashArgs<P64, C12>& a, double mk, int s, const int (&c)[4], int hl,
+                                         Cx<double> (&au)[3], Cx<double> (&ald)[3], Cx<double> (&alo)[3]) {
+  constexpr int S = DIR == 0 ? SF : -SF;  // projector sign: forward (1 + SF gamma), backward the opposite
+  constexpr int E = (MU == 0 || MU == 2) ? 1 : 0;
+  const int V = a.g.V;
+  bool wrap;
+  int nb;
+  if (DIR == 0) {
+    wrap = c[MU] == a.g.L[MU] - 1;
+    nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
+  } else {
+    wrap = c[MU] == 0;
+    nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
+  }
+  const double k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
+  // sigma: B_mu[h][pi(h)] = sigma i^E
+  const double sigma = MU == 0 ? -1.0 : (MU == 3 ? 1.0 : (hl ? 1.0 : -1.0));
+  const double ssig = S > 0 ? sigma : -sigma;
+  const int lower = (MU < 2) ? 3 - hl : 2 + hl;  // spin paired with upper spin hl
+  Cx<double> hh[3];
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    const double2 pu = __ldg(a.in.p + (size_t)(3 * hl + col) * V + nb);
+    const double2 pl = __ldg(a.in.p + (size_t)(3 * lower + col) * V + nb);
+    if (E == 0)
+      hh[col] = cx(fma(ssig, pl.x, pu.x), fma(ssig, pl.y, pu.y));
+    else  // i z = (-z.im, z.re)
+      hh[col] = cx(fma(-ssig, pl.y, pu.x), fma(ssig, pl.x, pu.y));
+  }
+  Cx<double> u[9];
+  load_link(a.u, MU, DIR == 0 ? s : nb, V, u);
+  Cx<double> chi[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Cx<double> u0, u1, u2;
+    if (DIR == 0) {
+      u0 = u[3 * r];
+      u1 = u[3 * r + 1];
+      u2 = u[3 * r + 2];
+    } else {
+      u0 = conj_(u[r]);
+      u1 = conj_(u[3 + r]);
+      u2 = conj_(u[6 + r]);
+    }
+    double re = u0.re * hh[0].re;
+    re = fma(-u0.im, hh[0].im, re);
+    re = fma(u1.re, hh[1].re, re);
+    re = fma(-u1.im, hh[1].im, re);
+    re = fma(u2.re, hh[2].re, re);
+    re = fma(-u2.im, hh[2].im, re);
+    double im = u0.re * hh[0].im;
+    im = fma(u0.im, hh[0].re, im);
+    im = fma(u1.re, hh[1].im, im);
+    im = fma(u1.im, hh[1].re, im);
+    im = fma(u2.re, hh[2].im, im);
+    im = fma(u2.im, hh[2].re, im);
+    chi[r] = cx(re, im);
+  }
+  // upper spin hl += k chi; lower spin 2 + pi(hl) += k S conj(sigma i^E) chi = k S sigma (-i)^E chi
+  const double kl = k * ssig;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    au[r].re = fma(k, chi[r].re, au[r].re);
+    au[r].im = fma(k, chi[r].im, au[r].im);
+    Cx<double>& t = (MU < 2) ? alo[r] : ald[r];
+    if (E == 0) {
+      t.re = fma(kl, chi[r].re, t.re);
+      t.im = fma(kl, chi[r].im, t.im);
+    } else {  // (-i) z = (z.im, -z.re)
+      t.re = fma(kl, chi[r].im, t.re);
+      t.im = fma(-kl, chi[r].re, t.im);
+    }
+  }
+}
+
+template <bool C12, bool DAG, int EPI, bool NORM>
+__global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_pair_kernel(const DslashArgs<P64, C12> a) {
+  if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
+  const int V = a.g.V;
+  const int hl = threadIdx.x & 1;
+  double n2 = 0.0;
+  const int step = (gridDim.x * blockDim.x) >> 1;
+  // The loop runs on the warp's first site, so all 32 lanes take the same trips and meet at the
+  // full-warp shuffle below; lanes past the last site recompute the warp's first site and store
+  // nothing.
+  for (int s0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 1; s0 < V; s0 += step) {
+    const int sl = s0 + ((threadIdx.x & 31) >> 1);
+    const bool live = sl < V;
+    const int s = live ? sl : s0;
+    int c[4];
+    {
+      int r = s;
+      c[0] = r % a.g.L[0];
+      r /= a.g.L[0];
+      c[1] = r % a.g.L[1];
+      r /= a.g.L[1];
+      c[2] = r % a.g.L[2];
+      c[3] = r / a.g.L[2];
+    }
+    const double mk = a.kappa_dev ? -*a.kappa_dev : a.mkappa;
+    Cx<double> au[3], ald[3], alo[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const double2 pu = __ldg(a.in.p + (size_t)(3 * hl + col) * V + s);
+      const double2 pl = __ldg(a.in.p + (size_t)(3 * (2 + hl) + col) * V + s);
+      au[col] = cx(pu.x, pu.y);
+      ald[col] = cx(pl.x, pl.y);
+      alo[col] = cx(0.0, 0.0);
+    }
+    constexpr int SF = DAG ? +1 : -1;
+    pair_hop<0, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<0, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<1, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<1, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<2, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<2, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<3, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<3, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    // lower spin 2 + hl: own z, t part + the partner's x, y part
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const Cx<double> o = shfl_xor_cx(alo[col], 1);
+      ald[col] = cx(ald[col].re + o.re, ald[col].im + o.im);
+    }
+    if (!live) continue;  // after the shuffle: the loop condition is warp-uniform
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      Cx<double> up = au[col], lo = ald[col];
+      if (EPI == EPI_RESID) {
+        const double2 bu = __ldg(a.b.p + (size_t)(3 * hl + col) * V + s);
+        const double2 bl = __ldg(a.b.p + (size_t)(3 * (2 + hl) + col) * V + s);
+        up = cx(bu.x - up.re, bu.y - up.im);
+        lo = cx(bl.x - lo.re, bl.y - lo.im);
+      }
+      a.out.p[(size_t)(3 * hl + col) * V + s] = make_double2(up.re, up.im);
+      a.out.p[(size_t)(3 * (2 + hl) + col) * V + s] = make_double2(lo.re, lo.im);
+      if (NORM) {
+        n2 = fma(up.re, up.re, n2);
+        n2 = fma(up.im, up.im, n2);
+        n2 = fma(lo.re, lo.re, n2);
+        n2 = fma(lo.im, lo.im, n2);
+      }
+    }
+  }
+  if (NORM) {
+    double v[1] = {n2}, tot[1];
+    if (grid_reduce<OpSum, 1>(v, a.partials, a.ticket, tot) && threadIdx.x == 0) *a.result = tot[0];
+  }
+}
+
 template <int SP, bool C12, bool DAG, int EPI>
 static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   DslashArgs<SP, C12> a;
@@ -189,6 +357,18 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   a.partials = c.red.partials;
   a.ticket = c.red.ticket;
   a.result = c.red.result;
+  if constexpr (SP == P64 && !C12) {
+    if (c.variant == 1) {  // two lanes per site
+      if (c.red.result) {
+        auto k = dslash_pair_kernel<C12, DAG, EPI, true>;
+        k<<<stride_grid(k, 2 * c.g.V, c.block), c.block, 0, st>>>(a);
+      } else {
+        auto k = dslash_pair_kernel<C12, DAG, EPI, false>;
+        k<<<stride_grid(k, 2 * c.g.V, c.block), c.block, 0, st>>>(a);
+      }
+      return cudaGetLastError();
+    }
+  }
   if (c.red.result) {
     auto k = dslash_kernel<SP, C12, DAG, EPI, true>;
     k<<<stride_grid(k, c.g.V, c.block), c.block, 0, st>>>(a);
@@ -209,6 +389,7 @@ static cudaError_t launch_p(const DslashCall& c, cudaStream_t st) {
 
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32) return cudaErrorInvalidValue;
+  if (c.variant != 0 && (c.variant != 1 || c.in.prec != SP64)) return cudaErrorInvalidValue;
   if (c.in.prec == SPDF) {
     if (c.u.prec != SPDF) return cudaErrorInvalidValue;
     return launch_p<PDF, false>(c, st);

@@ -91,6 +91,7 @@ struct DslashCall {
   Red red;          // optional |out|^2
   int block;
   const double* kappa_dev;  // optional: kappa read from device memory (overrides `kappa`)
+  int variant;              // FP64 only: 0 one thread per site, 1 two threads per site
 };
 
 // Launchers. Each returns cudaGetLastError() after the launch.

@@ -151,3 +151,55 @@ def test_api_errors_on_gpu():
         wd.wd_set_option(op.ctx, wd.WD_OPT_BLOCK_DSLASH, 33)
     assert e.value.status == wd.WD_EINVAL
     op.close()
+
+
+@pytest.mark.parametrize("dims", SIZES)
+@pytest.mark.parametrize("dagger", [False, True])
+def test_fp64_two_threads_per_site_matches_oracle(dims, dagger):
+    """The FP64 variant in which lanes 2i and 2i+1 share a site (forced)."""
+    wd = require_gpu()
+    U, psi = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_F64)
+    op.load_gauge(to_dev(U))
+    op.set_option(wd.WD_OPT_DSLASH_VARIANT, 2)
+    for block in (64, 256):
+        op.set_option(wd.WD_OPT_BLOCK_DSLASH, block)
+        out = to_np(op.apply(to_dev(psi), dagger=dagger))
+        assert rel(out, wilson.apply_D(U, psi, 0.12, BC, dagger)) < 1e-13, block
+    op.close()
+
+
+@pytest.mark.parametrize("bc", [(-1, 1, -1, 1), (1, 1, 1, 1), (-1, -1, -1, -1), (1, -1, 1, 1)])
+def test_fp64_two_threads_per_site_boundaries(bc):
+    wd = require_gpu()
+    dims = (4, 2, 3, 6)
+    U, psi = fields(dims)
+    op = wd.WilsonDirac(dims, 0.137, bc, wd.WD_PREC_F64)
+    op.load_gauge(to_dev(U))
+    op.set_option(wd.WD_OPT_DSLASH_VARIANT, 2)
+    for dagger in (False, True):
+        out = to_np(op.apply(to_dev(psi), dagger=dagger))
+        assert rel(out, wilson.apply_D(U, psi, 0.137, bc, dagger)) < 1e-13
+    op.close()
+
+
+def test_fp64_two_threads_per_site_in_solves_and_its_errors():
+    wd = require_gpu()
+    from oracle import cg as ocg
+    dims = (6, 4, 4, 10)
+    U, eta = fields(dims)
+    for prec, c12 in ((wd.WD_PREC_F64, False), (wd.WD_PREC_MIXED_F16, True)):
+        op = wd.WilsonDirac(dims, 0.12, BC, prec)
+        op.load_gauge(to_dev(U), compress12=c12)
+        op.set_option(wd.WD_OPT_DSLASH_VARIANT, 2)
+        x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+        assert st == wd.WD_OK and ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10
+        assert abs(res - ocg.true_residual(U, eta, to_np(x), 0.12)) < 1e-12
+        op.close()
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_F32)
+    with pytest.raises(wd.WdError) as e:
+        op.set_option(wd.WD_OPT_DSLASH_VARIANT, 2)
+    assert e.value.status == wd.WD_EINVAL
+    with pytest.raises(wd.WdError):
+        op.set_option(wd.WD_OPT_DSLASH_VARIANT, 3)
+    op.close()
