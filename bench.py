@@ -443,6 +443,31 @@ def _multi_24x48(wd, dev, stream):
         t.append(time.perf_counter() - t0)
     out["gaussian_one_at_a_time_mixed_ms"] = 1e3 * sum(t)
     op.close()
+    # the same with FP16 spinors (per-site norm) in the inner solver
+    op = wd.WilsonDirac(dims, KAPPA, BC, wd.WD_PREC_MIXED_F16, stream=stream)
+    op.generate_gauge(EPS, GAUGE_SEED, compress12=True)
+    x = torch.zeros_like(gauss)
+    wd.cg_solve_multi(op.ctx, gauss, x, TOL, 20000)
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, iters, res = wd.cg_solve_multi(op.ctx, gauss, x, TOL, 20000)
+    t1 = time.perf_counter()
+    ms = wd.wd_get_multi_stats(op.ctx)
+    out["f16_gaussian_sources"] = {"ms": 1e3 * (t1 - t0), "status": st, "iterations_max": max(iters),
+                                   "true_rel_residual_max": max(res), "reliable_updates": ms["reliable_updates"],
+                                   "group_K": ms["group"], "sites_per_block": ms["sites_per_block"]}
+    x1 = torch.zeros_like(gauss[0])
+    wd.cg_solve(op.ctx, gauss[0], x1, TOL, 20000)
+    t = []
+    for k in range(12):
+        x1.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        wd.cg_solve(op.ctx, gauss[k], x1, TOL, 20000)
+        t.append(time.perf_counter() - t0)
+    out["f16_gaussian_one_at_a_time_ms"] = 1e3 * sum(t)
+    op.close()
     # plain FP64, one right-hand side (x 12 for the batch-equivalent time)
     ref = wd.WilsonDirac(dims, KAPPA, BC, wd.WD_PREC_F64, stream=stream)
     ref.generate_gauge(EPS, GAUGE_SEED)
@@ -488,7 +513,8 @@ def _even_odd(wd, dev, stream):
     out = {}
     for name, dims, kappa, prec in (("14x4_f64", DIMS, KAPPA, wd.WD_PREC_F64),
                                     ("14x4_mixed_f32", DIMS, KAPPA, wd.WD_PREC_MIXED_F32),
-                                    ("32x64_mixed_f32", (32, 32, 32, 64), 0.124, wd.WD_PREC_MIXED_F32)):
+                                    ("32x64_mixed_f32", (32, 32, 32, 64), 0.124, wd.WD_PREC_MIXED_F32),
+                                    ("32x64_mixed_f16", (32, 32, 32, 64), 0.124, wd.WD_PREC_MIXED_F16)):
         rec = {}
         for tag, flag in (("plain", 0), ("even_odd", wd.WD_EVEN_ODD)):
             op = wd.WilsonDirac(dims, kappa, BC, prec | flag, stream=stream)
