@@ -181,6 +181,30 @@ __device__ __forceinline__ void load_spinor(const SpinorRef<P16>& f, int s, int 
   }
 }
 
+// Neighbour spinor of a hop, returning the hop's reconstruction factor. The FP16 form leaves the
+// per-site norm out of the 24 values and folds it into that factor instead (the hop is linear in
+// the spinor): one multiply per hop instead of 24.
+template <typename Ref, typename R>
+__device__ __forceinline__ R load_hop_spinor(const Ref& f, int s, int V, Cx<R> (&v)[12], R k) {
+  load_spinor(f, s, V, v);
+  return k;
+}
+
+__device__ __forceinline__ float load_hop_spinor(const SpinorRef<P16>& f, int s, int V, Cx<float> (&v)[12], float k) {
+  const float nrm = __ldg(f.norm + s);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const uint4 d = __ldg(f.p + (size_t)j * V + s);
+    const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&w[q]));
+      v[4 * j + q] = cx(fl.x, fl.y);
+    }
+  }
+  return k * nrm;
+}
+
 __device__ __forceinline__ void store_spinor(const SpinorRef<P64>& f, int s, int V, const Cx<double> (&v)[12]) {
 #pragma unroll
   for (int c = 0; c < 12; ++c) f.p[(size_t)c * V + s] = make_double2(v[c].re, v[c].im);

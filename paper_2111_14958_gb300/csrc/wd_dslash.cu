@@ -63,9 +63,8 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int
   {
     const bool wrap = c[MU] == a.g.L[MU] - 1;
     const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12];
-    load_spinor(a.in, nb, V, psi);
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     Cx<R> h[6];
     spin_project<MU, S_FWD>(psi, h);
     Cx<R> u[9];
@@ -78,9 +77,8 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int
   {
     const bool wrap = c[MU] == 0;
     const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12];
-    load_spinor(a.in, nb, V, psi);
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     Cx<R> h[6];
     spin_project<MU, -S_FWD>(psi, h);
     Cx<R> u[9];
@@ -459,9 +457,8 @@ __device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int 
     const bool wrap = n[MU] == a.e.g.L[MU] - 1;
     n[MU] = wrap ? 0 : n[MU] + 1;
     const int nb = eo_index(a.e.g, n);
-    const R k = (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0;
     Cx<R> psi[12], h[6], u[9], chi[6];
-    load_spinor(a.in, nb, V, psi);
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
     spin_project<MU, SF>(psi, h);
     load_link(a.u, MU, s, V, u);
     su3_mul(u, h, chi);
@@ -472,9 +469,8 @@ __device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int 
     const bool wrap = n[MU] == 0;
     n[MU] = wrap ? a.e.g.L[MU] - 1 : n[MU] - 1;
     const int nb = eo_index(a.e.g, n);
-    const R k = (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0;
     Cx<R> psi[12], h[6], u[9], chi[6];
-    load_spinor(a.in, nb, V, psi);
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
     spin_project<MU, -SF>(psi, h);
     load_link(a.u, MU, nb, V, u);
     su3_dag_mul(u, h, chi);

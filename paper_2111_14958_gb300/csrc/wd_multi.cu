@@ -92,6 +92,30 @@ __device__ __forceinline__ void mload(const MSpinor<P16>& f, int s, int r, int V
   }
 }
 
+// Neighbour spinor of a hop, returning the hop's reconstruction factor (FP16: the per-site norm is
+// folded into the factor instead of the 24 values, as in the single right-hand-side kernel).
+template <typename Ref, typename R>
+__device__ __forceinline__ R mload_hop(const Ref& f, int s, int r, int V, int N, Cx<R> (&v)[12], R k) {
+  mload(f, s, r, V, N, v);
+  return k;
+}
+
+__device__ __forceinline__ float mload_hop(const MSpinor<P16>& f, int s, int r, int V, int N, Cx<float> (&v)[12],
+                                           float k) {
+  const float nrm = __ldg(f.norm + (size_t)s * N + r);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const uint4 d = __ldg(f.p + ((size_t)j * V + s) * N + r);
+    const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&w[q]));
+      v[4 * j + q] = cx(fl.x, fl.y);
+    }
+  }
+  return k * nrm;
+}
+
 __device__ __forceinline__ void mstore(const MSpinor<P64>& f, int s, int r, int V, int N, const Cx<double> (&v)[12]) {
 #pragma unroll
   for (int c = 0; c < 12; ++c) f.p[((size_t)c * V + s) * N + r] = make_double2(v[c].re, v[c].im);
@@ -264,9 +288,8 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r
   {
     const bool wrap = c[MU] == a.g.L[MU] - 1;
     const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12], h[6], u[9], chi[6];
-    mload(a.in, nb, r, V, N, psi);
+    const R k = mload_hop(a.in, nb, r, V, N, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     spin_project<MU, SF>(psi, h);
     load_link(a.u, MU, s, V, u);
     su3_mul(u, h, chi);
@@ -275,9 +298,8 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r
   {
     const bool wrap = c[MU] == 0;
     const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
-    const R k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
     Cx<R> psi[12], h[6], u[9], chi[6];
-    mload(a.in, nb, r, V, N, psi);
+    const R k = mload_hop(a.in, nb, r, V, N, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     spin_project<MU, -SF>(psi, h);
     load_link(a.u, MU, nb, V, u);
     su3_dag_mul(u, h, chi);
