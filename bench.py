@@ -589,9 +589,10 @@ def _cpu_baseline(gpu_iters):
     dt = time.perf_counter() - t0
     per_apply = dt / (2 * k + 3)
     ms = 1e3 * per_apply * (2 * gpu_iters + 3)
-    return {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"{k} CGLS iterations of the 14^4 FP64 solve (numpy, one thread), "
-                      f"scaled to the {gpu_iters} iterations + setup of the full solve"}
+    return {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "host_cores": os.cpu_count(),
+            "sample": f"{k} CGLS iterations of the 14^4 FP64 solve (numpy, one thread: the oracle's "
+                      f"einsum contractions do not call a threaded BLAS), scaled to the {gpu_iters} "
+                      f"iterations + setup of the full solve"}
 
 
 def main():
