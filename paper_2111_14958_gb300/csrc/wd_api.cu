@@ -321,12 +321,11 @@ cudaError_t paper_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long l
   if ((e = op(c, c->s, c->q, 0, EPI_PLAIN, none_field(), nullptr, TK_DSLASH_B, &sc->status, st)) != cudaSuccess)
     return e;
   // alpha; r -= alpha q; gamma' = |r|^2
-  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->nsolve, c->V, sc, c->partials, bb, c->sms, st, 1)) !=
+  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->nsolve, c->V, sc, c->partials, bb, st, 1)) !=
       cudaSuccess)
     return e;
   // x += alpha s; p = r + beta p; loop condition
-  return launch_cg_update_xp(c->wprec, c->x, c->s, c->p, c->r, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb,
-                             c->sms, st);
+  return launch_cg_update_xp(c->wprec, c->x, c->s, c->p, c->r, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb, st);
 }
 
 cudaError_t plain_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long long cond) {
@@ -338,14 +337,13 @@ cudaError_t plain_body(wd_ctx* c, cudaStream_t st, int use_cond, unsigned long l
   if ((e = op(c, c->p, c->q, 0, EPI_PLAIN, none_field(), &sc->qq, TK_DSLASH_A, &sc->status, st)) != cudaSuccess)
     return e;
   // alpha; r -= alpha q; |r|^2
-  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->nsolve, c->V, sc, c->partials, bb, c->sms, st)) != cudaSuccess) return e;
+  if ((e = launch_cg_update_r(c->wprec, c->r, c->q, c->nsolve, c->V, sc, c->partials, bb, st)) != cudaSuccess) return e;
   // s = D^dag r, gamma' = |s|^2
   if ((e = op(c, c->r, c->s, 1, EPI_PLAIN, none_field(), &sc->gamma_new, TK_DSLASH_B, &sc->status, st)) !=
       cudaSuccess)
     return e;
   // x += alpha p; p = s + beta p; loop condition
-  return launch_cg_update_xp(c->wprec, c->x, c->p, c->p, c->s, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb,
-                             c->sms, st);
+  return launch_cg_update_xp(c->wprec, c->x, c->p, c->p, c->s, c->nsolve, c->V, sc, c->partials, use_cond, cond, bb, st);
 }
 
 cudaError_t plain_epilogue(wd_ctx* c, cudaStream_t st) {

@@ -433,9 +433,8 @@ cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond
 #define WD_STRIDE(K) K<<<stride_grid(K, n, block), block, 0, st>>>
 
 cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, CgScalars* sc, double* partials,
-                               int block, int sms, cudaStream_t st, int gamma_from_rr) {
+                               int block, cudaStream_t st, int gamma_from_rr) {
   const int g = gamma_from_rr;
-  (void)sms;
   switch (prec) {
     case SP64: WD_STRIDE(cg_update_r_kernel<P64>)(view<P64>(r), view<P64>(q), n, V, sc, partials, g); break;
     case SP32: WD_STRIDE(cg_update_r_kernel<P32>)(view<P32>(r), view<P32>(q), n, V, sc, partials, g); break;
@@ -447,9 +446,8 @@ cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, C
 
 cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr d, FieldPtr p, FieldPtr s, int n, int V,
                                 CgScalars* sc, double* partials, int use_cond, unsigned long long cond, int block,
-                                int sms, cudaStream_t st) {
+                                cudaStream_t st) {
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
-  (void)sms;
   switch (prec) {
     case SP64:
       WD_STRIDE(cg_update_xp_kernel<P64>)(view<P64>(x), view<P64>(d), view<P64>(p), view<P64>(s), n, V, sc, partials,

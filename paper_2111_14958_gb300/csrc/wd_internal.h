@@ -117,14 +117,14 @@ cudaError_t launch_cg_init(CgScalars* sc, int reset_iter, cudaStream_t st);
 // gamma_from_rr: the search direction starts as r itself (the paper's form), so gamma = |r|^2
 cudaError_t launch_cg_check(CgScalars* sc, int use_cond, unsigned long long cond, cudaStream_t st,
                             int gamma_from_rr = 0);
-// sms: SM count of the device (sizes the grid of the element-wise FP64/FP32 kernels)
+// grid-stride launches sized to one wave of resident blocks
 // gamma_from_rr: |r|^2 after the update is also the next gamma (the paper's form)
 cudaError_t launch_cg_update_r(int prec, FieldPtr r, FieldPtr q, int n, int V, CgScalars* sc, double* partials,
-                               int block, int sms, cudaStream_t st, int gamma_from_rr = 0);
+                               int block, cudaStream_t st, int gamma_from_rr = 0);
 // x += alpha d; p = s + beta p (d = p in the CGLS arrangement, d = D^dag p in the paper's form)
 cudaError_t launch_cg_update_xp(int prec, FieldPtr x, FieldPtr d, FieldPtr p, FieldPtr s, int n, int V,
                                 CgScalars* sc, double* partials, int use_cond, unsigned long long cond, int block,
-                                int sms, cudaStream_t st);
+                                cudaStream_t st);
 // Mixed precision (inner W = SP32 or SP16 spinors, x_lo in SP32, outer FP64)
 cudaError_t launch_mp_update_rx(int precw, FieldPtr r, FieldPtr q, FieldPtr p, FieldPtr xlo, int n, int V,
                                 CgScalars* sc, double* partials, int use_cond, unsigned long long upd, int block,
