@@ -401,6 +401,11 @@ def _mixed_32x64(wd, dev, stream):
         rec["rel_diff_vs_f64_solution"] = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
         rec["speedup_vs_f64"] = out["plain_f64"]["ms"] / rec["ms"]
         out[name] = rec
+        # the same solve with a reliable update every 100x drop of |r| instead of 10x
+        op.set_option(wd.WD_OPT_RELIABLE_DELTA, 0.01)
+        _, rec = _timed_solve(op, wd, eta, TOL, repeats=2)
+        rec["speedup_vs_f64"] = out["plain_f64"]["ms"] / rec["ms"]
+        out[name + "_delta_0.01"] = rec
         op.close()
     ref.close()
     return out

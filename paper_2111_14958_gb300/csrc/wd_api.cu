@@ -1157,7 +1157,7 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
   c->geom.V = (int)V;
   for (int i = 0; i < 4; ++i) c->geom.bc[i] = bc[i];
   c->stream = (cudaStream_t)cuda_stream;
-  c->delta = 0.1;
+  c->delta = 0.1;  // a reliable update each time |r| has dropped 10x
   c->use_graph = 1;
   c->block_blas = 256;
   c->max_restarts = 5;
