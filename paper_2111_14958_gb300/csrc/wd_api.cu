@@ -1,5 +1,5 @@
 // C ABI of the Wilson-Dirac CG library: context management, gauge loading, operator application
-// and the CG drivers (plain FP64/FP32 and mixed precision with reliable updates).
+// and the CG solvers (plain FP64/FP32 and mixed precision with reliable updates).
 //
 // The CG iteration runs as one CUDA graph per context: a prologue (r = eta - D x, p = D^dag r,
 // convergence check), a device-side while node whose body is one CG iteration (the body's last
