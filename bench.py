@@ -41,6 +41,7 @@ GAUGE_SEED, SOURCE_SEED = 1, 2
 BC = (1, 1, 1, -1)
 FLOPS_PER_SITE = 1320          # hopping part of one dslash, the usual convention
 BYTES_SITE_F64_18 = 192 + 576 + 192  # spinor in + 4 links + spinor out (FP64, 18-real links)
+BLAS_FLOPS_PER_SITE_ITER = 288        # per CG iteration: 3 norms + 3 axpy-type updates, 24 FMA each
 
 
 def _peaks():
@@ -210,7 +211,7 @@ def run_native(args, rank, world):
         return wd.cg_solve(op.ctx, etad, x, TOL, MAXIT)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters_seen, res_seen = [], []
+    iters_seen, res_seen, loop_ms_seen = [], [], []
     # clocks are sampled from the start of the warm-up to the end of the timed region
     with ClockSampler(local) as clk:
         for _ in range(max(args.warmup, 3)):
@@ -225,6 +226,7 @@ def run_native(args, rank, world):
             ev[i][1].record(stream)
             iters_seen.append(it)
             res_seen.append(rr)
+            loop_ms_seen.append(op.stats()["loop_ms"])  # host read of the finished solve's record
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -232,9 +234,14 @@ def run_native(args, rank, world):
     ms = max_over_ranks(statistics.mean(step_ms), world, dev)
     stats = op.stats()
     iters = iters_seen[-1]
-    # our kernels per step: gauge load 1, parameter set 1, pack 2, prologue 4, 4 per iteration,
-    # true residual 1, unpack 1 (per restart: prologue + epilogue again)
-    launches = sum(10 + 4 * it for it in iters_seen)
+    # our kernels per step: gauge load 1, parameter set 1, pack 2, unpack 1, and per pass of the
+    # solver (1 + restarts) prologue 4 (init, two dslash, check) + true residual 1 + the loop: one
+    # persistent kernel, or 4 per iteration (two dslash, two updates)
+    passes = 1 + stats["restarts"]
+    if stats["loop_mode"] == 2:
+        launches = len(iters_seen) * (5 + 6 * passes)
+    else:
+        launches = sum(5 + 5 * passes + 4 * it for it in iters_seen)
 
     # dominant kernel: the FP64 dslash as the solver launches it, timed with CUDA events on the
     # solver's stream over 200 back-to-back launches on the resident workload
@@ -245,20 +252,41 @@ def run_native(args, rank, world):
     achieved_gbs = BYTES_SITE_F64_18 * V / (dslash_ms * 1e-3) / 1e9
     share = 2 * iters * dslash_ms / ms
     traffic = _profile_traffic("dslash_f64_14x4")
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "dslash_kernel<FP64, 18r> (q = D p with fused |q|^2)",
-                "algorithmic": f"{FLOPS_PER_SITE} flop/site x {V} sites per launch; "
-                               f"{BYTES_SITE_F64_18} B/site",
-                "peak_source": "FP64 FMA throughput measured on GB300 (1.202 TFLOP/s)",
-                "achieved_hbm_gbs": achieved_gbs, "launch_ms": dslash_ms,
-                "share_of_step": share}
+    dslash_roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                   "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                   "kernel": "dslash_kernel<FP64, 18r> (q = D p with fused |q|^2), the launch shape the "
+                             "solver uses",
+                   "algorithmic": f"{FLOPS_PER_SITE} flop/site x {V} sites per launch; "
+                                  f"{BYTES_SITE_F64_18} B/site",
+                   "peak_source": "FP64 FMA throughput measured on GB300 (1.202 TFLOP/s)",
+                   "achieved_hbm_gbs": achieved_gbs, "launch_ms": dslash_ms,
+                   "share_of_step": share}
+    if stats["loop_mode"] == 2:
+        # the whole CG loop is one persistent kernel: its own launch is the unit. FP64 flops per site
+        # and iteration: two dslash (2 x 1320) + the BLAS-1 steps (|q|^2, |s|^2, r -= alpha q with
+        # |r|^2, x += alpha p, p = s + beta p: 6 x 24 real FMA = 288)
+        loop_ms = statistics.mean(loop_ms_seen)
+        loop_flops = (2 * FLOPS_PER_SITE + BLAS_FLOPS_PER_SITE_ITER) * V * iters
+        ach = loop_flops / (loop_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": _profile_traffic("cg_loop_f64_14x4"),
+                    "kernel": f"cg_loop_kernel<FP64> (the whole CG loop in one cooperative launch: {iters} "
+                              f"iterations of q = D p, r update, s = D^dag r, x and p update)",
+                    "algorithmic": f"(2 x {FLOPS_PER_SITE} dslash + {BLAS_FLOPS_PER_SITE_ITER} BLAS-1) flop/site x "
+                                   f"{V} sites x {iters} iterations per launch",
+                    "peak_source": "FP64 FMA throughput measured on GB300 (1.202 TFLOP/s)",
+                    "launch_ms": loop_ms, "share_of_step": loop_ms / ms,
+                    "dslash_standalone": dslash_roof}
+    else:
+        roofline = dslash_roof
 
     out = {
         "metric": "CG time-to-1e-10 residual", "value": ms, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(), "iterations": iters, "true_rel_residual": res_seen[-1],
+        "cg_loop": {0: "host loop", 1: "CUDA graph with a device-side while node",
+                    2: "one persistent cooperative kernel"}[stats["loop_mode"]],
         "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
         "solve_stats": stats,
     }

@@ -71,8 +71,13 @@ enum {
                                 1e-10: 0.01 takes the iterations of 0.1 with half the updates
                                 (10-12 % faster); FP16 inner solves need more iterations below
                                 about 0.003                                                      */
-  WD_OPT_USE_GRAPH = 2,      /* 1 (default): run the CG loop as a CUDA graph with a device-side
-                                while node; 0: plain stream launches with a host poll           */
+  WD_OPT_USE_GRAPH = 2,      /* how cg_solve runs the CG loop: 0 plain stream launches with a
+                                host poll; 1 a CUDA graph with a device-side while node; 2 one
+                                persistent cooperative kernel for the whole loop (plain FP64 /
+                                FP32 CGLS on the lexicographic layout; other contexts use the
+                                graph); 3 (default) automatic: the persistent kernel for plain
+                                FP32 at every volume and plain FP64 up to 48,000 sites, where it
+                                measured faster on GB300, the graph otherwise                  */
   WD_OPT_BLOCK_DSLASH = 3,   /* threads per block of the dslash kernel, 32..256 (0 = 256)       */
   WD_OPT_BLOCK_BLAS = 4,     /* threads per block of the BLAS-1 kernels (0 = default)            */
   WD_OPT_MAX_RESTARTS = 5,   /* max restarts from the true residual (default 5)                  */
@@ -107,8 +112,12 @@ typedef struct {
   int dslash_calls;        /* dslash applications, all precisions                              */
   int dslash_calls_f64;    /* of which in FP64                                                  */
   int status;              /* wd_status of the solve                                            */
+  int loop_mode;           /* how the CG loop ran: 0 host loop, 1 CUDA graph, 2 persistent kernel */
+  int reserved;
   double true_rel_residual;/* ||eta - D x|| / ||eta||, recomputed in the outer precision         */
   double solve_ms;         /* host wall time of cg_solve                                          */
+  double loop_ms;          /* persistent kernel (loop_mode 2): its device time (CUDA events), all
+                              passes; 0 for the other modes                                     */
 } wd_stats;
 
 /* Statistics of the last cg_solve_multi / wd_apply_multi, filled by wd_get_multi_stats. */

@@ -115,6 +115,44 @@ __device__ __forceinline__ void hops_rt(const DslashArgs<SP, C12>& a, R mk, int 
   }
 }
 
+// One site of out = D in (or b - D in); returns |out(s)|^2.
+template <int SP, bool C12, bool DAG, int EPI>
+__device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int s) {
+  typedef typename RealOf<SP>::type R;
+  const int V = a.g.V;
+  int c[4];
+  {
+    int r = s;
+    c[0] = r % a.g.L[0];
+    r /= a.g.L[0];
+    c[1] = r % a.g.L[1];
+    r /= a.g.L[1];
+    c[2] = r % a.g.L[2];
+    c[3] = r / a.g.L[2];
+  }
+  const R mk = a.kappa_dev ? (R)(-*a.kappa_dev) : a.mkappa;
+  Cx<R> acc[12];
+  load_spinor(a.in, s, V, acc);
+  // D: forward (1 - gamma), backward (1 + gamma); D^dagger: the reverse
+  constexpr int SF = DAG ? +1 : -1;
+  if constexpr (SP == PDF) {
+    hops_rt<SF>(a, mk, s, c, acc);
+  } else {
+    hop_pair<0, SF>(a, mk, s, c, acc);
+    hop_pair<1, SF>(a, mk, s, c, acc);
+    hop_pair<2, SF>(a, mk, s, c, acc);
+    hop_pair<3, SF>(a, mk, s, c, acc);
+  }
+  if (EPI == EPI_RESID) {
+    Cx<R> bv[12];
+    load_spinor(a.b, s, V, bv);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cx<R>(bv[i].re - acc[i].re, bv[i].im - acc[i].im);
+  }
+  store_spinor(a.out, s, V, acc);
+  return norm2_site(acc);
+}
+
 // Occupancy: the kernel is latency-bound at large volumes (memory-level parallelism comes from
 // resident warps), so registers are capped for 3 blocks of 256 threads per SM in FP32/FP16
 // (24 warps) and 2 in FP64 (whose FP64 pipe saturates with few warps).
@@ -127,44 +165,14 @@ struct DslashMinBlocks {
 template <int SP, bool C12, bool DAG, int EPI, bool NORM>
 __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
     dslash_kernel(const DslashArgs<SP, C12> a) {
-  typedef typename RealOf<SP>::type R;
   if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
   const int V = a.g.V;
   double n2 = 0.0;
   // grid-stride over sites: the launch is one wave of resident blocks, so the fused norm has one
   // partial per resident block and no block waits in a queue
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
-    int c[4];
-    {
-      int r = s;
-      c[0] = r % a.g.L[0];
-      r /= a.g.L[0];
-      c[1] = r % a.g.L[1];
-      r /= a.g.L[1];
-      c[2] = r % a.g.L[2];
-      c[3] = r / a.g.L[2];
-    }
-    const R mk = a.kappa_dev ? (R)(-*a.kappa_dev) : a.mkappa;
-    Cx<R> acc[12];
-    load_spinor(a.in, s, V, acc);
-    // D: forward (1 - gamma), backward (1 + gamma); D^dagger: the reverse
-    constexpr int SF = DAG ? +1 : -1;
-    if constexpr (SP == PDF) {
-      hops_rt<SF>(a, mk, s, c, acc);
-    } else {
-      hop_pair<0, SF>(a, mk, s, c, acc);
-      hop_pair<1, SF>(a, mk, s, c, acc);
-      hop_pair<2, SF>(a, mk, s, c, acc);
-      hop_pair<3, SF>(a, mk, s, c, acc);
-    }
-    if (EPI == EPI_RESID) {
-      Cx<R> bv[12];
-      load_spinor(a.b, s, V, bv);
-#pragma unroll
-      for (int i = 0; i < 12; ++i) acc[i] = cx<R>(bv[i].re - acc[i].re, bv[i].im - acc[i].im);
-    }
-    store_spinor(a.out, s, V, acc);
-    if (NORM) n2 += norm2_site(acc);
+    const double v = dslash_site<SP, C12, DAG, EPI>(a, s);
+    if (NORM) n2 += v;
   }
   if (NORM) {
     double v[1] = {n2}, tot[1];
@@ -265,9 +273,10 @@ __device__ __forceinline__ void pair_hop(const DslashArgs<P64, C12>& a, double m
   }
 }
 
-template <bool C12, bool DAG, int EPI, bool NORM>
-__global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_pair_kernel(const DslashArgs<P64, C12> a) {
-  if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
+// All sites of out = D in (or b - D in) with two lanes per site, over the whole grid (grid-stride
+// on the warp's first site); returns this thread's share of |out|^2.
+template <bool C12, bool DAG, int EPI>
+__device__ __forceinline__ double pair_sites(const DslashArgs<P64, C12>& a) {
   const int V = a.g.V;
   const int hl = threadIdx.x & 1;
   double n2 = 0.0;
@@ -326,18 +335,271 @@ __global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_pair_kernel(const
       }
       a.out.p[(size_t)(3 * hl + col) * V + s] = make_double2(up.re, up.im);
       a.out.p[(size_t)(3 * (2 + hl) + col) * V + s] = make_double2(lo.re, lo.im);
-      if (NORM) {
-        n2 = fma(up.re, up.re, n2);
-        n2 = fma(up.im, up.im, n2);
-        n2 = fma(lo.re, lo.re, n2);
-        n2 = fma(lo.im, lo.im, n2);
-      }
+      n2 = fma(up.re, up.re, n2);
+      n2 = fma(up.im, up.im, n2);
+      n2 = fma(lo.re, lo.re, n2);
+      n2 = fma(lo.im, lo.im, n2);
     }
   }
+  return n2;
+}
+
+template <bool C12, bool DAG, int EPI, bool NORM>
+__global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_pair_kernel(const DslashArgs<P64, C12> a) {
+  if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
+  const double n2 = pair_sites<C12, DAG, EPI>(a);
   if (NORM) {
     double v[1] = {n2}, tot[1];
     if (grid_reduce<OpSum, 1>(v, a.partials, a.ticket, tot) && threadIdx.x == 0) *a.result = tot[0];
   }
+}
+
+// ---------------------------------------------------------------- persistent CG loop
+//
+// At the paper's volumes every kernel of a CG iteration costs a launch and a grid-reduction tail
+// of several microseconds, comparable to its work. This kernel runs the whole CGLS loop (the four
+// phases of each iteration) in one cooperative launch: the grid is one wave of resident blocks,
+// the phases are separated by a grid barrier, and each norm is summed by every block from the
+// block partials in one fixed order, so all blocks hold the same scalars and the results are
+// reproducible. The launch is cooperative, so all blocks are resident and the barrier always
+// completes; its wait is still bounded: past the limit the kernel records an error and stops.
+
+struct LoopSync {
+  unsigned* bar;  // [0] arrivals, [1] generation
+  int* err;       // set to 1 when a barrier wait gave up
+};
+
+constexpr long long kBarrierSpinLimit = 1LL << 26;  // x 64 ns sleep: about 4 s
+
+// All blocks arrive, then continue. Returns false (everywhere, eventually) if a wait gave up.
+__device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = y.bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(y.bar, 1u);
+    int good = 1;
+    if (arrived == gridDim.x - 1) {
+      y.bar[0] = 0u;
+      __threadfence();
+      atomicAdd(y.bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g0) {
+        if (++spins > kBarrierSpinLimit || *(volatile int*)y.err) {
+          atomicExch(y.err, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good && !*(volatile int*)y.err;
+  }
+  __syncthreads();
+  return ok;
+}
+
+// Sum over the grid of one value per thread: block partial, barrier, then every block sums the
+// partials in the same order (lanes stride over them, then a fixed shuffle tree).
+__device__ __forceinline__ bool loop_sum(double v, double* partials, const LoopSync& y, double* out) {
+  __shared__ double smem[32];
+  __shared__ double total;
+  double w[1] = {v};
+  block_reduce<OpSum, 1>(w, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = w[0];
+    __threadfence();
+  }
+  if (!grid_barrier(y)) return false;
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) a += __ldcg(partials + b);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (threadIdx.x == 0) total = a;
+  }
+  __syncthreads();
+  *out = total;
+  return true;
+}
+
+template <int SP, bool C12>
+struct LoopArgs {
+  DslashArgs<SP, C12> dq;  // q = D p
+  DslashArgs<SP, C12> ds;  // s = D^dag r
+  SpinorRef<SP> x, r, p, q, s;
+  int n;                   // sites
+  CgScalars* sc;
+  double* partials;        // 3 x gridDim.x
+  LoopSync y;
+};
+
+// The dslash phases of the loop: one thread per site, or (FP64, PAIR) two lanes per site.
+template <int SP, bool C12, bool DAG, bool PAIR>
+__device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int n, int t0, int tstep) {
+  if constexpr (SP == P64 && PAIR) {
+    return pair_sites<C12, DAG, EPI_PLAIN>(d);
+  } else {
+    double v = 0.0;
+    for (int i = t0; i < n; i += tstep) v += dslash_site<SP, C12, DAG, EPI_PLAIN>(d, i);
+    return v;
+  }
+}
+
+template <int SP, bool C12, bool PAIR>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value) cg_loop_kernel(const LoopArgs<SP, C12> a) {
+  typedef typename RealOf<SP>::type R;
+  CgScalars* sc = a.sc;
+  if (sc->status != ST_RUNNING) return;  // uniform over the grid
+  const int n = a.n, V = a.dq.g.V, G = gridDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  double gamma = sc->gamma, rr = sc->rr;
+  const double tol2e = sc->tol2 * sc->eta2;
+  int iter = sc->iter, status = ST_RUNNING;
+  const int maxit = sc->maxit;
+  double alpha = 0.0, beta = 0.0;
+  for (;;) {
+    // q = D p, |q|^2
+    double v = loop_dslash<SP, C12, false, PAIR>(a.dq, n, t0, tstep);
+    double qq;
+    if (!loop_sum(v, a.partials, a.y, &qq)) break;
+    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / qq;
+    const R ar = (R)alpha;
+    // r -= alpha q, |r|^2
+    v = 0.0;
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> rv[12], qv[12];
+      load_spinor(a.r, i, V, rv);
+      load_spinor(a.q, i, V, qv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        rv[c].re = fma(-ar, qv[c].re, rv[c].re);
+        rv[c].im = fma(-ar, qv[c].im, rv[c].im);
+      }
+      store_spinor(a.r, i, V, rv);
+      v += norm2_site(rv);
+    }
+    if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (!isfinite(rr)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    const bool conv = rr <= tol2e;
+    // s = D^dag r, |s|^2 (not needed once converged)
+    double gnew = 0.0;
+    if (!conv) {
+      v = loop_dslash<SP, C12, true, PAIR>(a.ds, n, t0, tstep);
+      if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
+    }
+    const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
+    beta = do_p ? gnew / gamma : 0.0;
+    const R br = (R)beta;
+    // x += alpha p; p = s + beta p
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> xv[12], pv[12];
+      load_spinor(a.x, i, V, xv);
+      load_spinor(a.p, i, V, pv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fma(ar, pv[c].re, xv[c].re);
+        xv[c].im = fma(ar, pv[c].im, xv[c].im);
+      }
+      store_spinor(a.x, i, V, xv);
+      if (do_p) {
+        Cx<R> sv[12];
+        load_spinor(a.s, i, V, sv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          pv[c].re = fma(br, pv[c].re, sv[c].re);
+          pv[c].im = fma(br, pv[c].im, sv[c].im);
+        }
+        store_spinor(a.p, i, V, pv);
+      }
+    }
+    iter += 1;
+    if (conv) {
+      status = ST_CONVERGED;
+      break;
+    }
+    if (!do_p) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    gamma = gnew;
+    if (iter >= maxit) {
+      status = ST_MAXIT;
+      break;
+    }
+    if (!grid_barrier(a.y)) break;  // p complete before the next dslash reads its neighbours
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->alpha = alpha;
+    sc->beta = beta;
+  }
+}
+
+template <int SP, bool C12, bool PAIR>
+static cudaError_t loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+  LoopArgs<SP, C12> a;
+  for (DslashArgs<SP, C12>* d : {&a.dq, &a.ds}) {
+    memcpy(&d->g, &c.g, sizeof(Geom));
+    d->u.p = reinterpret_cast<decltype(d->u.p)>(c.u.p);
+    d->mkappa = (typename RealOf<SP>::type)(-c.kappa);
+    d->kappa_dev = c.kappa_dev;
+    d->skip = nullptr;
+    d->partials = nullptr;
+    d->ticket = nullptr;
+    d->result = nullptr;
+  }
+  a.dq.in = make_ref<SP>(c.p, c.g.V);
+  a.dq.out = make_ref<SP>(c.q, c.g.V);
+  a.dq.b = make_ref<SP>(FieldPtr{}, c.g.V);
+  a.ds.in = make_ref<SP>(c.r, c.g.V);
+  a.ds.out = make_ref<SP>(c.s, c.g.V);
+  a.ds.b = a.dq.b;
+  a.x = make_ref<SP>(c.x, c.g.V);
+  a.r = make_ref<SP>(c.r, c.g.V);
+  a.p = make_ref<SP>(c.p, c.g.V);
+  a.q = make_ref<SP>(c.q, c.g.V);
+  a.s = make_ref<SP>(c.s, c.g.V);
+  a.n = c.g.V;
+  a.sc = c.sc;
+  a.partials = c.partials;
+  a.y.bar = c.bar;
+  a.y.err = c.err;
+  auto k = cg_loop_kernel<SP, C12, PAIR>;
+  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
+  const int need = grid_for(PAIR ? 2 * c.g.V : c.g.V, c.block);
+  if (need < grid) grid = need;
+  if (grid > c.max_grid) grid = c.max_grid;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+}
+
+cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1) return cudaErrorInvalidValue;
+  if (c.x.prec != c.r.prec || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec)
+    return cudaErrorInvalidValue;
+  if (c.r.prec == SP64) {
+    if (c.u.prec != SP64) return cudaErrorInvalidValue;
+    return c.variant == 1 ? loop_launch_t<P64, false, true>(c, st) : loop_launch_t<P64, false, false>(c, st);
+  }
+  if (c.r.prec == SP32 && c.u.prec == SP32)
+    return c.u.c12 ? loop_launch_t<P32, true, false>(c, st) : loop_launch_t<P32, false, false>(c, st);
+  return cudaErrorInvalidValue;
 }
 
 template <int SP, bool C12, bool DAG, int EPI>

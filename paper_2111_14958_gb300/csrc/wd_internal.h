@@ -97,6 +97,25 @@ struct DslashCall {
 // Launchers. Each returns cudaGetLastError() after the launch.
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st);
 
+// The whole plain CG loop (CGLS, lexicographic layout, FP64 or FP32) as one cooperative launch,
+// from the state the prologue leaves in sc; it writes status, iterations and scalars back.
+struct CgLoopCall {
+  GeomH g;
+  GaugePtr u;
+  FieldPtr x, r, p, q, s;
+  double kappa;
+  const double* kappa_dev;
+  CgScalars* sc;
+  double* partials;  // >= 3 * max_grid
+  unsigned* bar;     // two counters, zero at the first launch (the kernel leaves them reusable)
+  int* err;          // zero; set to 1 if a barrier wait gave up
+  int block;
+  int max_grid;
+  int variant;  // FP64: 1 = the dslash phases use two lanes per site
+};
+cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st);
+constexpr int kLoopMaxGrid = 8192;
+
 // eo: null for lexicographic storage, else the geometry of a parity-ordered context.
 // canonical complex128 [V][12] -> field; optional |src|^2 into red
 cudaError_t launch_pack(const double* canon, FieldPtr out, int V, const GeomH* eo, Red red, int block,

@@ -88,7 +88,9 @@ class WdStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
                 ("dslash_calls_f64", ctypes.c_int), ("status", ctypes.c_int),
-                ("true_rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("loop_mode", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("loop_ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

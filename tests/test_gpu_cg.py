@@ -264,3 +264,58 @@ def test_paper_form_uses_the_initial_guess_and_is_rejected_where_unsupported():
         mixed.set_option(wd.WD_OPT_CG_FORM, 1)
     assert e.value.status == wd.WD_EINVAL
     mixed.close()
+
+
+# ---------------------------------------------------------------- persistent (cooperative) CG loop
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 5), (14, 14, 14, 14)])
+@pytest.mark.parametrize("prec", ["f64", "f32c12", "f32"])
+def test_persistent_loop_matches_oracle_and_graph(dims, prec):
+    wd = require_gpu()
+    U, eta = fields(dims)
+    p, tol, c12 = {"f64": (wd.WD_PREC_F64, 1e-10, False), "f32c12": (wd.WD_PREC_F32, 1e-6, True),
+                   "f32": (wd.WD_PREC_F32, 1e-6, False)}[prec]
+    got = {}
+    for mode in (1, 2):
+        x, iters, res, status, stats, _, _ = _solve(wd, dims, 0.12, p, tol, U=U, eta=eta, c12=c12,
+                                                    options={wd.WD_OPT_USE_GRAPH: mode})
+        assert status == wd.WD_OK
+        assert ocg.true_residual(U, eta, x, 0.12) <= tol * 1.05
+        assert abs(res - ocg.true_residual(U, eta, x, 0.12)) < max(1e-12, 0.05 * tol)
+        got[mode] = (x, iters)
+    # same algorithm, reductions summed in another fixed order: same iterations within one
+    assert abs(got[1][1] - got[2][1]) <= 1
+    assert rel(got[2][0], got[1][0]) < 1e3 * tol
+
+
+def test_persistent_loop_edge_cases():
+    wd = require_gpu()
+    dims = (4, 4, 4, 8)
+    U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_F64)
+    op.load_gauge(to_dev(U))
+    op.set_option(wd.WD_OPT_USE_GRAPH, 2)
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10, maxit=5)       # iteration limit
+    assert st == wd.WD_NOT_CONVERGED and iters == 5
+    x, iters, res, st = op.solve(to_dev(np.zeros_like(eta)), tol=1e-10)  # zero source
+    assert st == wd.WD_OK and iters == 0 and float(torch.abs(x).max()) == 0.0
+    x1, _, _, _ = op.solve(to_dev(eta), tol=1e-5)
+    x2, it2, r2, st2 = op.solve(to_dev(eta), x0=x1, tol=1e-10)           # initial guess
+    assert st2 == wd.WD_OK and ocg.true_residual(U, eta, to_np(x2), 0.12) <= 1e-10
+    bad = eta.copy()
+    bad[0, 0, 0, 0, 0, 0] = np.nan
+    x, iters, res, st = op.solve(to_dev(bad), tol=1e-10)                 # breakdown
+    assert st == wd.WD_BREAKDOWN
+    x3, it3, r3, st3 = op.solve(to_dev(eta), tol=1e-10)                  # the context still works
+    assert st3 == wd.WD_OK and ocg.true_residual(U, eta, to_np(x3), 0.12) <= 1e-10
+    with pytest.raises(wd.WdError):
+        op.set_option(wd.WD_OPT_USE_GRAPH, 4)
+    op.close()
+    # contexts the persistent loop does not serve fall back to the graph solver
+    for prec, flag in ((wd.WD_PREC_MIXED_F32, 0), (wd.WD_PREC_F64, wd.WD_EVEN_ODD)):
+        op = wd.WilsonDirac(dims, 0.12, BC, prec | flag)
+        op.load_gauge(to_dev(U), compress12=prec != wd.WD_PREC_F64)
+        op.set_option(wd.WD_OPT_USE_GRAPH, 2)
+        x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+        assert st == wd.WD_OK and ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10
+        op.close()
