@@ -550,14 +550,16 @@ wd_status build_graph(wd_ctx* c) {
 
 // Run one solve attempt without graphs: direct launches, the host reads the status each step.
 // The plain CGLS loop as one cooperative kernel between the usual prologue and epilogue.
-// Volume up to which the persistent FP64 loop measured faster than the graph on GB300 (14^4:
-// 4 %; 16^4 and above: the graph, by 1-5 %). FP32 was faster at every volume measured (8^4 to 32^4).
-constexpr int kPersistentF64MaxSites = 48000;
+// Volume up to which the persistent loop measured faster than the graph on GB300: plain FP64
+// (14^4: 4 %; 16^4 and above: the graph, by 1-5 %) and mixed precision (8^4: 5-8 %, 14^4: 2-3 %;
+// 24^3x48 and above: level or the graph). Plain FP32 was faster at every volume (8^4 to 32^4).
+constexpr int kPersistentMaxSites = 48000;
 
 bool persistent_loop(const wd_ctx* c) {
-  if (is_mixed(c->precision) || c->eo || c->cg_form) return false;
+  if (c->eo || c->cg_form) return false;
   if (c->use_graph == 2) return true;
-  return c->use_graph == 3 && (c->wprec == SP32 || c->V <= kPersistentF64MaxSites);
+  const bool plain32 = !is_mixed(c->precision) && c->wprec == SP32;
+  return c->use_graph == 3 && (plain32 || c->V <= kPersistentMaxSites);
 }
 
 wd_status run_persistent(wd_ctx* c, double* loop_ms) {
@@ -595,6 +597,52 @@ wd_status run_persistent(wd_ctx* c, double* loop_ms) {
   float ms = 0.f;
   WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   *loop_ms += ms;
+  return WD_OK;
+}
+
+// Mixed precision: the inner loop as a cooperative kernel that returns whenever a reliable update
+// is due; the update runs as its separate kernels and the loop resumes in the same iteration.
+wd_status run_mixed_persistent(wd_ctx* c, double* loop_ms) {
+  WD_CUDA(mixed_prologue(c, c->stream, 0, 0));
+  CgLoopCall L;
+  memset(&L, 0, sizeof(L));
+  L.g = c->geom;
+  L.u = gauge_for(c, c->wprec);
+  L.x = c->x;
+  L.r = c->r;
+  L.p = c->p;
+  L.q = c->q;
+  L.s = c->s;
+  L.kappa = c->kappa;
+  L.kappa_dev = &c->sc->kappa;
+  L.sc = c->sc;
+  L.partials = c->loop_partials;
+  L.bar = c->loop_sync;
+  L.err = reinterpret_cast<int*>(c->loop_sync + 2);
+  L.block = dslash_block(c, c->wprec);
+  L.max_grid = kLoopMaxGrid;
+  for (int launch = 0;; ++launch) {
+    L.start_b = launch > 0;
+    WD_CUDA(cudaEventRecord(c->ev0, c->stream));
+    WD_CUDA(launch_cg_mixed_loop(L, c->stream));
+    WD_CUDA(cudaEventRecord(c->ev1, c->stream));
+    WD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+    WD_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned flags[4];
+    WD_CUDA(cudaMemcpy(flags, c->loop_sync, sizeof(flags), cudaMemcpyDeviceToHost));
+    if (flags[2] != 0) {
+      WD_CUDA(cudaMemset(c->loop_sync, 0, sizeof(flags)));
+      return fail(WD_ECUDA, "persistent CG loop: a grid barrier wait gave up");
+    }
+    float ms = 0.f;
+    WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    *loop_ms += ms;
+    if (!c->sc_host->need_update) break;  // converged, iteration limit or breakdown
+    WD_CUDA(mixed_update(c, c->stream));
+  }
+  WD_CUDA(mixed_epilogue(c, c->stream));
+  WD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
   return WD_OK;
 }
 
@@ -1535,7 +1583,7 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
   int status = ST_RUNNING;
   for (;;) {
     if (persistent) {
-      if ((st = run_persistent(c, &loop_ms)) != WD_OK) return st;
+      if ((st = mixed ? run_mixed_persistent(c, &loop_ms) : run_persistent(c, &loop_ms)) != WD_OK) return st;
     } else if (c->use_graph) {
       WD_CUDA(cudaGraphLaunch(c->exec, c->stream));
       WD_CUDA(cudaStreamSynchronize(c->stream));

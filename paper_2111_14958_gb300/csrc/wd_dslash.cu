@@ -551,6 +551,179 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
   }
 }
 
+// The inner loop of the mixed-precision solver (FP32 or FP16 vectors, x_lo in FP32) in one
+// cooperative launch. Phase A: q = D p, |q|^2; r_lo -= alpha q, x_lo += alpha p, |r_lo|^2, and
+// the reliable-update test. Phase B: s = D^dag r_lo, |s|^2; p = s + beta p. The kernel starts at A
+// (or at B right after a reliable update) and returns as soon as an update is due or the loop
+// ends, leaving the same scalars and flags as the separate kernels of the graph solver.
+template <int SPW, bool C12>
+struct MixedLoopArgs {
+  DslashArgs<SPW, C12> dq;  // q = D p
+  DslashArgs<SPW, C12> ds;  // s = D^dag r
+  SpinorRef<SPW> r, p, q, s;
+  SpinorRef<P32> xlo;
+  int n;
+  int start_b;
+  CgScalars* sc;
+  double* partials;  // 3 x gridDim.x
+  LoopSync y;
+};
+
+template <int SPW, bool C12>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SPW>::value)
+    cg_mixed_loop_kernel(const MixedLoopArgs<SPW, C12> a) {
+  CgScalars* sc = a.sc;
+  const int st_in = sc->status;
+  if (st_in != ST_RUNNING && !(a.start_b && st_in == ST_CONVERGED)) return;  // uniform over the grid
+  const int n = a.n, V = a.dq.g.V, G = gridDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  double gamma = sc->gamma, rr = sc->rr, alpha = sc->alpha, beta = sc->beta;
+  const double tol2e = sc->tol2 * sc->eta2, d2ref = sc->delta2 * sc->rr_ref;
+  int iter = sc->iter, status = st_in, need = 0;
+  const int maxit = sc->maxit;
+  bool phase_b = a.start_b != 0;
+  for (;;) {
+    if (phase_b) {
+      // s = D^dag r_lo, gamma' = |s|^2 (skipped once the last update converged)
+      double gnew = 0.0;
+      if (status == ST_RUNNING) {
+        double v = 0.0;
+        for (int i = t0; i < n; i += tstep) v += dslash_site<SPW, C12, true, EPI_PLAIN>(a.ds, i);
+        if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
+      }
+      const bool do_p = status == ST_RUNNING && isfinite(gnew) && gamma > 0.0;
+      beta = do_p ? gnew / gamma : 0.0;
+      const float bf = (float)beta;
+      if (do_p) {
+        for (int i = t0; i < n; i += tstep) {
+          Cx<float> pv[12], sv[12];
+          load_spinor(a.p, i, V, pv);
+          load_spinor(a.s, i, V, sv);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            pv[c].re = fmaf(bf, pv[c].re, sv[c].re);
+            pv[c].im = fmaf(bf, pv[c].im, sv[c].im);
+          }
+          store_spinor(a.p, i, V, pv);
+        }
+      }
+      iter += 1;  // the iteration whose r update ran, including one that converged in its update
+      if (status != ST_RUNNING) break;
+      if (!do_p) {
+        status = ST_BREAKDOWN;
+        break;
+      }
+      gamma = gnew;
+      if (iter >= maxit) {
+        status = ST_MAXIT;
+        break;
+      }
+      if (!grid_barrier(a.y)) break;  // p complete before the next dslash reads its neighbours
+    }
+    phase_b = true;
+    // q = D p, |q|^2
+    double v = 0.0;
+    for (int i = t0; i < n; i += tstep) v += dslash_site<SPW, C12, false, EPI_PLAIN>(a.dq, i);
+    double qq;
+    if (!loop_sum(v, a.partials, a.y, &qq)) break;
+    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / qq;
+    const float af = (float)alpha;
+    // r_lo -= alpha q; x_lo += alpha p; |r_lo|^2
+    v = 0.0;
+    for (int i = t0; i < n; i += tstep) {
+      Cx<float> rv[12], qv[12], pv[12], xv[12];
+      load_spinor(a.r, i, V, rv);
+      load_spinor(a.q, i, V, qv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        rv[c].re = fmaf(-af, qv[c].re, rv[c].re);
+        rv[c].im = fmaf(-af, qv[c].im, rv[c].im);
+      }
+      store_spinor(a.r, i, V, rv);
+      v += norm2_site(rv);
+      load_spinor(a.p, i, V, pv);
+      load_spinor(a.xlo, i, V, xv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fmaf(af, pv[c].re, xv[c].re);
+        xv[c].im = fmaf(af, pv[c].im, xv[c].im);
+      }
+      store_spinor(a.xlo, i, V, xv);
+    }
+    if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (!isfinite(rr)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    need = (rr <= d2ref) || (rr <= tol2e);
+    if (need) break;  // the reliable update runs outside; the loop resumes at phase B
+    if (!grid_barrier(a.y)) break;  // r complete before D^dag reads its neighbours
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->alpha = alpha;
+    sc->beta = beta;
+    sc->need_update = need;
+    sc->no_update = !need;
+  }
+}
+
+template <int SPW, bool C12>
+static cudaError_t mixed_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+  MixedLoopArgs<SPW, C12> a;
+  for (DslashArgs<SPW, C12>* d : {&a.dq, &a.ds}) {
+    memcpy(&d->g, &c.g, sizeof(Geom));
+    d->u.p = reinterpret_cast<decltype(d->u.p)>(c.u.p);
+    d->mkappa = (float)(-c.kappa);
+    d->kappa_dev = c.kappa_dev;
+    d->skip = nullptr;
+    d->partials = nullptr;
+    d->ticket = nullptr;
+    d->result = nullptr;
+  }
+  a.dq.in = make_ref<SPW>(c.p, c.g.V);
+  a.dq.out = make_ref<SPW>(c.q, c.g.V);
+  a.dq.b = make_ref<SPW>(FieldPtr{}, c.g.V);
+  a.ds.in = make_ref<SPW>(c.r, c.g.V);
+  a.ds.out = make_ref<SPW>(c.s, c.g.V);
+  a.ds.b = a.dq.b;
+  a.r = make_ref<SPW>(c.r, c.g.V);
+  a.p = make_ref<SPW>(c.p, c.g.V);
+  a.q = make_ref<SPW>(c.q, c.g.V);
+  a.s = make_ref<SPW>(c.s, c.g.V);
+  a.xlo = make_ref<P32>(c.x, c.g.V);
+  a.n = c.g.V;
+  a.start_b = c.start_b;
+  a.sc = c.sc;
+  a.partials = c.partials;
+  a.y.bar = c.bar;
+  a.y.err = c.err;
+  auto k = cg_mixed_loop_kernel<SPW, C12>;
+  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
+  const int need = grid_for(c.g.V, c.block);
+  if (need < grid) grid = need;
+  if (grid > c.max_grid) grid = c.max_grid;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+}
+
+cudaError_t launch_cg_mixed_loop(const CgLoopCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1) return cudaErrorInvalidValue;
+  if (c.x.prec != SP32 || c.u.prec != SP32 || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec)
+    return cudaErrorInvalidValue;
+  if (c.r.prec == SP32) return c.u.c12 ? mixed_loop_launch_t<P32, true>(c, st) : mixed_loop_launch_t<P32, false>(c, st);
+  if (c.r.prec == SP16) return c.u.c12 ? mixed_loop_launch_t<P16, true>(c, st) : mixed_loop_launch_t<P16, false>(c, st);
+  return cudaErrorInvalidValue;
+}
+
 template <int SP, bool C12, bool PAIR>
 static cudaError_t loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   LoopArgs<SP, C12> a;

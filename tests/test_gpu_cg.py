@@ -319,3 +319,47 @@ def test_persistent_loop_edge_cases():
         x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
         assert st == wd.WD_OK and ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10
         op.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed32", "mixed16"])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 5), (14, 14, 14, 14)])
+def test_persistent_mixed_loop_matches_oracle_and_graph(prec, dims):
+    wd = require_gpu()
+    U, eta = fields(dims)
+    p = wd.WD_PREC_MIXED_F32 if prec == "mixed32" else wd.WD_PREC_MIXED_F16
+    got = {}
+    for mode in (1, 2):
+        x, iters, res, status, stats, _, _ = _solve(wd, dims, 0.12, p, 1e-10, U=U, eta=eta, c12=True,
+                                                    options={wd.WD_OPT_USE_GRAPH: mode})
+        assert status == wd.WD_OK
+        assert ocg.true_residual(U, eta, x, 0.12) <= 1e-10
+        assert abs(res - ocg.true_residual(U, eta, x, 0.12)) < 1e-12
+        assert stats["reliable_updates"] >= 1
+        got[mode] = (x, iters, stats)
+    assert got[2][2]["loop_mode"] == 2 and got[1][2]["loop_mode"] == 1
+    assert abs(got[1][1] - got[2][1]) <= 1
+    assert rel(got[2][0], got[1][0]) < 1e-7
+
+
+def test_persistent_mixed_loop_edge_cases():
+    wd = require_gpu()
+    dims = (4, 4, 4, 8)
+    U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_MIXED_F16)
+    op.load_gauge(to_dev(U), compress12=True)
+    op.set_option(wd.WD_OPT_USE_GRAPH, 2)
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10, maxit=7)       # iteration limit
+    assert st == wd.WD_NOT_CONVERGED and iters == 7
+    x, iters, res, st = op.solve(to_dev(np.zeros_like(eta)), tol=1e-10)  # zero source
+    assert st == wd.WD_OK and iters == 0
+    bad = eta.copy()
+    bad[1, 0, 0, 0, 2, 1] = np.inf
+    x, iters, res, st = op.solve(to_dev(bad), tol=1e-10)                 # breakdown
+    assert st == wd.WD_BREAKDOWN
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)                 # the context still works
+    assert st == wd.WD_OK and ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10
+    op.set_option(wd.WD_OPT_DF_UPDATES, 0)                               # FP64 reliable updates
+    op.load_gauge(to_dev(U), compress12=True)
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+    assert st == wd.WD_OK and ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10
+    op.close()
