@@ -73,13 +73,13 @@ enum {
                                 about 0.003                                                      */
   WD_OPT_USE_GRAPH = 2,      /* how cg_solve runs the CG loop: 0 plain stream launches with a
                                 host poll; 1 a CUDA graph with a device-side while node; 2 a
-                                persistent cooperative kernel for the loop (CGLS on the
-                                lexicographic layout; mixed precision returns to the host for
-                                each reliable update; even-odd contexts and the paper's CG form
-                                use the graph); 3 (default) automatic: the persistent kernel
-                                for plain FP32 at every volume and for FP64 and mixed precision
-                                up to 48,000 sites, where it measured faster on GB300, the
-                                graph otherwise                                                  */
+                                persistent cooperative kernel for the loop (CGLS; mixed
+                                precision returns to the host for each reliable update; mixed
+                                even-odd contexts and the paper's CG form use the graph); 3
+                                (default) automatic: the persistent kernel for plain FP32 on
+                                the lexicographic layout at every volume, and for the other
+                                cases it serves up to 48,000 sites, where it measured faster on
+                                GB300; the graph otherwise                                       */
   WD_OPT_BLOCK_DSLASH = 3,   /* threads per block of the dslash kernel, 32..256 (0 = 256)       */
   WD_OPT_BLOCK_BLAS = 4,     /* threads per block of the BLAS-1 kernels (0 = default)            */
   WD_OPT_MAX_RESTARTS = 5,   /* max restarts from the true residual (default 5)                  */

@@ -941,43 +941,51 @@ __device__ __forceinline__ void eo_hops_rt(const EoArgs<SP, C12>& a, R k0, int s
   }
 }
 
+// Half-site i of the output parity: out = [b -] ([self] + c * H in); returns |out|^2.
+template <int SP, bool C12, bool DAG, bool SELF, bool RESID>
+__device__ __forceinline__ double eo_site(const EoArgs<SP, C12>& a, int i) {
+  typedef typename RealOf<SP>::type R;
+  const int Vh = a.e.g.V >> 1, V = a.e.g.V;
+  const int p = a.e.parity;
+  int c[4];
+  eo_coords(a.e.g, i, p, c);
+  const int s = p * Vh + i;
+  const R k0 = (R)(a.e.sign * *a.e.kappa_dev);
+  Cx<R> acc[12];
+  if (SELF) {
+    load_spinor(a.self, s, V, acc);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = cx<R>(0, 0);
+  }
+  constexpr int SF = DAG ? +1 : -1;
+  if constexpr (SP == PDF) {
+    eo_hops_rt<SF>(a, k0, s, c, acc);
+  } else {
+    eo_hop_pair<0, SF>(a, k0, s, c, acc);
+    eo_hop_pair<1, SF>(a, k0, s, c, acc);
+    eo_hop_pair<2, SF>(a, k0, s, c, acc);
+    eo_hop_pair<3, SF>(a, k0, s, c, acc);
+  }
+  if (RESID) {
+    Cx<R> bv[12];
+    load_spinor(a.b, s, V, bv);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = cx<R>(bv[j].re - acc[j].re, bv[j].im - acc[j].im);
+  }
+  store_spinor(a.out, s, V, acc);
+  return norm2_site(acc);
+}
+
 template <int SP, bool C12, bool DAG, bool SELF, bool RESID, bool NORM>
 __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
     dslash_eo_kernel(const EoArgs<SP, C12> a) {
-  typedef typename RealOf<SP>::type R;
   if (a.e.skip != nullptr && *a.e.skip != 0) return;
-  const int Vh = a.e.g.V >> 1, V = a.e.g.V;
+  const int Vh = a.e.g.V >> 1;
   double n2 = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
-    const int p = a.e.parity;
-    int c[4];
-    eo_coords(a.e.g, i, p, c);
-    const int s = p * Vh + i;
-    const R k0 = (R)(a.e.sign * *a.e.kappa_dev);
-    Cx<R> acc[12];
-    if (SELF) {
-      load_spinor(a.self, s, V, acc);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 12; ++j) acc[j] = cx<R>(0, 0);
-    }
-    constexpr int SF = DAG ? +1 : -1;
-    if constexpr (SP == PDF) {
-      eo_hops_rt<SF>(a, k0, s, c, acc);
-    } else {
-      eo_hop_pair<0, SF>(a, k0, s, c, acc);
-      eo_hop_pair<1, SF>(a, k0, s, c, acc);
-      eo_hop_pair<2, SF>(a, k0, s, c, acc);
-      eo_hop_pair<3, SF>(a, k0, s, c, acc);
-    }
-    if (RESID) {
-      Cx<R> bv[12];
-      load_spinor(a.b, s, V, bv);
-#pragma unroll
-      for (int j = 0; j < 12; ++j) acc[j] = cx<R>(bv[j].re - acc[j].re, bv[j].im - acc[j].im);
-    }
-    store_spinor(a.out, s, V, acc);
-    if (NORM) n2 += norm2_site(acc);
+    const double v = eo_site<SP, C12, DAG, SELF, RESID>(a, i);
+    if (NORM) n2 += v;
   }
   if (NORM) {
     double v[1] = {n2}, tot[1];
@@ -1037,6 +1045,184 @@ cudaError_t launch_dslash_eo(const EoCall& c, cudaStream_t st) {
   if (c.u.prec != SP32) return cudaErrorInvalidValue;
   if (c.in.prec == SP32) return c.u.c12 ? eo_launch_p<P32, true>(c, st) : eo_launch_p<P32, false>(c, st);
   if (c.in.prec == SP16) return c.u.c12 ? eo_launch_p<P16, true>(c, st) : eo_launch_p<P16, false>(c, st);
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- persistent CG loop, even-odd
+//
+// The plain CGLS loop on M = 1 - kappa^2 H_eo H_oe over the even sites, in one cooperative launch:
+// each application of M (or M^dag) is two half-lattice passes through the odd temporary t with a
+// grid barrier between them; the vector updates run over the even half. Six barriers per
+// iteration; the scalars and the stopping rule are those of the lexicographic loop.
+template <int SP, bool C12>
+struct EoLoopArgs {
+  EoArgs<SP, C12> pt, tq, rt, ts;  // t = kappa H_oe p; q = p - kappa H_eo t; the same with H^dag for r -> s
+  SpinorRef<SP> x, r, p, q, s;
+  int n;                           // even sites (V / 2)
+  CgScalars* sc;
+  double* partials;
+  LoopSync y;
+};
+
+template <int SP, bool C12>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
+    cg_eo_loop_kernel(const EoLoopArgs<SP, C12> a) {
+  typedef typename RealOf<SP>::type R;
+  CgScalars* sc = a.sc;
+  if (sc->status != ST_RUNNING) return;  // uniform over the grid
+  const int n = a.n, V = a.pt.e.g.V, G = gridDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  double gamma = sc->gamma, rr = sc->rr;
+  const double tol2e = sc->tol2 * sc->eta2;
+  int iter = sc->iter, status = ST_RUNNING;
+  const int maxit = sc->maxit;
+  double alpha = 0.0, beta = 0.0;
+  for (;;) {
+    // q = M p, |q|^2
+    for (int i = t0; i < n; i += tstep) (void)eo_site<SP, C12, false, false, false>(a.pt, i);
+    if (!grid_barrier(a.y)) break;
+    double v = 0.0;
+    for (int i = t0; i < n; i += tstep) v += eo_site<SP, C12, false, true, false>(a.tq, i);
+    double qq;
+    if (!loop_sum(v, a.partials, a.y, &qq)) break;
+    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / qq;
+    const R ar = (R)alpha;
+    // r -= alpha q, |r|^2
+    v = 0.0;
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> rv[12], qv[12];
+      load_spinor(a.r, i, V, rv);
+      load_spinor(a.q, i, V, qv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        rv[c].re = fma(-ar, qv[c].re, rv[c].re);
+        rv[c].im = fma(-ar, qv[c].im, rv[c].im);
+      }
+      store_spinor(a.r, i, V, rv);
+      v += norm2_site(rv);
+    }
+    if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (!isfinite(rr)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    const bool conv = rr <= tol2e;
+    // s = M^dag r, |s|^2 (not needed once converged)
+    double gnew = 0.0;
+    if (!conv) {
+      for (int i = t0; i < n; i += tstep) (void)eo_site<SP, C12, true, false, false>(a.rt, i);
+      if (!grid_barrier(a.y)) break;
+      v = 0.0;
+      for (int i = t0; i < n; i += tstep) v += eo_site<SP, C12, true, true, false>(a.ts, i);
+      if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
+    }
+    const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
+    beta = do_p ? gnew / gamma : 0.0;
+    const R br = (R)beta;
+    // x += alpha p; p = s + beta p
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> xv[12], pv[12];
+      load_spinor(a.x, i, V, xv);
+      load_spinor(a.p, i, V, pv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fma(ar, pv[c].re, xv[c].re);
+        xv[c].im = fma(ar, pv[c].im, xv[c].im);
+      }
+      store_spinor(a.x, i, V, xv);
+      if (do_p) {
+        Cx<R> sv[12];
+        load_spinor(a.s, i, V, sv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          pv[c].re = fma(br, pv[c].re, sv[c].re);
+          pv[c].im = fma(br, pv[c].im, sv[c].im);
+        }
+        store_spinor(a.p, i, V, pv);
+      }
+    }
+    iter += 1;
+    if (conv) {
+      status = ST_CONVERGED;
+      break;
+    }
+    if (!do_p) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    gamma = gnew;
+    if (iter >= maxit) {
+      status = ST_MAXIT;
+      break;
+    }
+    if (!grid_barrier(a.y)) break;  // p complete before the next pass reads its neighbours
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->alpha = alpha;
+    sc->beta = beta;
+  }
+}
+
+template <int SP, bool C12>
+static void eo_args(EoArgs<SP, C12>& e, const CgLoopCall& c, FieldPtr in, FieldPtr out, const FieldPtr* self,
+                    int parity, double sign) {
+  memset(&e, 0, sizeof(e));
+  memcpy(&e.e.g, &c.g, sizeof(Geom));
+  e.e.parity = parity;
+  e.e.sign = sign;
+  e.e.kappa_dev = c.kappa_dev;
+  e.u.p = reinterpret_cast<decltype(e.u.p)>(c.u.p);
+  e.in = make_ref<SP>(in, c.g.V);
+  e.out = make_ref<SP>(out, c.g.V);
+  if (self) e.self = make_ref<SP>(*self, c.g.V);
+}
+
+template <int SP, bool C12>
+static cudaError_t eo_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+  EoLoopArgs<SP, C12> a;
+  eo_args(a.pt, c, c.p, c.t, nullptr, 1, +1.0);
+  eo_args(a.tq, c, c.t, c.q, &c.p, 0, -1.0);
+  eo_args(a.rt, c, c.r, c.t, nullptr, 1, +1.0);
+  eo_args(a.ts, c, c.t, c.s, &c.r, 0, -1.0);
+  a.x = make_ref<SP>(c.x, c.g.V);
+  a.r = make_ref<SP>(c.r, c.g.V);
+  a.p = make_ref<SP>(c.p, c.g.V);
+  a.q = make_ref<SP>(c.q, c.g.V);
+  a.s = make_ref<SP>(c.s, c.g.V);
+  a.n = c.g.V / 2;
+  a.sc = c.sc;
+  a.partials = c.partials;
+  a.y.bar = c.bar;
+  a.y.err = c.err;
+  auto k = cg_eo_loop_kernel<SP, C12>;
+  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
+  const int need = grid_for(c.g.V / 2, c.block);
+  if (need < grid) grid = need;
+  if (grid > c.max_grid) grid = c.max_grid;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+}
+
+cudaError_t launch_cg_eo_loop(const CgLoopCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1 || !c.t.p) return cudaErrorInvalidValue;
+  if (c.x.prec != c.r.prec || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec ||
+      c.t.prec != c.r.prec)
+    return cudaErrorInvalidValue;
+  if (c.r.prec == SP64) {
+    if (c.u.prec != SP64) return cudaErrorInvalidValue;
+    return eo_loop_launch_t<P64, false>(c, st);
+  }
+  if (c.r.prec == SP32 && c.u.prec == SP32)
+    return c.u.c12 ? eo_loop_launch_t<P32, true>(c, st) : eo_loop_launch_t<P32, false>(c, st);
   return cudaErrorInvalidValue;
 }
 

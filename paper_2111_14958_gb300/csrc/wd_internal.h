@@ -113,11 +113,14 @@ struct CgLoopCall {
   int max_grid;
   int variant;  // FP64: 1 = the dslash phases use two lanes per site
   int start_b;  // mixed loop: resume at the D^dag half of an iteration (after a reliable update)
+  FieldPtr t;   // even-odd loop: the odd-site temporary
 };
 cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st);
 // The inner loop of the mixed-precision solver (x = x_lo in FP32; r, p, q, s in the working
 // precision) as one cooperative launch that returns when a reliable update is due or the loop ends.
 cudaError_t launch_cg_mixed_loop(const CgLoopCall& c, cudaStream_t st);
+// The plain CGLS loop on the even-site Schur complement of a parity-ordered context.
+cudaError_t launch_cg_eo_loop(const CgLoopCall& c, cudaStream_t st);
 constexpr int kLoopMaxGrid = 8192;
 
 // eo: null for lexicographic storage, else the geometry of a parity-ordered context.

@@ -87,3 +87,26 @@ def test_eo_restart_keeps_the_schur_source():
     assert st1 == st2 == wd.WD_OK
     assert ocg.true_residual(U, eta, to_np(x2), 0.12) <= 1e-11
     op.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-6)])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (14, 14, 14, 14)])
+def test_eo_persistent_loop_matches_graph_and_oracle(prec, tol, dims):
+    wd = require_gpu()
+    U, eta = fields(dims)
+    base = wd.WD_PREC_F64 if prec == "f64" else wd.WD_PREC_F32
+    got = {}
+    for mode in (1, 2):
+        op = wd.WilsonDirac(dims, 0.124, BC, base | wd.WD_EVEN_ODD)
+        op.load_gauge(to_dev(U), compress12=prec != "f64")
+        op.set_option(wd.WD_OPT_USE_GRAPH, mode)
+        x, iters, r, st = op.solve(to_dev(eta), tol=tol, maxit=5000)
+        assert st == wd.WD_OK
+        xs = to_np(x)
+        assert ocg.true_residual(U, eta, xs, 0.124) <= tol * 1.05
+        assert abs(r - ocg.true_residual(U, eta, xs, 0.124)) < max(1e-12, 0.05 * tol)
+        assert op.stats()["loop_mode"] == mode
+        got[mode] = (iters, xs)
+        op.close()
+    assert abs(got[1][0] - got[2][0]) <= 1
+    assert rel(got[2][1], got[1][1]) < 1e3 * tol
