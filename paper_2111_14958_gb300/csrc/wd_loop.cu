@@ -1,0 +1,605 @@
+// Persistent cooperative CG loops: plain (lexicographic), mixed-precision inner loop and even-odd.
+#include "wd_stencil.cuh"
+
+namespace wdk {
+
+// ---------------------------------------------------------------- persistent CG loop
+//
+// At the paper's volumes every kernel of a CG iteration costs a launch and a grid-reduction tail
+// of several microseconds, comparable to its work. This kernel runs the whole CGLS loop (the four
+// phases of each iteration) in one cooperative launch: the grid is one wave of resident blocks,
+// the phases are separated by a grid barrier, and each norm is summed by every block from the
+// block partials in one fixed order, so all blocks hold the same scalars and the results are
+// reproducible. The launch is cooperative, so all blocks are resident and the barrier always
+// completes; its wait is still bounded: past the limit the kernel records an error and stops.
+
+struct LoopSync {
+  unsigned* bar;  // [0] arrivals, [1] generation
+  int* err;       // set to 1 when a barrier wait gave up
+};
+
+constexpr long long kBarrierSpinLimit = 1LL << 26;  // x 64 ns sleep: about 4 s
+
+// All blocks arrive, then continue. Returns false (everywhere, eventually) if a wait gave up.
+__device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = y.bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(y.bar, 1u);
+    int good = 1;
+    if (arrived == gridDim.x - 1) {
+      y.bar[0] = 0u;
+      __threadfence();
+      atomicAdd(y.bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g0) {
+        if (++spins > kBarrierSpinLimit || *(volatile int*)y.err) {
+          atomicExch(y.err, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good && !*(volatile int*)y.err;
+  }
+  __syncthreads();
+  return ok;
+}
+
+// Sum over the grid of one value per thread: block partial, barrier, then every block sums the
+// partials in the same order (lanes stride over them, then a fixed shuffle tree).
+__device__ __forceinline__ bool loop_sum(double v, double* partials, const LoopSync& y, double* out) {
+  __shared__ double smem[32];
+  __shared__ double total;
+  double w[1] = {v};
+  block_reduce<OpSum, 1>(w, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = w[0];
+    __threadfence();
+  }
+  if (!grid_barrier(y)) return false;
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) a += __ldcg(partials + b);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (threadIdx.x == 0) total = a;
+  }
+  __syncthreads();
+  *out = total;
+  return true;
+}
+
+template <int SP, bool C12>
+struct LoopArgs {
+  DslashArgs<SP, C12> dq;  // q = D p
+  DslashArgs<SP, C12> ds;  // s = D^dag r
+  SpinorRef<SP> x, r, p, q, s;
+  int n;                   // sites
+  CgScalars* sc;
+  double* partials;        // 3 x gridDim.x
+  LoopSync y;
+};
+
+// The dslash phases of the loop: one thread per site, or (FP64, PAIR) two lanes per site.
+template <int SP, bool C12, bool DAG, bool PAIR>
+__device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int n, int t0, int tstep) {
+  if constexpr (SP == P64 && PAIR) {
+    return pair_sites<C12, DAG, EPI_PLAIN>(d);
+  } else {
+    double v = 0.0;
+    for (int i = t0; i < n; i += tstep) v += dslash_site<SP, C12, DAG, EPI_PLAIN>(d, i);
+    return v;
+  }
+}
+
+template <int SP, bool C12, bool PAIR>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value) cg_loop_kernel(const LoopArgs<SP, C12> a) {
+  typedef typename RealOf<SP>::type R;
+  CgScalars* sc = a.sc;
+  if (sc->status != ST_RUNNING) return;  // uniform over the grid
+  const int n = a.n, V = a.dq.g.V, G = gridDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  double gamma = sc->gamma, rr = sc->rr;
+  const double tol2e = sc->tol2 * sc->eta2;
+  int iter = sc->iter, status = ST_RUNNING;
+  const int maxit = sc->maxit;
+  double alpha = 0.0, beta = 0.0;
+  for (;;) {
+    // q = D p, |q|^2
+    double v = loop_dslash<SP, C12, false, PAIR>(a.dq, n, t0, tstep);
+    double qq;
+    if (!loop_sum(v, a.partials, a.y, &qq)) break;
+    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / qq;
+    const R ar = (R)alpha;
+    // r -= alpha q, |r|^2
+    v = 0.0;
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> rv[12], qv[12];
+      load_spinor(a.r, i, V, rv);
+      load_spinor(a.q, i, V, qv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        rv[c].re = fma(-ar, qv[c].re, rv[c].re);
+        rv[c].im = fma(-ar, qv[c].im, rv[c].im);
+      }
+      store_spinor(a.r, i, V, rv);
+      v += norm2_site(rv);
+    }
+    if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (!isfinite(rr)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    const bool conv = rr <= tol2e;
+    // s = D^dag r, |s|^2 (not needed once converged)
+    double gnew = 0.0;
+    if (!conv) {
+      v = loop_dslash<SP, C12, true, PAIR>(a.ds, n, t0, tstep);
+      if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
+    }
+    const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
+    beta = do_p ? gnew / gamma : 0.0;
+    const R br = (R)beta;
+    // x += alpha p; p = s + beta p
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> xv[12], pv[12];
+      load_spinor(a.x, i, V, xv);
+      load_spinor(a.p, i, V, pv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fma(ar, pv[c].re, xv[c].re);
+        xv[c].im = fma(ar, pv[c].im, xv[c].im);
+      }
+      store_spinor(a.x, i, V, xv);
+      if (do_p) {
+        Cx<R> sv[12];
+        load_spinor(a.s, i, V, sv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          pv[c].re = fma(br, pv[c].re, sv[c].re);
+          pv[c].im = fma(br, pv[c].im, sv[c].im);
+        }
+        store_spinor(a.p, i, V, pv);
+      }
+    }
+    iter += 1;
+    if (conv) {
+      status = ST_CONVERGED;
+      break;
+    }
+    if (!do_p) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    gamma = gnew;
+    if (iter >= maxit) {
+      status = ST_MAXIT;
+      break;
+    }
+    if (!grid_barrier(a.y)) break;  // p complete before the next dslash reads its neighbours
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->alpha = alpha;
+    sc->beta = beta;
+  }
+}
+
+// The inner loop of the mixed-precision solver (FP32 or FP16 vectors, x_lo in FP32) in one
+// cooperative launch. Phase A: q = D p, |q|^2; r_lo -= alpha q, x_lo += alpha p, |r_lo|^2, and
+// the reliable-update test. Phase B: s = D^dag r_lo, |s|^2; p = s + beta p. The kernel starts at A
+// (or at B right after a reliable update) and returns as soon as an update is due or the loop
+// ends, leaving the same scalars and flags as the separate kernels of the graph solver.
+template <int SPW, bool C12>
+struct MixedLoopArgs {
+  DslashArgs<SPW, C12> dq;  // q = D p
+  DslashArgs<SPW, C12> ds;  // s = D^dag r
+  SpinorRef<SPW> r, p, q, s;
+  SpinorRef<P32> xlo;
+  int n;
+  int start_b;
+  CgScalars* sc;
+  double* partials;  // 3 x gridDim.x
+  LoopSync y;
+};
+
+template <int SPW, bool C12>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SPW>::value)
+    cg_mixed_loop_kernel(const MixedLoopArgs<SPW, C12> a) {
+  CgScalars* sc = a.sc;
+  const int st_in = sc->status;
+  if (st_in != ST_RUNNING && !(a.start_b && st_in == ST_CONVERGED)) return;  // uniform over the grid
+  const int n = a.n, V = a.dq.g.V, G = gridDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  double gamma = sc->gamma, rr = sc->rr, alpha = sc->alpha, beta = sc->beta;
+  const double tol2e = sc->tol2 * sc->eta2, d2ref = sc->delta2 * sc->rr_ref;
+  int iter = sc->iter, status = st_in, need = 0;
+  const int maxit = sc->maxit;
+  bool phase_b = a.start_b != 0;
+  for (;;) {
+    if (phase_b) {
+      // s = D^dag r_lo, gamma' = |s|^2 (skipped once the last update converged)
+      double gnew = 0.0;
+      if (status == ST_RUNNING) {
+        double v = 0.0;
+        for (int i = t0; i < n; i += tstep) v += dslash_site<SPW, C12, true, EPI_PLAIN>(a.ds, i);
+        if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
+      }
+      const bool do_p = status == ST_RUNNING && isfinite(gnew) && gamma > 0.0;
+      beta = do_p ? gnew / gamma : 0.0;
+      const float bf = (float)beta;
+      if (do_p) {
+        for (int i = t0; i < n; i += tstep) {
+          Cx<float> pv[12], sv[12];
+          load_spinor(a.p, i, V, pv);
+          load_spinor(a.s, i, V, sv);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            pv[c].re = fmaf(bf, pv[c].re, sv[c].re);
+            pv[c].im = fmaf(bf, pv[c].im, sv[c].im);
+          }
+          store_spinor(a.p, i, V, pv);
+        }
+      }
+      iter += 1;  // the iteration whose r update ran, including one that converged in its update
+      if (status != ST_RUNNING) break;
+      if (!do_p) {
+        status = ST_BREAKDOWN;
+        break;
+      }
+      gamma = gnew;
+      if (iter >= maxit) {
+        status = ST_MAXIT;
+        break;
+      }
+      if (!grid_barrier(a.y)) break;  // p complete before the next dslash reads its neighbours
+    }
+    phase_b = true;
+    // q = D p, |q|^2
+    double v = 0.0;
+    for (int i = t0; i < n; i += tstep) v += dslash_site<SPW, C12, false, EPI_PLAIN>(a.dq, i);
+    double qq;
+    if (!loop_sum(v, a.partials, a.y, &qq)) break;
+    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / qq;
+    const float af = (float)alpha;
+    // r_lo -= alpha q; x_lo += alpha p; |r_lo|^2
+    v = 0.0;
+    for (int i = t0; i < n; i += tstep) {
+      Cx<float> rv[12], qv[12], pv[12], xv[12];
+      load_spinor(a.r, i, V, rv);
+      load_spinor(a.q, i, V, qv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        rv[c].re = fmaf(-af, qv[c].re, rv[c].re);
+        rv[c].im = fmaf(-af, qv[c].im, rv[c].im);
+      }
+      store_spinor(a.r, i, V, rv);
+      v += norm2_site(rv);
+      load_spinor(a.p, i, V, pv);
+      load_spinor(a.xlo, i, V, xv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fmaf(af, pv[c].re, xv[c].re);
+        xv[c].im = fmaf(af, pv[c].im, xv[c].im);
+      }
+      store_spinor(a.xlo, i, V, xv);
+    }
+    if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (!isfinite(rr)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    need = (rr <= d2ref) || (rr <= tol2e);
+    if (need) break;  // the reliable update runs outside; the loop resumes at phase B
+    if (!grid_barrier(a.y)) break;  // r complete before D^dag reads its neighbours
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->alpha = alpha;
+    sc->beta = beta;
+    sc->need_update = need;
+    sc->no_update = !need;
+  }
+}
+
+template <int SPW, bool C12>
+static cudaError_t mixed_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+  MixedLoopArgs<SPW, C12> a;
+  for (DslashArgs<SPW, C12>* d : {&a.dq, &a.ds}) {
+    memcpy(&d->g, &c.g, sizeof(Geom));
+    d->u.p = reinterpret_cast<decltype(d->u.p)>(c.u.p);
+    d->mkappa = (float)(-c.kappa);
+    d->kappa_dev = c.kappa_dev;
+    d->skip = nullptr;
+    d->partials = nullptr;
+    d->ticket = nullptr;
+    d->result = nullptr;
+  }
+  a.dq.in = make_ref<SPW>(c.p, c.g.V);
+  a.dq.out = make_ref<SPW>(c.q, c.g.V);
+  a.dq.b = make_ref<SPW>(FieldPtr{}, c.g.V);
+  a.ds.in = make_ref<SPW>(c.r, c.g.V);
+  a.ds.out = make_ref<SPW>(c.s, c.g.V);
+  a.ds.b = a.dq.b;
+  a.r = make_ref<SPW>(c.r, c.g.V);
+  a.p = make_ref<SPW>(c.p, c.g.V);
+  a.q = make_ref<SPW>(c.q, c.g.V);
+  a.s = make_ref<SPW>(c.s, c.g.V);
+  a.xlo = make_ref<P32>(c.x, c.g.V);
+  a.n = c.g.V;
+  a.start_b = c.start_b;
+  a.sc = c.sc;
+  a.partials = c.partials;
+  a.y.bar = c.bar;
+  a.y.err = c.err;
+  auto k = cg_mixed_loop_kernel<SPW, C12>;
+  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
+  const int need = grid_for(c.g.V, c.block);
+  if (need < grid) grid = need;
+  if (grid > c.max_grid) grid = c.max_grid;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+}
+
+cudaError_t launch_cg_mixed_loop(const CgLoopCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1) return cudaErrorInvalidValue;
+  if (c.x.prec != SP32 || c.u.prec != SP32 || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec)
+    return cudaErrorInvalidValue;
+  if (c.r.prec == SP32) return c.u.c12 ? mixed_loop_launch_t<P32, true>(c, st) : mixed_loop_launch_t<P32, false>(c, st);
+  if (c.r.prec == SP16) return c.u.c12 ? mixed_loop_launch_t<P16, true>(c, st) : mixed_loop_launch_t<P16, false>(c, st);
+  return cudaErrorInvalidValue;
+}
+
+template <int SP, bool C12, bool PAIR>
+static cudaError_t loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+  LoopArgs<SP, C12> a;
+  for (DslashArgs<SP, C12>* d : {&a.dq, &a.ds}) {
+    memcpy(&d->g, &c.g, sizeof(Geom));
+    d->u.p = reinterpret_cast<decltype(d->u.p)>(c.u.p);
+    d->mkappa = (typename RealOf<SP>::type)(-c.kappa);
+    d->kappa_dev = c.kappa_dev;
+    d->skip = nullptr;
+    d->partials = nullptr;
+    d->ticket = nullptr;
+    d->result = nullptr;
+  }
+  a.dq.in = make_ref<SP>(c.p, c.g.V);
+  a.dq.out = make_ref<SP>(c.q, c.g.V);
+  a.dq.b = make_ref<SP>(FieldPtr{}, c.g.V);
+  a.ds.in = make_ref<SP>(c.r, c.g.V);
+  a.ds.out = make_ref<SP>(c.s, c.g.V);
+  a.ds.b = a.dq.b;
+  a.x = make_ref<SP>(c.x, c.g.V);
+  a.r = make_ref<SP>(c.r, c.g.V);
+  a.p = make_ref<SP>(c.p, c.g.V);
+  a.q = make_ref<SP>(c.q, c.g.V);
+  a.s = make_ref<SP>(c.s, c.g.V);
+  a.n = c.g.V;
+  a.sc = c.sc;
+  a.partials = c.partials;
+  a.y.bar = c.bar;
+  a.y.err = c.err;
+  auto k = cg_loop_kernel<SP, C12, PAIR>;
+  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
+  const int need = grid_for(PAIR ? 2 * c.g.V : c.g.V, c.block);
+  if (need < grid) grid = need;
+  if (grid > c.max_grid) grid = c.max_grid;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+}
+
+cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1) return cudaErrorInvalidValue;
+  if (c.x.prec != c.r.prec || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec)
+    return cudaErrorInvalidValue;
+  if (c.r.prec == SP64) {
+    if (c.u.prec != SP64) return cudaErrorInvalidValue;
+    return c.variant == 1 ? loop_launch_t<P64, false, true>(c, st) : loop_launch_t<P64, false, false>(c, st);
+  }
+  if (c.r.prec == SP32 && c.u.prec == SP32)
+    return c.u.c12 ? loop_launch_t<P32, true, false>(c, st) : loop_launch_t<P32, false, false>(c, st);
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- persistent CG loop, even-odd
+//
+// The plain CGLS loop on M = 1 - kappa^2 H_eo H_oe over the even sites, in one cooperative launch:
+// each application of M (or M^dag) is two half-lattice passes through the odd temporary t with a
+// grid barrier between them; the vector updates run over the even half. Six barriers per
+// iteration; the scalars and the stopping rule are those of the lexicographic loop.
+template <int SP, bool C12>
+struct EoLoopArgs {
+  EoArgs<SP, C12> pt, tq, rt, ts;  // t = kappa H_oe p; q = p - kappa H_eo t; the same with H^dag for r -> s
+  SpinorRef<SP> x, r, p, q, s;
+  int n;                           // even sites (V / 2)
+  CgScalars* sc;
+  double* partials;
+  LoopSync y;
+};
+
+template <int SP, bool C12>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
+    cg_eo_loop_kernel(const EoLoopArgs<SP, C12> a) {
+  typedef typename RealOf<SP>::type R;
+  CgScalars* sc = a.sc;
+  if (sc->status != ST_RUNNING) return;  // uniform over the grid
+  const int n = a.n, V = a.pt.e.g.V, G = gridDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  double gamma = sc->gamma, rr = sc->rr;
+  const double tol2e = sc->tol2 * sc->eta2;
+  int iter = sc->iter, status = ST_RUNNING;
+  const int maxit = sc->maxit;
+  double alpha = 0.0, beta = 0.0;
+  for (;;) {
+    // q = M p, |q|^2
+    for (int i = t0; i < n; i += tstep) (void)eo_site<SP, C12, false, false, false>(a.pt, i);
+    if (!grid_barrier(a.y)) break;
+    double v = 0.0;
+    for (int i = t0; i < n; i += tstep) v += eo_site<SP, C12, false, true, false>(a.tq, i);
+    double qq;
+    if (!loop_sum(v, a.partials, a.y, &qq)) break;
+    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / qq;
+    const R ar = (R)alpha;
+    // r -= alpha q, |r|^2
+    v = 0.0;
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> rv[12], qv[12];
+      load_spinor(a.r, i, V, rv);
+      load_spinor(a.q, i, V, qv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        rv[c].re = fma(-ar, qv[c].re, rv[c].re);
+        rv[c].im = fma(-ar, qv[c].im, rv[c].im);
+      }
+      store_spinor(a.r, i, V, rv);
+      v += norm2_site(rv);
+    }
+    if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (!isfinite(rr)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    const bool conv = rr <= tol2e;
+    // s = M^dag r, |s|^2 (not needed once converged)
+    double gnew = 0.0;
+    if (!conv) {
+      for (int i = t0; i < n; i += tstep) (void)eo_site<SP, C12, true, false, false>(a.rt, i);
+      if (!grid_barrier(a.y)) break;
+      v = 0.0;
+      for (int i = t0; i < n; i += tstep) v += eo_site<SP, C12, true, true, false>(a.ts, i);
+      if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
+    }
+    const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
+    beta = do_p ? gnew / gamma : 0.0;
+    const R br = (R)beta;
+    // x += alpha p; p = s + beta p
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> xv[12], pv[12];
+      load_spinor(a.x, i, V, xv);
+      load_spinor(a.p, i, V, pv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fma(ar, pv[c].re, xv[c].re);
+        xv[c].im = fma(ar, pv[c].im, xv[c].im);
+      }
+      store_spinor(a.x, i, V, xv);
+      if (do_p) {
+        Cx<R> sv[12];
+        load_spinor(a.s, i, V, sv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          pv[c].re = fma(br, pv[c].re, sv[c].re);
+          pv[c].im = fma(br, pv[c].im, sv[c].im);
+        }
+        store_spinor(a.p, i, V, pv);
+      }
+    }
+    iter += 1;
+    if (conv) {
+      status = ST_CONVERGED;
+      break;
+    }
+    if (!do_p) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    gamma = gnew;
+    if (iter >= maxit) {
+      status = ST_MAXIT;
+      break;
+    }
+    if (!grid_barrier(a.y)) break;  // p complete before the next pass reads its neighbours
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->alpha = alpha;
+    sc->beta = beta;
+  }
+}
+
+template <int SP, bool C12>
+static void eo_args(EoArgs<SP, C12>& e, const CgLoopCall& c, FieldPtr in, FieldPtr out, const FieldPtr* self,
+                    int parity, double sign) {
+  memset(&e, 0, sizeof(e));
+  memcpy(&e.e.g, &c.g, sizeof(Geom));
+  e.e.parity = parity;
+  e.e.sign = sign;
+  e.e.kappa_dev = c.kappa_dev;
+  e.u.p = reinterpret_cast<decltype(e.u.p)>(c.u.p);
+  e.in = make_ref<SP>(in, c.g.V);
+  e.out = make_ref<SP>(out, c.g.V);
+  if (self) e.self = make_ref<SP>(*self, c.g.V);
+}
+
+template <int SP, bool C12>
+static cudaError_t eo_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+  EoLoopArgs<SP, C12> a;
+  eo_args(a.pt, c, c.p, c.t, nullptr, 1, +1.0);
+  eo_args(a.tq, c, c.t, c.q, &c.p, 0, -1.0);
+  eo_args(a.rt, c, c.r, c.t, nullptr, 1, +1.0);
+  eo_args(a.ts, c, c.t, c.s, &c.r, 0, -1.0);
+  a.x = make_ref<SP>(c.x, c.g.V);
+  a.r = make_ref<SP>(c.r, c.g.V);
+  a.p = make_ref<SP>(c.p, c.g.V);
+  a.q = make_ref<SP>(c.q, c.g.V);
+  a.s = make_ref<SP>(c.s, c.g.V);
+  a.n = c.g.V / 2;
+  a.sc = c.sc;
+  a.partials = c.partials;
+  a.y.bar = c.bar;
+  a.y.err = c.err;
+  auto k = cg_eo_loop_kernel<SP, C12>;
+  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
+  const int need = grid_for(c.g.V / 2, c.block);
+  if (need < grid) grid = need;
+  if (grid > c.max_grid) grid = c.max_grid;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+}
+
+cudaError_t launch_cg_eo_loop(const CgLoopCall& c, cudaStream_t st) {
+  if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1 || !c.t.p) return cudaErrorInvalidValue;
+  if (c.x.prec != c.r.prec || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec ||
+      c.t.prec != c.r.prec)
+    return cudaErrorInvalidValue;
+  if (c.r.prec == SP64) {
+    if (c.u.prec != SP64) return cudaErrorInvalidValue;
+    return eo_loop_launch_t<P64, false>(c, st);
+  }
+  if (c.r.prec == SP32 && c.u.prec == SP32)
+    return c.u.c12 ? eo_loop_launch_t<P32, true>(c, st) : eo_loop_launch_t<P32, false>(c, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace wdk

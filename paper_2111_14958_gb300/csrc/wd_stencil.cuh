@@ -1,0 +1,465 @@
+// Device-side building blocks of the Wilson-Dirac stencil (Eq. (1)), shared by the dslash,
+// even-odd and persistent-loop translation units: precision views, the per-hop spin algebra and
+// SU(3) multiply, one output site of D (or of a half-lattice hop), and the FP64 two-lanes-per-site
+// pass. See wd_dslash.cu for the arithmetic and byte counts per site.
+#pragma once
+
+#include "wd_device.cuh"
+#include "wd_internal.h"
+
+namespace wdk {
+
+
+template <int SP>
+struct RealOf {
+  typedef float type;
+};
+template <>
+struct RealOf<P64> {
+  typedef double type;
+};
+template <>
+struct RealOf<PDF> {
+  typedef dfloat type;
+};
+
+// device view of a field (hi/lo halves for double-float)
+template <int SP>
+__host__ SpinorRef<SP> make_ref(FieldPtr f, int V) {
+  SpinorRef<SP> r;
+  if constexpr (SP == PDF) {
+    r.hi = reinterpret_cast<float4*>(f.p);
+    r.lo = f.p ? reinterpret_cast<float4*>(f.p) + (size_t)6 * V : nullptr;
+  } else {
+    r.p = reinterpret_cast<decltype(r.p)>(f.p);
+    if constexpr (SP == P16) r.norm = f.norm;
+  }
+  return r;
+}
+
+template <int SP, bool C12>
+struct DslashArgs {
+  Geom g;
+  GaugeRef<typename RealOf<SP>::type, C12> u;
+  SpinorRef<SP> in, out, b;
+  typename RealOf<SP>::type mkappa;  // -kappa (used when kappa_dev is null)
+  const double* kappa_dev;
+  const int* skip;
+  double* partials;
+  unsigned* ticket;
+  double* result;
+};
+
+template <int MU, int S_FWD, int SP, bool C12, typename R>
+__device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int s, const int (&c)[4],
+                                         Cx<R> (&acc)[12]) {
+  const int V = a.g.V;
+  // forward hop n -> n + mu with U_mu(n)
+  {
+    const bool wrap = c[MU] == a.g.L[MU] - 1;
+    const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
+    Cx<R> psi[12];
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
+    Cx<R> h[6];
+    spin_project<MU, S_FWD>(psi, h);
+    Cx<R> u[9];
+    load_link(a.u, MU, s, V, u);
+    Cx<R> chi[6];
+    su3_mul(u, h, chi);
+    spin_reconstruct<MU, S_FWD>(acc, chi, k);
+  }
+  // backward hop n -> n - mu with U_mu(n - mu)^dagger and the opposite projector
+  {
+    const bool wrap = c[MU] == 0;
+    const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
+    Cx<R> psi[12];
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
+    Cx<R> h[6];
+    spin_project<MU, -S_FWD>(psi, h);
+    Cx<R> u[9];
+    load_link(a.u, MU, nb, V, u);
+    Cx<R> chi[6];
+    su3_dag_mul(u, h, chi);
+    spin_reconstruct<MU, -S_FWD>(acc, chi, k);
+  }
+}
+
+// All 8 hops in a runtime loop (one copy of the per-hop code): for double-float arithmetic, whose
+// unrolled form overflows the instruction cache.
+template <int SF, int SP, bool C12, typename R>
+__device__ __forceinline__ void hops_rt(const DslashArgs<SP, C12>& a, R mk, int s, const int (&c)[4], Cx<R> (&acc)[12]) {
+  const int V = a.g.V;
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int mu = hop >> 1, dir = hop & 1;
+    const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+    const int L = a.g.L[mu], st = a.g.stride[mu];
+    const bool wrap = dir == 0 ? cm == L - 1 : cm == 0;
+    const int nb = dir == 0 ? (wrap ? s - (L - 1) * st : s + st) : (wrap ? s + (L - 1) * st : s - st);
+    const R k = (wrap && a.g.bc[mu] < 0) ? -mk : mk;
+    const int S = dir == 0 ? SF : -SF;
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    load_spinor(a.in, nb, V, psi);
+    spin_project_rt(mu, S, psi, h);
+    load_link(a.u, mu, dir == 0 ? s : nb, V, u);
+    if (dir == 0)
+      su3_mul(u, h, chi);
+    else
+      su3_dag_mul(u, h, chi);
+    spin_reconstruct_rt(mu, S, acc, chi, k);
+  }
+}
+
+// One site of out = D in (or b - D in); returns |out(s)|^2.
+template <int SP, bool C12, bool DAG, int EPI>
+__device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int s) {
+  typedef typename RealOf<SP>::type R;
+  const int V = a.g.V;
+  int c[4];
+  {
+    int r = s;
+    c[0] = r % a.g.L[0];
+    r /= a.g.L[0];
+    c[1] = r % a.g.L[1];
+    r /= a.g.L[1];
+    c[2] = r % a.g.L[2];
+    c[3] = r / a.g.L[2];
+  }
+  const R mk = a.kappa_dev ? (R)(-*a.kappa_dev) : a.mkappa;
+  Cx<R> acc[12];
+  load_spinor(a.in, s, V, acc);
+  // D: forward (1 - gamma), backward (1 + gamma); D^dagger: the reverse
+  constexpr int SF = DAG ? +1 : -1;
+  if constexpr (SP == PDF) {
+    hops_rt<SF>(a, mk, s, c, acc);
+  } else {
+    hop_pair<0, SF>(a, mk, s, c, acc);
+    hop_pair<1, SF>(a, mk, s, c, acc);
+    hop_pair<2, SF>(a, mk, s, c, acc);
+    hop_pair<3, SF>(a, mk, s, c, acc);
+  }
+  if (EPI == EPI_RESID) {
+    Cx<R> bv[12];
+    load_spinor(a.b, s, V, bv);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cx<R>(bv[i].re - acc[i].re, bv[i].im - acc[i].im);
+  }
+  store_spinor(a.out, s, V, acc);
+  return norm2_site(acc);
+}
+
+// Occupancy: the kernel is latency-bound at large volumes (memory-level parallelism comes from
+// resident warps), so registers are capped for 3 blocks of 256 threads per SM in FP32/FP16
+// (24 warps) and 2 in FP64 (whose FP64 pipe saturates with few warps).
+constexpr int kDslashMaxThreads = 256;
+template <int SP>
+struct DslashMinBlocks {
+  static constexpr int value = SP == P64 ? 2 : (SP == PDF ? 1 : 3);
+};
+
+
+// ---------------------------------------------------------------- FP64: two threads per site
+//
+// The FP64 dslash is bound by the FP64 pipe. At the paper's volumes (14^4 = 38,416 sites) one
+// thread per site leaves 8 warps per SM, too few to keep that pipe fed through the load and
+// dependency latencies. Here lanes 2i and 2i+1 share a site: lane h projects only the half-spinor
+// row h, multiplies it by the link and reconstructs it, so both lanes run the same instructions
+// (no divergence) and together execute the same FP64 operations as one thread of dslash_kernel.
+// Row h of (1 -/+ gamma_mu) pairs upper spin h with lower spin 2 + pi(h), pi(h) = 1 - h for x, y
+// (B_mu off-diagonal) and h for z, t, with the coefficient B_mu[h][pi(h)] = sigma * i^e; the
+// reconstructed row feeds upper spin h and lower spin 2 + pi(h) with S conj(B_mu[h][pi(h)]).
+// Lane h accumulates its upper spin, its own lower spin 2 + h (z, t hops) and the partner's
+// lower spin (x, y hops), which the lanes exchange with one shuffle at the end.
+
+__device__ __forceinline__ Cx<double> shfl_xor_cx(Cx<double> z, int m) {
+  return cx(__shfl_xor_sync(0xffffffffu, z.re, m), __shfl_xor_sync(0xffffffffu, z.im, m));
+}
+
+template <int MU, int DIR, int SF, bool C12>
+__device__ __forceinline__ void pair_hop(const DslashArgs<P64, C12>& a, double mk, int s, const int (&c)[4], int hl,
+                                         Cx<double> (&au)[3], Cx<double> (&ald)[3], Cx<double> (&alo)[3]) {
+  constexpr int S = DIR == 0 ? SF : -SF;  // projector sign: forward (1 + SF gamma), backward the opposite
+  constexpr int E = (MU == 0 || MU == 2) ? 1 : 0;
+  const int V = a.g.V;
+  bool wrap;
+  int nb;
+  if (DIR == 0) {
+    wrap = c[MU] == a.g.L[MU] - 1;
+    nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
+  } else {
+    wrap = c[MU] == 0;
+    nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
+  }
+  const double k = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
+  // sigma: B_mu[h][pi(h)] = sigma i^E
+  const double sigma = MU == 0 ? -1.0 : (MU == 3 ? 1.0 : (hl ? 1.0 : -1.0));
+  const double ssig = S > 0 ? sigma : -sigma;
+  const int lower = (MU < 2) ? 3 - hl : 2 + hl;  // spin paired with upper spin hl
+  Cx<double> hh[3];
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    const double2 pu = __ldg(a.in.p + (size_t)(3 * hl + col) * V + nb);
+    const double2 pl = __ldg(a.in.p + (size_t)(3 * lower + col) * V + nb);
+    if (E == 0)
+      hh[col] = cx(fma(ssig, pl.x, pu.x), fma(ssig, pl.y, pu.y));
+    else  // i z = (-z.im, z.re)
+      hh[col] = cx(fma(-ssig, pl.y, pu.x), fma(ssig, pl.x, pu.y));
+  }
+  Cx<double> u[9];
+  load_link(a.u, MU, DIR == 0 ? s : nb, V, u);
+  Cx<double> chi[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Cx<double> u0, u1, u2;
+    if (DIR == 0) {
+      u0 = u[3 * r];
+      u1 = u[3 * r + 1];
+      u2 = u[3 * r + 2];
+    } else {
+      u0 = conj_(u[r]);
+      u1 = conj_(u[3 + r]);
+      u2 = conj_(u[6 + r]);
+    }
+    double re = u0.re * hh[0].re;
+    re = fma(-u0.im, hh[0].im, re);
+    re = fma(u1.re, hh[1].re, re);
+    re = fma(-u1.im, hh[1].im, re);
+    re = fma(u2.re, hh[2].re, re);
+    re = fma(-u2.im, hh[2].im, re);
+    double im = u0.re * hh[0].im;
+    im = fma(u0.im, hh[0].re, im);
+    im = fma(u1.re, hh[1].im, im);
+    im = fma(u1.im, hh[1].re, im);
+    im = fma(u2.re, hh[2].im, im);
+    im = fma(u2.im, hh[2].re, im);
+    chi[r] = cx(re, im);
+  }
+  // upper spin hl += k chi; lower spin 2 + pi(hl) += k S conj(sigma i^E) chi = k S sigma (-i)^E chi
+  const double kl = k * ssig;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    au[r].re = fma(k, chi[r].re, au[r].re);
+    au[r].im = fma(k, chi[r].im, au[r].im);
+    Cx<double>& t = (MU < 2) ? alo[r] : ald[r];
+    if (E == 0) {
+      t.re = fma(kl, chi[r].re, t.re);
+      t.im = fma(kl, chi[r].im, t.im);
+    } else {  // (-i) z = (z.im, -z.re)
+      t.re = fma(kl, chi[r].im, t.re);
+      t.im = fma(-kl, chi[r].re, t.im);
+    }
+  }
+}
+
+// All sites of out = D in (or b - D in) with two lanes per site, over the whole grid (grid-stride
+// on the warp's first site); returns this thread's share of |out|^2.
+template <bool C12, bool DAG, int EPI>
+__device__ __forceinline__ double pair_sites(const DslashArgs<P64, C12>& a) {
+  const int V = a.g.V;
+  const int hl = threadIdx.x & 1;
+  double n2 = 0.0;
+  const int step = (gridDim.x * blockDim.x) >> 1;
+  // The loop runs on the warp's first site, so all 32 lanes take the same trips and meet at the
+  // full-warp shuffle below; lanes past the last site recompute the warp's first site and store
+  // nothing.
+  for (int s0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 1; s0 < V; s0 += step) {
+    const int sl = s0 + ((threadIdx.x & 31) >> 1);
+    const bool live = sl < V;
+    const int s = live ? sl : s0;
+    int c[4];
+    {
+      int r = s;
+      c[0] = r % a.g.L[0];
+      r /= a.g.L[0];
+      c[1] = r % a.g.L[1];
+      r /= a.g.L[1];
+      c[2] = r % a.g.L[2];
+      c[3] = r / a.g.L[2];
+    }
+    const double mk = a.kappa_dev ? -*a.kappa_dev : a.mkappa;
+    Cx<double> au[3], ald[3], alo[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const double2 pu = __ldg(a.in.p + (size_t)(3 * hl + col) * V + s);
+      const double2 pl = __ldg(a.in.p + (size_t)(3 * (2 + hl) + col) * V + s);
+      au[col] = cx(pu.x, pu.y);
+      ald[col] = cx(pl.x, pl.y);
+      alo[col] = cx(0.0, 0.0);
+    }
+    constexpr int SF = DAG ? +1 : -1;
+    pair_hop<0, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<0, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<1, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<1, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<2, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<2, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<3, 0, SF>(a, mk, s, c, hl, au, ald, alo);
+    pair_hop<3, 1, SF>(a, mk, s, c, hl, au, ald, alo);
+    // lower spin 2 + hl: own z, t part + the partner's x, y part
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const Cx<double> o = shfl_xor_cx(alo[col], 1);
+      ald[col] = cx(ald[col].re + o.re, ald[col].im + o.im);
+    }
+    if (!live) continue;  // after the shuffle: the loop condition is warp-uniform
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      Cx<double> up = au[col], lo = ald[col];
+      if (EPI == EPI_RESID) {
+        const double2 bu = __ldg(a.b.p + (size_t)(3 * hl + col) * V + s);
+        const double2 bl = __ldg(a.b.p + (size_t)(3 * (2 + hl) + col) * V + s);
+        up = cx(bu.x - up.re, bu.y - up.im);
+        lo = cx(bl.x - lo.re, bl.y - lo.im);
+      }
+      a.out.p[(size_t)(3 * hl + col) * V + s] = make_double2(up.re, up.im);
+      a.out.p[(size_t)(3 * (2 + hl) + col) * V + s] = make_double2(lo.re, lo.im);
+      n2 = fma(up.re, up.re, n2);
+      n2 = fma(up.im, up.im, n2);
+      n2 = fma(lo.re, lo.re, n2);
+      n2 = fma(lo.im, lo.im, n2);
+    }
+  }
+  return n2;
+}
+
+// ---------------------------------------------------------------- even-odd (Schur) hopping
+//
+// With all extents even, sites split into parities p = (x + y + z + t) mod 2 and the hopping term
+// H of D = 1 - kappa H only connects opposite parities. An even-odd context stores every field in
+// parity order: site (x, y, z, t) of parity p sits at s = p * V/2 + (x/2 + Lx/2 (y + Ly (z + Lz t))).
+// The half kernel computes, for every site of output parity p,
+//   out = [b -] ([self] + c * H in)           c = sign * kappa (kappa read from device memory)
+// with `in` read on parity 1 - p. M = 1 - kappa^2 H_eo H_oe on the even sites is two launches:
+// t_o = kappa H_oe x_e, then M x_e = x_e - kappa H_eo t_o.
+
+struct EoArgsBase {
+  Geom g;
+  int parity;         // output parity
+  double sign;        // c = sign * kappa
+  const double* kappa_dev;
+  const int* skip;
+  double* partials;
+  unsigned* ticket;
+  double* result;
+};
+
+template <int SP, bool C12>
+struct EoArgs {
+  EoArgsBase e;
+  GaugeRef<typename RealOf<SP>::type, C12> u;
+  SpinorRef<SP> in, out, self, b;
+};
+
+// full coordinates of half index i of parity p
+__device__ __forceinline__ void eo_coords(const Geom& g, int i, int p, int (&c)[4]) {
+  const int lxh = g.L[0] >> 1;
+  int r = i;
+  const int xh = r % lxh;
+  r /= lxh;
+  c[1] = r % g.L[1];
+  r /= g.L[1];
+  c[2] = r % g.L[2];
+  c[3] = r / g.L[2];
+  c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
+}
+
+__device__ __forceinline__ int eo_index(const Geom& g, const int (&c)[4]) {
+  const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+  return par * (g.V >> 1) + (c[0] >> 1) + (g.L[0] >> 1) * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
+}
+
+template <int MU, int SF, int SP, bool C12, typename R>
+__device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int s, const int (&c)[4],
+                                            Cx<R> (&acc)[12]) {
+  const int V = a.e.g.V;
+  {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    const bool wrap = n[MU] == a.e.g.L[MU] - 1;
+    n[MU] = wrap ? 0 : n[MU] + 1;
+    const int nb = eo_index(a.e.g, n);
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
+    spin_project<MU, SF>(psi, h);
+    load_link(a.u, MU, s, V, u);
+    su3_mul(u, h, chi);
+    spin_reconstruct<MU, SF>(acc, chi, k);
+  }
+  {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    const bool wrap = n[MU] == 0;
+    n[MU] = wrap ? a.e.g.L[MU] - 1 : n[MU] - 1;
+    const int nb = eo_index(a.e.g, n);
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
+    spin_project<MU, -SF>(psi, h);
+    load_link(a.u, MU, nb, V, u);
+    su3_dag_mul(u, h, chi);
+    spin_reconstruct<MU, -SF>(acc, chi, k);
+  }
+}
+
+template <int SF, int SP, bool C12, typename R>
+__device__ __forceinline__ void eo_hops_rt(const EoArgs<SP, C12>& a, R k0, int s, const int (&c)[4],
+                                           Cx<R> (&acc)[12]) {
+  const int V = a.e.g.V;
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int mu = hop >> 1, dir = hop & 1;
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    const int L = a.e.g.L[mu];
+    const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+    const bool wrap = dir == 0 ? cm == L - 1 : cm == 0;
+    const int nm = dir == 0 ? (wrap ? 0 : cm + 1) : (wrap ? L - 1 : cm - 1);
+    if (mu == 0) n[0] = nm; else if (mu == 1) n[1] = nm; else if (mu == 2) n[2] = nm; else n[3] = nm;
+    const int nb = eo_index(a.e.g, n);
+    const R k = (wrap && a.e.g.bc[mu] < 0) ? -k0 : k0;
+    const int S = dir == 0 ? SF : -SF;
+    Cx<R> psi[12], h[6], u[9], chi[6];
+    load_spinor(a.in, nb, V, psi);
+    spin_project_rt(mu, S, psi, h);
+    load_link(a.u, mu, dir == 0 ? s : nb, V, u);
+    if (dir == 0)
+      su3_mul(u, h, chi);
+    else
+      su3_dag_mul(u, h, chi);
+    spin_reconstruct_rt(mu, S, acc, chi, k);
+  }
+}
+
+// Half-site i of the output parity: out = [b -] ([self] + c * H in); returns |out|^2.
+template <int SP, bool C12, bool DAG, bool SELF, bool RESID>
+__device__ __forceinline__ double eo_site(const EoArgs<SP, C12>& a, int i) {
+  typedef typename RealOf<SP>::type R;
+  const int Vh = a.e.g.V >> 1, V = a.e.g.V;
+  const int p = a.e.parity;
+  int c[4];
+  eo_coords(a.e.g, i, p, c);
+  const int s = p * Vh + i;
+  const R k0 = (R)(a.e.sign * *a.e.kappa_dev);
+  Cx<R> acc[12];
+  if (SELF) {
+    load_spinor(a.self, s, V, acc);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = cx<R>(0, 0);
+  }
+  constexpr int SF = DAG ? +1 : -1;
+  if constexpr (SP == PDF) {
+    eo_hops_rt<SF>(a, k0, s, c, acc);
+  } else {
+    eo_hop_pair<0, SF>(a, k0, s, c, acc);
+    eo_hop_pair<1, SF>(a, k0, s, c, acc);
+    eo_hop_pair<2, SF>(a, k0, s, c, acc);
+    eo_hop_pair<3, SF>(a, k0, s, c, acc);
+  }
+  if (RESID) {
+    Cx<R> bv[12];
+    load_spinor(a.b, s, V, bv);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = cx<R>(bv[j].re - acc[j].re, bv[j].im - acc[j].im);
+  }
+  store_spinor(a.out, s, V, acc);
+  return norm2_site(acc);
+}
+
+}  // namespace wdk
