@@ -99,11 +99,15 @@ enum {
                                 x directly (x += alpha D^dag p), so x on input is the initial
                                 guess in both forms. Same two operator applications, stopping
                                 rule and true residual; mixed-precision contexts reject 1.       */
-  WD_OPT_DSLASH_VARIANT = 11 /* FP64 single-RHS dslash (FP64 contexts, and the reliable updates
+  WD_OPT_DSLASH_VARIANT = 11,/* FP64 single-RHS dslash (FP64 contexts, and the reliable updates
                                 of mixed ones): 0 (default) chosen with the block size on first
                                 use; 1 one thread per site; 2 two threads per site (each owns one
                                 half-spinor row). Lexicographic layout only: even-odd contexts
                                 ignore it.                                                       */
+  WD_OPT_LOOP_WAIT_LIMIT = 12 /* persistent loop: polls of 64 ns before a grid-barrier wait gives
+                                up and cg_solve returns WD_ECUDA ("a grid barrier wait gave
+                                up"), leaving the context usable; 0 or 2^26 (default, about
+                                4 s). Small values exercise that failure path.                  */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

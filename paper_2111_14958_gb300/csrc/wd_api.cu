@@ -80,6 +80,7 @@ struct wd_ctx {
   size_t partials_len;
   double* loop_partials;   // persistent CG loop: 3 x kLoopMaxGrid block partials
   unsigned* loop_sync;     // persistent CG loop: barrier arrivals, generation, error flag
+  long long loop_wait_limit;  // grid-barrier polls before a wait gives up (WD_OPT_LOOP_WAIT_LIMIT)
   CgScalars* sc;
   CgScalars* sc_host;  // pinned
 
@@ -582,6 +583,7 @@ wd_status run_persistent(wd_ctx* c, double* loop_ms) {
   L.err = reinterpret_cast<int*>(c->loop_sync + 2);
   L.block = dslash_block(c, c->wprec);
   L.max_grid = kLoopMaxGrid;
+  L.wait_limit = c->loop_wait_limit;
   L.variant = dslash_variant(c, c->wprec);
   L.t = c->t;
   WD_CUDA(cudaEventRecord(c->ev0, c->stream));
@@ -623,6 +625,7 @@ wd_status run_mixed_persistent(wd_ctx* c, double* loop_ms) {
   L.err = reinterpret_cast<int*>(c->loop_sync + 2);
   L.block = dslash_block(c, c->wprec);
   L.max_grid = kLoopMaxGrid;
+  L.wait_limit = c->loop_wait_limit;
   for (int launch = 0;; ++launch) {
     L.start_b = launch > 0;
     WD_CUDA(cudaEventRecord(c->ev0, c->stream));
@@ -1267,6 +1270,7 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
   c->stream = (cudaStream_t)cuda_stream;
   c->delta = 0.1;  // a reliable update each time |r| has dropped 10x
   c->use_graph = 3;
+  c->loop_wait_limit = kLoopWaitLimit;
   c->block_blas = 256;
   c->max_restarts = 5;
   wd_status st = WD_OK;
@@ -1435,6 +1439,12 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
         return fail(WD_EINVAL, "two threads per site is an FP64 dslash variant");
       c->force_var = v;
       destroy_graph(c);
+      return WD_OK;
+    }
+    case WD_OPT_LOOP_WAIT_LIMIT: {
+      if (!(value >= 0.0 && value <= (double)kLoopWaitLimit) || value != std::floor(value))
+        return fail(WD_EINVAL, "loop wait limit must be an integer in [0, 2^26]");
+      c->loop_wait_limit = value == 0.0 ? kLoopWaitLimit : (long long)value;
       return WD_OK;
     }
     case WD_OPT_CG_FORM: {

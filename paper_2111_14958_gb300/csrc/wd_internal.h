@@ -114,7 +114,9 @@ struct CgLoopCall {
   int variant;  // FP64: 1 = the dslash phases use two lanes per site
   int start_b;  // mixed loop: resume at the D^dag half of an iteration (after a reliable update)
   FieldPtr t;   // even-odd loop: the odd-site temporary
+  long long wait_limit;  // grid-barrier polls (64 ns sleep each) before a wait gives up
 };
+constexpr long long kLoopWaitLimit = 1LL << 26;  // about 4 s
 cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st);
 // The inner loop of the mixed-precision solver (x = x_lo in FP32; r, p, q, s in the working
 // precision) as one cooperative launch that returns when a reliable update is due or the loop ends.

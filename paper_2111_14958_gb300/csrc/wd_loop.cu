@@ -14,11 +14,10 @@ namespace wdk {
 // completes; its wait is still bounded: past the limit the kernel records an error and stops.
 
 struct LoopSync {
-  unsigned* bar;  // [0] arrivals, [1] generation
-  int* err;       // set to 1 when a barrier wait gave up
+  unsigned* bar;    // [0] arrivals, [1] generation
+  int* err;         // set to 1 when a barrier wait gave up
+  long long limit;  // polls (64 ns sleep each) before a wait gives up
 };
-
-constexpr long long kBarrierSpinLimit = 1LL << 26;  // x 64 ns sleep: about 4 s
 
 // All blocks arrive, then continue. Returns false (everywhere, eventually) if a wait gave up.
 __device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
@@ -37,7 +36,7 @@ __device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
     } else {
       long long spins = 0;
       while (*gen == g0) {
-        if (++spins > kBarrierSpinLimit || *(volatile int*)y.err) {
+        if (++spins > y.limit || *(volatile int*)y.err) {
           atomicExch(y.err, 1);
           good = 0;
           break;
@@ -354,6 +353,7 @@ static cudaError_t mixed_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   a.sc = c.sc;
   a.partials = c.partials;
   a.y.bar = c.bar;
+  a.y.limit = c.wait_limit;
   a.y.err = c.err;
   auto k = cg_mixed_loop_kernel<SPW, C12>;
   int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
@@ -401,6 +401,7 @@ static cudaError_t loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   a.sc = c.sc;
   a.partials = c.partials;
   a.y.bar = c.bar;
+  a.y.limit = c.wait_limit;
   a.y.err = c.err;
   auto k = cg_loop_kernel<SP, C12, PAIR>;
   int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
@@ -578,6 +579,7 @@ static cudaError_t eo_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   a.sc = c.sc;
   a.partials = c.partials;
   a.y.bar = c.bar;
+  a.y.limit = c.wait_limit;
   a.y.err = c.err;
   auto k = cg_eo_loop_kernel<SP, C12>;
   int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);

@@ -55,6 +55,7 @@ WD_OPT_DF_UPDATES = 8
 WD_OPT_APPLY_DF = 9
 WD_OPT_CG_FORM = 10
 WD_OPT_DSLASH_VARIANT = 11
+WD_OPT_LOOP_WAIT_LIMIT = 12
 
 
 class WdMultiStats(ctypes.Structure):

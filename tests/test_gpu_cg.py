@@ -363,3 +363,28 @@ def test_persistent_mixed_loop_edge_cases():
     x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
     assert st == wd.WD_OK and ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10
     op.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed16"])
+def test_persistent_loop_wait_limit_reports_and_recovers(prec):
+    """Failure detection without a GPU fault: with a grid-barrier wait limit of a single poll the
+    persistent loop's waits run out, the kernel stops and cg_solve reports WD_ECUDA; with the
+    limit restored the same context solves again."""
+    wd = require_gpu()
+    dims = (8, 8, 8, 8)
+    U, eta = fields(dims)
+    p = wd.WD_PREC_F64 if prec == "f64" else wd.WD_PREC_MIXED_F16
+    op = wd.WilsonDirac(dims, 0.12, BC, p)
+    op.load_gauge(to_dev(U), compress12=prec != "f64")
+    op.set_option(wd.WD_OPT_USE_GRAPH, 2)
+    op.set_option(wd.WD_OPT_LOOP_WAIT_LIMIT, 1)
+    with pytest.raises(wd.WdError) as e:
+        op.solve(to_dev(eta), tol=1e-10)
+    assert e.value.status == wd.WD_ECUDA
+    assert "barrier" in wd.wd_last_error()
+    op.set_option(wd.WD_OPT_LOOP_WAIT_LIMIT, 0)          # back to the default limit
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+    assert st == wd.WD_OK and ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10
+    with pytest.raises(wd.WdError):
+        op.set_option(wd.WD_OPT_LOOP_WAIT_LIMIT, -1)
+    op.close()
