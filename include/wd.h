@@ -104,10 +104,13 @@ enum {
                                 use; 1 one thread per site; 2 two threads per site (each owns one
                                 half-spinor row). Lexicographic layout only: even-odd contexts
                                 ignore it.                                                       */
-  WD_OPT_LOOP_WAIT_LIMIT = 12 /* persistent loop: polls of 64 ns before a grid-barrier wait gives
+  WD_OPT_LOOP_WAIT_LIMIT = 12,/* persistent loop: polls of 64 ns before a grid-barrier wait gives
                                 up and cg_solve returns WD_ECUDA ("a grid barrier wait gave
                                 up"), leaving the context usable; 0 or 2^26 (default, about
                                 4 s). Small values exercise that failure path.                  */
+  WD_OPT_RESIDUAL_HISTORY = 13 /* cg_solve records the recursive residual of its first N
+                                iterations (N = value, 0 = off, the default) for
+                                wd_get_residual_history                                          */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */
@@ -308,6 +311,13 @@ wd_status wd_coo_build(wd_ctx* ctx, const double* U, int* row, int* col, double*
                        long long* nnz);
 wd_status wd_coo_spmv(wd_ctx* ctx, long long nnz, const int* row, const int* col, const double* val,
                       const double* in, double* out);
+
+/* Recursive relative residual ||r_k|| / ||eta|| after each CG iteration k of the last cg_solve
+ * (the residual the stopping rule tests: in mixed precision that of the inner solver, before any
+ * reliable update of that iteration), for the first min(iterations, WD_OPT_RESIDUAL_HISTORY,
+ * max_entries) iterations. out: host array of max_entries doubles; *count: entries written.
+ * Returns WD_EINVAL for null pointers or a negative length. */
+wd_status wd_get_residual_history(const wd_ctx* ctx, double* out, int max_entries, int* count);
 
 /* Set an option (WD_OPT_*). Returns WD_EINVAL for an unknown key or a value out of range. */
 wd_status wd_set_option(wd_ctx* ctx, int key, double value);

@@ -81,6 +81,8 @@ struct wd_ctx {
   double* loop_partials;   // persistent CG loop: 3 x kLoopMaxGrid block partials
   unsigned* loop_sync;     // persistent CG loop: barrier arrivals, generation, error flag
   long long loop_wait_limit;  // grid-barrier polls before a wait gives up (WD_OPT_LOOP_WAIT_LIMIT)
+  double* hist_dev;        // recursive ||r||^2 per iteration (WD_OPT_RESIDUAL_HISTORY entries)
+  int hist_cap;
   CgScalars* sc;
   CgScalars* sc_host;  // pinned
 
@@ -675,8 +677,10 @@ wd_status run_host_loop(wd_ctx* c) {
   return WD_OK;
 }
 
-__global__ void set_params_kernel(CgScalars* sc, double tol2, double delta2, int maxit, double* eta2_src) {
+__global__ void set_params_kernel(CgScalars* sc, double tol2, double delta2, int maxit, double* hist, int hist_len) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc->hist = hist;
+    sc->hist_len = hist_len;
     sc->tol2 = tol2;
     sc->delta2 = delta2;
     sc->maxit = maxit;
@@ -1363,6 +1367,7 @@ void wd_destroy(wd_ctx* c) {
   if (c->staging) cudaFree(c->staging);
   if (c->partials) cudaFree(c->partials);
   if (c->loop_partials) cudaFree(c->loop_partials);
+  if (c->hist_dev) cudaFree(c->hist_dev);
   if (c->loop_sync) cudaFree(c->loop_sync);
   if (c->sc) cudaFree(c->sc);
   if (c->sc_host) cudaFreeHost(c->sc_host);
@@ -1439,6 +1444,24 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
         return fail(WD_EINVAL, "two threads per site is an FP64 dslash variant");
       c->force_var = v;
       destroy_graph(c);
+      return WD_OK;
+    }
+    case WD_OPT_RESIDUAL_HISTORY: {
+      const int n = (int)value;
+      if (value != (double)n || n < 0 || n > 10000000) return fail(WD_EINVAL, "history length must be in [0, 10^7]");
+      if (n != c->hist_cap) {
+        if (c->hist_dev) cudaFree(c->hist_dev);
+        c->hist_dev = nullptr;
+        c->hist_cap = 0;
+        if (n > 0) {
+          if (cudaMalloc(&c->hist_dev, sizeof(double) * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(WD_ENOMEM, "cudaMalloc of the residual history failed");
+          }
+          c->hist_cap = n;
+        }
+        destroy_graph(c);  // the graph's parameter kernel holds the history pointer
+      }
       return WD_OK;
     }
     case WD_OPT_LOOP_WAIT_LIMIT: {
@@ -1572,7 +1595,7 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
   // inputs into the device layout: eta with ||eta||^2, x = initial guess
   FieldPtr eta = mixed ? c->eta64 : c->eta;
   FieldPtr xs = mixed ? c->x64 : c->x;
-  set_params_kernel<<<1, 32, 0, c->stream>>>(sc, tol * tol, c->delta * c->delta, maxit, nullptr);
+  set_params_kernel<<<1, 32, 0, c->stream>>>(sc, tol * tol, c->delta * c->delta, maxit, c->hist_dev, c->hist_cap);
   WD_CUDA(cudaGetLastError());
   WD_CUDA(launch_pack((const double*)src, eta, c->V, eo_geom(c), red_to(c, TK_PACK, &sc->eta2), bb, c->stream));
   WD_CUDA(launch_pack((const double*)x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
@@ -1646,6 +1669,21 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
     ret = fail(WD_NOT_CONVERGED, "maximum iterations reached before the true residual met tol");
   c->stats.status = ret;
   return ret;
+}
+
+wd_status wd_get_residual_history(const wd_ctx* c, double* out, int max_entries, int* count) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!out || !count || max_entries < 0) return fail(WD_EINVAL, "null argument or negative length");
+  int n = c->stats.iterations;
+  if (n > c->hist_cap) n = c->hist_cap;
+  if (n > max_entries) n = max_entries;
+  *count = n;
+  if (n == 0) return WD_OK;
+  WD_CUDA(cudaMemcpy(out, c->hist_dev, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+  const double eta2 = c->sc_host->eta2;
+  for (int i = 0; i < n; ++i) out[i] = eta2 > 0.0 ? std::sqrt(out[i] / eta2) : std::sqrt(out[i]);
+  return WD_OK;
 }
 
 wd_status wd_time_dslash(wd_ctx* c, int dagger, int launches, double* avg_ms) {

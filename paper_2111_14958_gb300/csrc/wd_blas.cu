@@ -346,6 +346,7 @@ __global__ void cg_update_r_kernel(SpinorRef<SP> r, SpinorRef<SP> q, int n, int 
   if (grid_reduce<OpSum, 1>(v, partials, &sc->ticket[TK_UPD_R], tot) && threadIdx.x == 0) {
     sc->alpha = alpha;
     sc->rr = tot[0];
+    record_residual(sc, sc->iter, tot[0]);
     if (gamma_from_rr) sc->gamma_new = tot[0];
     if (!ok || !isfinite(tot[0]))
       sc->status = ST_BREAKDOWN;
@@ -514,6 +515,7 @@ __global__ void mp_update_rx_kernel(SpinorRef<SPW> r, SpinorRef<SPW> q, SpinorRe
       } else {
         sc->alpha = alpha;
         sc->rr = tot[0];
+        record_residual(sc, sc->iter, tot[0]);
         need = (tot[0] <= sc->delta2 * sc->rr_ref) || (tot[0] <= sc->tol2 * sc->eta2);
       }
     }

@@ -40,6 +40,10 @@ struct GaugePtr {
 };
 
 // Device-resident solver scalars (one per context). Layout shared with the kernels.
+struct CgScalars;
+// Record the recursive residual of iteration `it` if the solve keeps a history (device side).
+__device__ __forceinline__ void record_residual(CgScalars* sc, int it, double rr);
+
 struct CgScalars {
   double eta2;       // ||eta||^2
   double rr;         // recursive ||r||^2
@@ -55,15 +59,20 @@ struct CgScalars {
   double delta2;     // mixed precision: reliable-update trigger factor, squared
   double kappa;      // hopping parameter read by every dslash of the context (settable between solves)
   double scratch[4];
+  double* hist;      // optional: recursive ||r||^2 of each iteration (index = iteration)
+  int hist_len;      // entries hist holds (0: no history)
   int iter;          // cumulative iterations
   int maxit;
   int status;        // ST_* below
   int updates;       // reliable updates done
   int need_update;   // mixed precision: set when ||r|| dropped by delta since the last update
   int no_update;     // = !need_update (skip flag of the FP64 dslash in the update)
-  int pad[2];
   unsigned ticket[16];
 };
+
+__device__ __forceinline__ void record_residual(CgScalars* sc, int it, double rr) {
+  if (sc->hist != nullptr && it >= 0 && it < sc->hist_len) sc->hist[it] = rr;
+}
 
 enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_BREAKDOWN = 3, ST_PENDING = 4 };
 

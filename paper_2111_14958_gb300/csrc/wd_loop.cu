@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
       v += norm2_site(rv);
     }
     if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr);
     if (!isfinite(rr)) {
       status = ST_BREAKDOWN;
       break;
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SPW>::value
       store_spinor(a.xlo, i, V, xv);
     }
     if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr);
     if (!isfinite(rr)) {
       status = ST_BREAKDOWN;
       break;
@@ -483,6 +485,7 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
       v += norm2_site(rv);
     }
     if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr);
     if (!isfinite(rr)) {
       status = ST_BREAKDOWN;
       break;

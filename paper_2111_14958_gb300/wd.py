@@ -56,6 +56,7 @@ WD_OPT_APPLY_DF = 9
 WD_OPT_CG_FORM = 10
 WD_OPT_DSLASH_VARIANT = 11
 WD_OPT_LOOP_WAIT_LIMIT = 12
+WD_OPT_RESIDUAL_HISTORY = 13
 
 
 class WdMultiStats(ctypes.Structure):
@@ -106,6 +107,7 @@ _sig = {
     "cg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "wd_set_option": (_I, [_P, _I, _D]),
     "wd_get_stats": (_I, [_P, ctypes.POINTER(WdStats)]),
+    "wd_get_residual_history": (_I, [_P, ctypes.POINTER(_D), _I, ctypes.POINTER(_I)]),
     "wd_time_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_D)]),
     "wd_apply_multi": (_I, [_P, _P, _P, _I, _I]),
     "cg_solve_multi": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -297,6 +299,13 @@ def wd_get_stats(ctx) -> dict:
     return {name: getattr(s, name) for name, _ in WdStats._fields_}
 
 
+def wd_get_residual_history(ctx, max_entries: int = 1 << 16) -> list:
+    buf = (_D * max_entries)()
+    n = _I(0)
+    _check(_lib.wd_get_residual_history(_P(ctx), buf, int(max_entries), ctypes.byref(n)), "wd_get_residual_history")
+    return list(buf[: n.value])
+
+
 def wd_time_dslash(ctx, dagger: bool = False, launches: int = 20) -> float:
     ms = _D(0.0)
     _check(_lib.wd_time_dslash(_P(ctx), int(bool(dagger)), int(launches), ctypes.byref(ms)), "wd_time_dslash")
@@ -358,6 +367,9 @@ class WilsonDirac:
 
     def stats(self):
         return wd_get_stats(self.ctx)
+
+    def residual_history(self, max_entries: int = 1 << 16):
+        return wd_get_residual_history(self.ctx, max_entries)
 
     def time_dslash(self, dagger=False, launches=20) -> float:
         return wd_time_dslash(self.ctx, dagger, launches)

@@ -388,3 +388,51 @@ def test_persistent_loop_wait_limit_reports_and_recovers(prec):
     with pytest.raises(wd.WdError):
         op.set_option(wd.WD_OPT_LOOP_WAIT_LIMIT, -1)
     op.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_residual_history_matches_the_oracle(mode):
+    """The recursive residual after every iteration, for the host loop, the graph and the
+    persistent loop, against the oracle's CGLS history (entry k + 1 there: it starts with the
+    initial residual)."""
+    wd = require_gpu()
+    dims = (4, 4, 4, 6)
+    U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_F64)
+    op.load_gauge(to_dev(U))
+    op.set_option(wd.WD_OPT_USE_GRAPH, mode)
+    op.set_option(wd.WD_OPT_RESIDUAL_HISTORY, 500)
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+    assert st == wd.WD_OK
+    h = np.array(op.residual_history())
+    assert len(h) == iters and h[-1] <= 1e-10 < h[-2]
+    assert np.all(h[1:] <= h[:-1] * (1 + 1e-9))           # CGLS: ||eta - D x_k|| does not grow
+    _, io, _, ho = ocg.cgls(U, eta, 0.12, 1e-10, 2000)
+    n = min(len(h), len(ho) - 1)
+    assert abs(len(h) - io) <= 1
+    assert np.max(np.abs(h[:20] / ho[1:21] - 1)) < 1e-9     # rounding-order differences only
+    assert np.max(np.abs(h[:n] / ho[1:n + 1] - 1)) < 1e-3
+    op.set_option(wd.WD_OPT_RESIDUAL_HISTORY, 10)           # shorter history: the first entries
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+    h10 = np.array(op.residual_history())
+    assert len(h10) == 10 and np.allclose(h10, h[:10], rtol=1e-12)
+    op.close()
+
+
+def test_residual_history_mixed_and_off():
+    wd = require_gpu()
+    dims = (6, 4, 4, 8)
+    U, eta = fields(dims)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_MIXED_F16)
+    op.load_gauge(to_dev(U), compress12=True)
+    assert op.residual_history() == []                      # no solve yet, history off
+    op.set_option(wd.WD_OPT_RESIDUAL_HISTORY, 1000)
+    x, iters, res, st = op.solve(to_dev(eta), tol=1e-10)
+    h = op.residual_history()
+    assert st == wd.WD_OK and len(h) == iters and h[-1] <= 1.1e-10
+    op.set_option(wd.WD_OPT_RESIDUAL_HISTORY, 0)
+    op.solve(to_dev(eta), tol=1e-10)
+    assert op.residual_history() == []
+    with pytest.raises(wd.WdError):
+        op.set_option(wd.WD_OPT_RESIDUAL_HISTORY, -2)
+    op.close()
