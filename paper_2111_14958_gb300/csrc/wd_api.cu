@@ -726,6 +726,7 @@ void tune_store(const TuneKey& k, int* a, int* b) {
 // size is timed per problem shape and precision on first use (CUDA events, the context's own
 // fields) and shared with later contexts of the same shape.
 wd_status autotune_single(wd_ctx* c) {
+  NvtxRange nvtx_("wd:autotune");
   if (c->block_dslash > 0) return WD_OK;
   const int precs[3] = {c->wprec, (is_mixed(c->precision) ? SP64 : -1), (c->use_df ? SPDF : -1)};
   for (int prec : precs) {
@@ -914,6 +915,7 @@ wd_status time_multi_shape(wd_ctx* c, FieldPtr in, FieldPtr out, int K, int spb,
 // Time candidate launch shapes of the multi-RHS dslash on the context's fields; keep the fastest
 // (shared with later contexts of the same problem shape, like the single-RHS block size).
 wd_status autotune_multi(wd_ctx* c, FieldPtr in, FieldPtr out, bool f64) {
+  NvtxRange nvtx_("wd:autotune_multi");
   const int N = c->mN;
   int bestK = N, bestS = 256 / N;
   float best = 1e30f;
@@ -1496,6 +1498,7 @@ wd_status wd_get_stats(const wd_ctx* c, wd_stats* out) {
 }
 
 wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress12, double* max_unitarity_dev) {
+  NvtxRange nvtx_("wd:load_gauge");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!U) return fail(WD_EINVAL, "U is null");
@@ -1553,6 +1556,7 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
 }
 
 wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
+  NvtxRange nvtx_("wd:apply");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!in || !out) return fail(WD_EINVAL, "null field pointer");
@@ -1582,6 +1586,7 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
 }
 
 wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, int* iters, double* true_rel_res) {
+  NvtxRange nvtx_("wd:cg_solve");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!src || !x) return fail(WD_EINVAL, "null field pointer");
@@ -1713,6 +1718,7 @@ wd_status wd_get_multi_stats(const wd_ctx* c, wd_multi_stats* out) {
 }
 
 wd_status wd_apply_multi(wd_ctx* c, const double* in, double* out, int nrhs, int dagger) {
+  NvtxRange nvtx_("wd:apply_multi");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!in || !out || in == out) return fail(WD_EINVAL, "null or aliased field pointer");
@@ -1735,6 +1741,7 @@ wd_status wd_apply_multi(wd_ctx* c, const double* in, double* out, int nrhs, int
 
 wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, double tol, int maxit, int* iters,
                          double* true_rel_res) {
+  NvtxRange nvtx_("wd:cg_solve_multi");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!src || !x) return fail(WD_EINVAL, "null field pointer");
@@ -1823,6 +1830,7 @@ wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, doub
 }
 
 wd_status wd_generate_gauge(wd_ctx* c, double eps, unsigned long long seed, int compress12, double* U_out) {
+  NvtxRange nvtx_("wd:generate_gauge");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
   if (!std::isfinite(eps)) return fail(WD_EINVAL, "eps must be finite");

@@ -7,9 +7,19 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace wdk {
+
+// NVTX range over a scope (shows the library's phases in Nsight timelines; free without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct Geom;  // defined in wd_device.cuh; mirrored by GeomH below
 

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/wd.h"
 
@@ -147,6 +148,10 @@ wd_status prepare(Slot* s, const wd_request& r, Resident** out) {
 }
 
 void run_job(Slot* s, Job* j) {
+  nvtxRangePushA("wd:serve_job");
+  struct PopRange {
+    ~PopRange() { nvtxRangePop(); }
+  } pop_;
   const wd_request& r = j->req;
   wd_result& out = j->res;
   memset(&out, 0, sizeof(out));
