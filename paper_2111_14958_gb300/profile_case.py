@@ -8,8 +8,11 @@ Examples:
       --apply 3 --apply-df        # the double-float dslash (through wd_apply)
   python -m paper_2111_14958_gb300.profile_case --prec 6432 --c12 --dims 16,16,16,32 --launches 0 \
       --multi 12                  # the multi-RHS dslash (through wd_apply_multi)
+  python -m paper_2111_14958_gb300.profile_case --prec 6432 --c12 --dims 24,24,24,48 --launches 0 \
+      --device-fields --msolve 12 # one multi-RHS mixed-precision solve of 12 Gaussian sources
 
-Fields come from the seeded generators (links exp(i 0.4 H), Gaussian source); the program prints
+Fields come from the seeded generators (links exp(i 0.4 H), Gaussian source; on the host, or with
+--device-fields from the library's own generators on the device); the program prints
 the timing of the dslash as the solver launches it (CUDA events) and, with --solve, one CG solve.
 """
 from __future__ import annotations
@@ -41,6 +44,8 @@ def main(argv=None):
     ap.add_argument("--multi", type=int, default=0, help="wd_apply_multi calls on this many Gaussian fields")
     ap.add_argument("--mgroup", type=int, default=0, help="multi-RHS group size K (0 = tuned)")
     ap.add_argument("--msites", type=int, default=0, help="multi-RHS sites per block (0 = tuned)")
+    ap.add_argument("--msolve", type=int, default=0, help="one cg_solve_multi on this many Gaussian sources")
+    ap.add_argument("--device-fields", action="store_true", help="generate links and sources on the device")
     args = ap.parse_args(argv)
 
     import torch
@@ -49,10 +54,17 @@ def main(argv=None):
     from paper_2111_14958_gb300 import wd
 
     dims = tuple(int(v) for v in args.dims.split(","))
-    U = torch.from_numpy(synthetic.gauge_field(dims, 0.4, 1)).cuda()
     prec = args.prec | (wd.WD_EVEN_ODD if args.even_odd else 0)
     op = wd.WilsonDirac(dims, args.kappa, (1, 1, 1, -1), prec)
-    op.load_gauge(U, compress12=args.c12)
+    if args.device_fields:
+        op.generate_gauge(0.4, 1, compress12=args.c12)
+    else:
+        op.load_gauge(torch.from_numpy(synthetic.gauge_field(dims, 0.4, 1)).cuda(), compress12=args.c12)
+
+    def source(seed):
+        if args.device_fields:
+            return op.generate_source(seed)
+        return torch.from_numpy(synthetic.gaussian_source(dims, seed)).cuda()
     if args.block:
         op.set_option(wd.WD_OPT_BLOCK_DSLASH, args.block)
     if args.launches:
@@ -61,7 +73,7 @@ def main(argv=None):
     if args.apply:
         if args.apply_df:
             op.set_option(wd.WD_OPT_APPLY_DF, 1)
-        psi = torch.from_numpy(synthetic.gaussian_source(dims, 3)).cuda()
+        psi = source(3)
         if args.prec == wd.WD_PREC_F32:
             psi = psi.to(torch.complex64)
         out = torch.empty_like(psi)
@@ -77,7 +89,7 @@ def main(argv=None):
             op.set_option(wd.WD_OPT_MULTI_GROUP, args.mgroup)
         if args.msites:
             op.set_option(wd.WD_OPT_MULTI_SITES, args.msites)
-        psi = torch.stack([torch.from_numpy(synthetic.gaussian_source(dims, 10 + i)) for i in range(args.multi)]).cuda()
+        psi = torch.stack([source(10 + i) for i in range(args.multi)])
         out = op.apply_multi(psi)  # tunes the launch shape
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -88,8 +100,16 @@ def main(argv=None):
         st = op.multi_stats()
         print(f"wd_apply_multi x3 ({args.multi} RHS): {a.elapsed_time(b) / 3 * 1e3:.1f} us per call with packing; "
               f"tuned group {st['group']} sites/block {st['sites_per_block']} dslash {st['dslash_ms'] * 1e3:.1f} us")
+    if args.msolve:
+        eta = torch.stack([source(100 + i) for i in range(args.msolve)])
+        x = torch.zeros_like(eta)
+        st, iters, res = wd.cg_solve_multi(op.ctx, eta, x, args.tol, 20000)
+        ms = wd.wd_get_multi_stats(op.ctx)
+        print(f"cg_solve_multi ({args.msolve} RHS): status {st} iterations {max(iters)} "
+              f"max true residual {max(res):.3e} reliable updates {ms['reliable_updates']} "
+              f"group {ms['group']} sites/block {ms['sites_per_block']}")
     if args.solve:
-        eta = torch.from_numpy(synthetic.gaussian_source(dims, 2)).cuda()
+        eta = source(2)
         x, iters, res, status = op.solve(eta, tol=args.tol, maxit=4000)
         s = op.stats()
         print(f"solve: status {status} iterations {iters} true residual {res:.3e} "
