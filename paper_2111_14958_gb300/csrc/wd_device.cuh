@@ -394,6 +394,44 @@ __device__ __forceinline__ void spin_reconstruct(Cx<R> (&acc)[12], const Cx<R> (
   }
 }
 
+// acc += k * [up ; S B^dag lo]: the reconstruction of spin_reconstruct with separate half-spinors
+// for the upper and the lower spins (the two hops of one direction combined, see hop_pair)
+template <int MU, int S, typename R>
+__device__ __forceinline__ void spin_reconstruct2(Cx<R> (&acc)[12], const Cx<R> (&up)[6], const Cx<R> (&lo)[6],
+                                                  R k) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c].re = madd(k, up[c].re, acc[c].re);
+    acc[c].im = madd(k, up[c].im, acc[c].im);
+    acc[3 + c].re = madd(k, up[3 + c].re, acc[3 + c].re);
+    acc[3 + c].im = madd(k, up[3 + c].im, acc[3 + c].im);
+    const Cx<R> c0 = lo[c], c1 = lo[3 + c];
+    Cx<R> l0, l1;
+    if (MU == 0) {
+      l0 = cx<R>(-c1.im, c1.re);
+      l1 = cx<R>(-c0.im, c0.re);
+    } else if (MU == 1) {
+      l0 = c1;
+      l1 = cx<R>(-c0.re, -c0.im);
+    } else if (MU == 2) {
+      l0 = cx<R>(-c0.im, c0.re);
+      l1 = cx<R>(c1.im, -c1.re);
+    } else {
+      l0 = c0;
+      l1 = c1;
+    }
+    acc[6 + c].re = madd(k, sg<S>(l0.re), acc[6 + c].re);
+    acc[6 + c].im = madd(k, sg<S>(l0.im), acc[6 + c].im);
+    acc[9 + c].re = madd(k, sg<S>(l1.re), acc[9 + c].re);
+    acc[9 + c].im = madd(k, sg<S>(l1.im), acc[9 + c].im);
+  }
+}
+
+// Sign flip of a double through its sign bit (an integer operation, off the FP64 pipe).
+__device__ __forceinline__ double flip_sign(double x, unsigned long long m) {
+  return __longlong_as_double(__double_as_longlong(x) ^ m);
+}
+
 // ---------------------------------------------------------------- runtime hop (compact code)
 //
 // The same spin algebra as spin_project / spin_reconstruct, driven by small tables instead of
@@ -482,6 +520,33 @@ __device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6]
       im = madd(u2.re, h2.im, im);
       im = madd(u2.im, h2.re, im);
       chi[3 * sp + a] = cx<R>(re, im);
+    }
+  }
+}
+
+// p = t + U^dag h (the product accumulated onto t: fused multiply-adds only)
+template <typename R>
+__device__ __forceinline__ void su3_dag_mul_add(const Cx<R> (&u)[9], const Cx<R> (&h)[6], const Cx<R> (&t)[6],
+                                                Cx<R> (&p)[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const Cx<R> u0 = u[a], u1 = u[3 + a], u2 = u[6 + a];
+      const Cx<R> h0 = h[3 * sp], h1 = h[3 * sp + 1], h2 = h[3 * sp + 2];
+      R re = madd(u0.re, h0.re, t[3 * sp + a].re);
+      re = madd(u0.im, h0.im, re);
+      re = madd(u1.re, h1.re, re);
+      re = madd(u1.im, h1.im, re);
+      re = madd(u2.re, h2.re, re);
+      re = madd(u2.im, h2.im, re);
+      R im = madd(u0.re, h0.im, t[3 * sp + a].im);
+      im = madd(-u0.im, h0.re, im);
+      im = madd(u1.re, h1.im, im);
+      im = madd(-u1.im, h1.re, im);
+      im = madd(u2.re, h2.im, im);
+      im = madd(-u2.im, h2.re, im);
+      p[3 * sp + a] = cx<R>(re, im);
     }
   }
 }

@@ -50,10 +50,52 @@ struct DslashArgs {
   double* result;
 };
 
+// Both hops of direction mu combined, for the FP64 kernels (bound by their FP64 instruction
+// count). With t = U_mu(n) h_f and the backward product t_b = U_mu(n-mu)^dag h_b, the two hops
+// add k_f t + k_b t_b to the upper spins and k_f S B^dag t - k_b S B^dag t_b to the lower ones.
+// k_b = rho k_f, rho = -1 when exactly one of the two hops crosses an antiperiodic boundary, so
+// the sums are k_f p and k_f S B^dag (2 t - p) with p = t + rho t_b: the backward product
+// accumulates onto t (no separate multiply), and the pair needs 36 reconstruction operations
+// instead of 48. rho is applied to h_b through the sign bits.
+template <int MU, int S_FWD, typename In, typename Gauge, typename R>
+__device__ __forceinline__ void hop_pair_combined(const In& in, const Gauge& gauge, int s, int nbf, int nbb, int V,
+                                                  bool wf, bool wb, bool aper, R mk, Cx<R> (&acc)[12]) {
+  Cx<R> t[6];
+  {
+    Cx<R> psi[12], h[6], u[9];
+    load_spinor(in, nbf, V, psi);
+    spin_project<MU, S_FWD>(psi, h);
+    load_link(gauge, MU, s, V, u);
+    su3_mul(u, h, t);
+  }
+  Cx<R> p[6];
+  {
+    Cx<R> psi[12], h[6], u[9];
+    load_spinor(in, nbb, V, psi);
+    spin_project<MU, -S_FWD>(psi, h);
+    const unsigned long long m = (unsigned long long)(aper && wf != wb) << 63;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) h[i] = cx<R>(flip_sign(h[i].re, m), flip_sign(h[i].im, m));
+    load_link(gauge, MU, nbb, V, u);
+    su3_dag_mul_add(u, h, t, p);
+  }
+  Cx<R> d[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d[i] = cx<R>(madd((R)2, t[i].re, -p[i].re), madd((R)2, t[i].im, -p[i].im));
+  spin_reconstruct2<MU, S_FWD>(acc, p, d, (aper && wf) ? -mk : mk);
+}
+
 template <int MU, int S_FWD, int SP, bool C12, typename R>
 __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int s, const int (&c)[4],
                                          Cx<R> (&acc)[12]) {
   const int V = a.g.V;
+  if constexpr (SP == P64) {
+    const bool wf = c[MU] == a.g.L[MU] - 1, wb = c[MU] == 0;
+    const int nbf = wf ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
+    const int nbb = wb ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
+    hop_pair_combined<MU, S_FWD>(a.in, a.u, s, nbf, nbb, V, wf, wb, a.g.bc[MU] < 0, mk, acc);
+    return;
+  }
   // forward hop n -> n + mu with U_mu(n)
   {
     const bool wrap = c[MU] == a.g.L[MU] - 1;
@@ -150,11 +192,14 @@ __device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int 
 
 // Occupancy: the kernel is latency-bound at large volumes (memory-level parallelism comes from
 // resident warps), so registers are capped for 3 blocks of 256 threads per SM in FP32/FP16
-// (24 warps) and 2 in FP64 (whose FP64 pipe saturates with few warps).
+// (24 warps). The FP64 kernels take one block per SM and up to 255 registers: their FP64 pipe
+// saturates with 8 warps, and the combined hops of a direction keep 24 more values live, which
+// spill under the 128-register cap of two blocks (measured at 14^4: 62.5 us with one block of
+// 255 registers, 63.0 us with two blocks and spills).
 constexpr int kDslashMaxThreads = 256;
 template <int SP>
 struct DslashMinBlocks {
-  static constexpr int value = SP == P64 ? 2 : (SP == PDF ? 1 : 3);
+  static constexpr int value = SP == P64 ? 1 : (SP == PDF ? 1 : 3);
 };
 
 
@@ -372,6 +417,16 @@ template <int MU, int SF, int SP, bool C12, typename R>
 __device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int s, const int (&c)[4],
                                             Cx<R> (&acc)[12]) {
   const int V = a.e.g.V;
+  if constexpr (SP == P64) {
+    const bool wf = c[MU] == a.e.g.L[MU] - 1, wb = c[MU] == 0;
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    n[MU] = wf ? 0 : c[MU] + 1;
+    const int nbf = eo_index(a.e.g, n);
+    n[MU] = wb ? a.e.g.L[MU] - 1 : c[MU] - 1;
+    const int nbb = eo_index(a.e.g, n);
+    hop_pair_combined<MU, SF>(a.in, a.u, s, nbf, nbb, V, wf, wb, a.e.g.bc[MU] < 0, k0, acc);
+    return;
+  }
   {
     int n[4] = {c[0], c[1], c[2], c[3]};
     const bool wrap = n[MU] == a.e.g.L[MU] - 1;
