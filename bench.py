@@ -614,7 +614,9 @@ def _serving(wd, n_req=60, rate=200.0, seed=7):
 
 
 def _cpu_baseline(gpu_iters):
+    import synthetic
     from oracle import cg as ocg
+    from oracle import wilson as owil
     U, eta = make_inputs(DIMS)
     k = 3
     t0 = time.perf_counter()
@@ -622,10 +624,28 @@ def _cpu_baseline(gpu_iters):
     dt = time.perf_counter() - t0
     per_apply = dt / (2 * k + 3)
     ms = 1e3 * per_apply * (2 * gpu_iters + 3)
-    return {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "host_cores": os.cpu_count(),
-            "sample": f"{k} CGLS iterations of the 14^4 FP64 solve (numpy, one thread: the oracle's "
-                      f"einsum contractions do not call a threaded BLAS), scaled to the {gpu_iters} "
-                      f"iterations + setup of the full solve"}
+    out = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "host_cores": os.cpu_count(),
+           "sample": f"{k} CGLS iterations of the 14^4 FP64 solve (numpy, one thread: the oracle's "
+                     f"einsum contractions do not call a threaded BLAS), scaled to the {gpu_iters} "
+                     f"iterations + setup of the full solve"}
+    # the whole 4^4 solve, and one oracle dslash per sweep volume (unit links: the oracle's
+    # arithmetic does not depend on the link values)
+    U4, eta4 = make_inputs((4, 4, 4, 4))
+    t0 = time.perf_counter()
+    _, it4, res4 = ocg.cgls(U4, eta4, KAPPA, TOL, 2000)[:3]
+    out["solve_4x4_ms"] = 1e3 * (time.perf_counter() - t0)
+    out["solve_4x4_iterations"] = int(it4)
+    out["solve_4x4_true_rel_residual"] = float(res4)
+    sweep = {}
+    for L in (8, 12, 14, 16, 24, 32):
+        d = (L, L, L, L)
+        Ul, psi = synthetic.unit_gauge(d), synthetic.gaussian_source(d, SOURCE_SEED)
+        t0 = time.perf_counter()
+        owil.apply_D(Ul, psi, KAPPA)
+        sweep[str(L)] = 1e3 * (time.perf_counter() - t0)
+        del Ul, psi
+    out["dslash_ms_by_L"] = sweep
+    return out
 
 
 def main():
