@@ -46,6 +46,8 @@ def main(argv=None):
     ap.add_argument("--msites", type=int, default=0, help="multi-RHS sites per block (0 = tuned)")
     ap.add_argument("--msolve", type=int, default=0, help="one cg_solve_multi on this many Gaussian sources")
     ap.add_argument("--device-fields", action="store_true", help="generate links and sources on the device")
+    ap.add_argument("--graph", type=int, default=-1,
+                    help="WD_OPT_USE_GRAPH for the solves (0 = plain launches, which ncu lists one by one)")
     args = ap.parse_args(argv)
 
     import torch
@@ -67,6 +69,8 @@ def main(argv=None):
         return torch.from_numpy(synthetic.gaussian_source(dims, seed)).cuda()
     if args.block:
         op.set_option(wd.WD_OPT_BLOCK_DSLASH, args.block)
+    if args.graph >= 0:
+        op.set_option(wd.WD_OPT_USE_GRAPH, args.graph)
     if args.launches:
         ms = op.time_dslash(args.dagger, args.launches)
         print(f"dslash dims={dims} prec={args.prec} c12={args.c12}: {ms * 1e3:.2f} us per launch")
