@@ -25,6 +25,20 @@ def test_eo_context_applies_the_full_operator(dims, dagger):
     op.close()
 
 
+@pytest.mark.parametrize("bc", [(-1, 1, -1, 1), (-1, -1, -1, -1), (1, -1, 1, 1)])
+def test_eo_fp64_boundaries(bc):
+    """Antiperiodic directions of extent 2 and 6: one of the two hops of a direction wraps."""
+    wd = require_gpu()
+    dims = (4, 2, 2, 6)
+    U, psi = fields(dims)
+    op = wd.WilsonDirac(dims, 0.137, bc, wd.WD_PREC_F64 | wd.WD_EVEN_ODD)
+    op.load_gauge(to_dev(U))
+    for dagger in (False, True):
+        out = to_np(op.apply(to_dev(psi), dagger=dagger))
+        assert rel(out, wilson.apply_D(U, psi, 0.137, bc, dagger)) < 1e-13
+    op.close()
+
+
 def test_eo_fp32_apply_and_generated_links():
     wd = require_gpu()
     dims = (4, 6, 4, 4)
