@@ -929,7 +929,6 @@ wd_status autotune_multi(wd_ctx* c, FieldPtr in, FieldPtr out, bool f64) {
     for (int K = 1; K <= N; ++K) {
       if (N % K) continue;
       if (fixK && K != fixK) continue;
-      if (f64 && K != N && !fixK) continue;  // FP64 is ALU-bound: only the full group is tried
       const int spbs[] = {4, 8, 16, 32, 64, 128};
       for (int spb : spbs) {
         if (fixS && spb != fixS) continue;
