@@ -299,6 +299,7 @@ def run_native(args, rank, world):
         out["mixed_f32"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_MIXED_F32, TOL, c12=True)
         out["mixed_f16"] = _variant(wd, U, eta, dev, stream, wd.WD_PREC_MIXED_F16, TOL, c12=True)
         out["dslash_sweep"] = _sweep(wd, dev, stream, args.sweep)
+        out["paper_sizes_f64_cg"] = _paper_sizes(wd, stream)
         out["mixed_32x64"] = _mixed_32x64(wd, dev, stream)
         out["multi_rhs_24x48"] = _multi_24x48(wd, dev, stream)
         out["even_odd"] = _even_odd(wd, dev, stream)
@@ -394,6 +395,24 @@ def _sweep(wd, dev, stream, sizes):
             row[name] = {"ms": ms, "gbs": bps * V / (ms * 1e-3) / 1e9,
                          "gflops": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e9}
         out.append(row)
+    return out
+
+
+def _paper_sizes(wd, stream):
+    """Plain FP64 CG to 1e-10 over the paper's lattice sizes (4^4 to 14^4), same generator."""
+    out = []
+    for L in (4, 8, 12, 14):
+        dims = (L, L, L, L)
+        op = wd.WilsonDirac(dims, KAPPA, BC, wd.WD_PREC_F64, stream=stream)
+        op.generate_gauge(EPS, GAUGE_SEED)
+        eta = op.generate_source(SOURCE_SEED)
+        _, rec = _timed_solve(op, wd, eta, TOL, repeats=3)
+        st = op.stats()
+        rec["L"] = L
+        rec["gflops_1320"] = 2 * FLOPS_PER_SITE * L ** 4 * rec["iterations"] / (rec["ms"] * 1e-3) / 1e9
+        rec["cg_loop"] = {0: "host loop", 1: "graph", 2: "persistent kernel"}[st["loop_mode"]]
+        op.close()
+        out.append(rec)
     return out
 
 
@@ -658,7 +677,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the solver's kernels one by one instead of as a CUDA graph (for "
                          "ncu launch lists, which do not list kernels inside conditional graph nodes)")
-    ap.add_argument("--sweep", default="8,12,14,16,24,32")
+    ap.add_argument("--sweep", default="4,8,12,14,16,24,32")
     args = ap.parse_args()
     args.sweep = [int(v) for v in args.sweep.split(",") if v]
     world = int(os.environ.get("WORLD_SIZE", "1"))
