@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import os
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -107,11 +108,16 @@ def main(argv=None):
     if args.msolve:
         eta = torch.stack([source(100 + i) for i in range(args.msolve)])
         x = torch.zeros_like(eta)
+        wd.cg_solve_multi(op.ctx, eta, x, args.tol, 20000)  # tunes the launch shapes
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         st, iters, res = wd.cg_solve_multi(op.ctx, eta, x, args.tol, 20000)
+        t1 = time.perf_counter()
         ms = wd.wd_get_multi_stats(op.ctx)
         print(f"cg_solve_multi ({args.msolve} RHS): status {st} iterations {max(iters)} "
               f"max true residual {max(res):.3e} reliable updates {ms['reliable_updates']} "
-              f"group {ms['group']} sites/block {ms['sites_per_block']}")
+              f"group {ms['group']} sites/block {ms['sites_per_block']} ms {1e3 * (t1 - t0):.1f}")
     if args.solve:
         eta = source(2)
         x, iters, res, status = op.solve(eta, tol=args.tol, maxit=4000)
