@@ -205,9 +205,12 @@ struct DslashMinBlocks {
 
 // ---------------------------------------------------------------- FP64: two threads per site
 //
-// The FP64 dslash is bound by the FP64 pipe. At the paper's volumes (14^4 = 38,416 sites) one
-// thread per site leaves 8 warps per SM, too few to keep that pipe fed through the load and
-// dependency latencies. Here lanes 2i and 2i+1 share a site: lane h projects only the half-spinor
+// The FP64 dslash is bound by the FP64 pipe. At small volumes (8^4, 12^4) one thread per site
+// leaves many SMs idle or with one warp per scheduler, and a site's ~850 FP64 instructions set
+// the time; splitting a site over two lanes halves that chain (measured at 8^4: 22.5 us against
+// 36 us). From 14^4 up the one-thread-per-site kernel, with its combined directions, is faster
+// (63 against 69 us), and the block-size tuner chooses between the two kernels per volume.
+// Here lanes 2i and 2i+1 share a site: lane h projects only the half-spinor
 // row h, multiplies it by the link and reconstructs it, so both lanes run the same instructions
 // (no divergence) and together execute the same FP64 operations as one thread of dslash_kernel.
 // Row h of (1 -/+ gamma_mu) pairs upper spin h with lower spin 2 + pi(h), pi(h) = 1 - h for x, y
