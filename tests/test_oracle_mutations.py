@@ -1,7 +1,8 @@
 """Planted mistakes in the oracle (on the CPU) must each fail at least one pin.
 
 This shows the pins are not vacuous: a dropped boundary phase, swapped projectors, transposed
-links, a flipped kappa sign or an undaggered backward link all change some checked fact.
+links, a flipped kappa sign or an undaggered backward link all change some checked fact, and so
+do mistakes in the two CG solvers (norms without their squares, D in place of D^dagger).
 """
 import functools
 
@@ -9,6 +10,7 @@ import numpy as np
 import pytest
 
 import synthetic
+from oracle import cg as ocg
 from oracle import freefield, wilson
 from oracle.gamma import GAMMA5
 
@@ -62,8 +64,31 @@ def check_plane_wave():
     assert np.abs(out - ref).max() < 1e-12
 
 
+def _dense_solution(dims, kappa):
+    U = synthetic.gauge_field(dims, 0.4, 1)
+    eta = synthetic.gaussian_source(dims, 2)
+    x = np.linalg.solve(wilson.dense_D(U, kappa, BC), eta.reshape(-1))
+    return U, eta, x
+
+
+def check_cgls_against_dense_solve():
+    dims = (2, 2, 2, 2)
+    U, eta, xd = _dense_solution(dims, 0.12)
+    x, k, res, hist = ocg.cgls(U, eta, 0.12, 1e-12, 150, boundary=BC)
+    assert wilson.rel_diff(x.reshape(-1), xd) < 1e-9
+    assert k < 150 and np.all(np.diff(hist) <= 1e-12 * hist[:-1])  # CGLS: monotone residual
+
+
+def check_cg_paper_against_dense_solve():
+    dims = (2, 2, 2, 2)
+    U, eta, xd = _dense_solution(dims, 0.12)
+    x, k, res, _ = ocg.cg_paper(U, eta, 0.12, 1e-12, 150, boundary=BC)
+    assert wilson.rel_diff(x.reshape(-1), xd) < 1e-9 and k < 150
+
+
 CHECKS = [check_fft_solve, check_gauge_covariance, check_gamma5_hermiticity_dense,
-          check_stencil_vs_coo, check_plane_wave]
+          check_stencil_vs_coo, check_plane_wave, check_cgls_against_dense_solve,
+          check_cg_paper_against_dense_solve]
 
 
 def _wrap_both(monkeypatch, transform_args):
@@ -128,6 +153,18 @@ def _mut_undaggered_backward_link(mp):
     assert orig is not apply
 
 
+def _mut_unsquared_cg_norms(mp):
+    # the printed algorithm's literal reading: norms where squared norms belong
+    orig = ocg.norm2
+    mp.setattr(ocg, "norm2", lambda v: float(np.sqrt(orig(v))))
+
+
+def _mut_cg_without_dagger(mp):
+    # both solvers apply D where D^dagger belongs
+    orig = ocg.apply_D
+    mp.setattr(ocg, "apply_D", lambda U, v, kappa, boundary=BC, dagger=False: orig(U, v, kappa, boundary, False))
+
+
 MUTATIONS = {
     "drop_boundary_phase": _mut_drop_phase,
     "transpose_links": _mut_transpose_links,
@@ -135,6 +172,8 @@ MUTATIONS = {
     "swap_projectors": _mut_swap_projectors,
     "flip_gamma_t": _mut_gamma_t_sign,
     "undaggered_backward_link": _mut_undaggered_backward_link,
+    "unsquared_cg_norms": _mut_unsquared_cg_norms,
+    "cg_without_dagger": _mut_cg_without_dagger,
 }
 
 
