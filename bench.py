@@ -52,7 +52,8 @@ def _peaks():
         return {}
 
 
-# FP64 FMA throughput measured on this machine's GB300 (152 SMs x 2 DFMA/clk x 2 flop x ~1.98 GHz)
+# FP64 FMA throughput measured on this machine's GB300 by a DFMA probe (nominal 152 SMs x 2 DFMA/clk x 2 flop
+# x 2.07 GHz = 1.259 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.202
 
 
