@@ -2,7 +2,9 @@
 
 This shows the pins are not vacuous: a dropped boundary phase, swapped projectors, transposed
 links, a flipped kappa sign or an undaggered backward link all change some checked fact, and so
-do mistakes in the two CG solvers (norms without their squares, D in place of D^dagger).
+do mistakes in the two CG solvers (norms without their squares, D in place of D^dagger) and in the
+two checking helpers every GPU test reads (a residual without its square root or with D^dagger,
+a relative difference normalised by the wrong argument or left squared).
 """
 import functools
 
@@ -86,9 +88,30 @@ def check_cg_paper_against_dense_solve():
     assert wilson.rel_diff(x.reshape(-1), xd) < 1e-9 and k < 150
 
 
+def check_true_residual_against_dense():
+    dims = (2, 2, 2, 2)
+    U, eta, xd = _dense_solution(dims, 0.12)
+    d = wilson.dense_D(U, 0.12, BC)
+    rng = np.random.default_rng(3)
+    x = xd + 1e-7 * (rng.standard_normal(xd.shape) + 1j * rng.standard_normal(xd.shape))
+    ref = np.linalg.norm(eta.reshape(-1) - d @ x) / np.linalg.norm(eta.reshape(-1))
+    got = ocg.true_residual(U, eta, x.reshape(eta.shape), 0.12, BC)
+    assert abs(got - ref) <= 1e-14 + 1e-10 * ref
+
+
+def check_rel_diff_against_numpy():
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal((6, 4, 3)) + 1j * rng.standard_normal((6, 4, 3))
+    a = b + 1e-6 * (rng.standard_normal(b.shape) + 1j * rng.standard_normal(b.shape))
+    for u, v in ((a, b), (3 * b, b), (b, 3 * b)):
+        ref = np.linalg.norm((u - v).reshape(-1)) / np.linalg.norm(v.reshape(-1))
+        assert abs(wilson.rel_diff(u, v) - ref) <= 1e-14 * ref
+
+
 CHECKS = [check_fft_solve, check_gauge_covariance, check_gamma5_hermiticity_dense,
           check_stencil_vs_coo, check_plane_wave, check_cgls_against_dense_solve,
-          check_cg_paper_against_dense_solve]
+          check_cg_paper_against_dense_solve, check_true_residual_against_dense,
+          check_rel_diff_against_numpy]
 
 
 def _wrap_both(monkeypatch, transform_args):
@@ -165,6 +188,28 @@ def _mut_cg_without_dagger(mp):
     mp.setattr(ocg, "apply_D", lambda U, v, kappa, boundary=BC, dagger=False: orig(U, v, kappa, boundary, False))
 
 
+def _mut_true_residual_squared(mp):
+    # the squared ratio ||eta - D x||^2 / ||eta||^2 (square root dropped)
+    mp.setattr(ocg, "true_residual", lambda U, eta, x, kappa, boundary=BC: float(
+        wilson.norm2(eta - wilson.apply_D(U, x, kappa, boundary)) / wilson.norm2(eta)))
+
+
+def _mut_true_residual_dagger(mp):
+    mp.setattr(ocg, "true_residual", lambda U, eta, x, kappa, boundary=BC: float(np.sqrt(
+        wilson.norm2(eta - wilson.apply_D(U, x, kappa, boundary, dagger=True)) / wilson.norm2(eta))))
+
+
+def _mut_rel_diff_wrong_norm(mp):
+    # normalised by the first argument instead of the second
+    mp.setattr(wilson, "rel_diff", lambda a, b: float(
+        np.sqrt(wilson.norm2(np.asarray(a) - np.asarray(b)) / wilson.norm2(a))))
+
+
+def _mut_rel_diff_squared(mp):
+    mp.setattr(wilson, "rel_diff", lambda a, b: float(
+        wilson.norm2(np.asarray(a) - np.asarray(b)) / wilson.norm2(b)))
+
+
 MUTATIONS = {
     "drop_boundary_phase": _mut_drop_phase,
     "transpose_links": _mut_transpose_links,
@@ -174,6 +219,10 @@ MUTATIONS = {
     "undaggered_backward_link": _mut_undaggered_backward_link,
     "unsquared_cg_norms": _mut_unsquared_cg_norms,
     "cg_without_dagger": _mut_cg_without_dagger,
+    "true_residual_squared": _mut_true_residual_squared,
+    "true_residual_dagger": _mut_true_residual_dagger,
+    "rel_diff_wrong_norm": _mut_rel_diff_wrong_norm,
+    "rel_diff_squared": _mut_rel_diff_squared,
 }
 
 
