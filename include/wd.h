@@ -349,10 +349,11 @@ wd_status wd_time_dslash(wd_ctx* ctx, int dagger, int launches, double* avg_ms);
  * process exits. The first call on each device looks up that array's device address (a one-time
  * set-up per device); make that first call before any stream capture. Every call shares the one
  * array, so calls whose kernels overlap on the GPU (different streams, concurrent threads) race
- * and give wrong norms; serialise them. The call allocates nothing: no cudaMalloc/cudaFree and
- * no allocating library routine.
- * Errors: WD_EINVAL (null pointer, bad dims, V > 2^20, bad kappa or boundary, in == out),
- * WD_ECUDA (device or launch failure).
+ * and give wrong norms; serialise them. The cached address belongs to the device's primary context:
+ * resetting the device (cudaDeviceReset) after the first call is not supported. The call allocates
+ * nothing: no cudaMalloc/cudaFree and no allocating library routine.
+ * Errors: WD_EINVAL (null pointer, bad dims, V > 2^20, bad kappa or boundary, in and out
+ * overlapping), WD_ECUDA (device or launch failure).
  */
 wd_status wd_dslash_noalloc(const int dims[4], double kappa, const int boundary[4], const double* U,
                             const double* in, double* out, int dagger, double* norm2_out,

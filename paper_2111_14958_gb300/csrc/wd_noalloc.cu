@@ -12,6 +12,7 @@
 // The array below lives in the library's module on every GPU that loads the library and stays
 // there until the process exits. Its size caps the volume this entry point accepts.
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -119,6 +120,9 @@ std::mutex g_addr_mu;
 void* g_addr[256];  // device address of g_noalloc_scratch, per device ordinal
 
 // Host code cannot use &g_noalloc_scratch as a device address: ask the runtime, once per device.
+// The address stays valid for the life of the device's primary context; a cudaDeviceReset after
+// the first call would unload the module and leave the cached address stale, so such a reset is
+// not supported in a process that uses this entry point.
 wd_status scratch_address(unsigned char** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -158,6 +162,7 @@ extern "C" wd_status wd_dslash_noalloc(const int dims[4], double kappa, const in
     wdk::set_last_error("in and out must differ");
     return WD_EINVAL;
   }
+  // the running product is checked at every step, so four large extents cannot overflow it
   long long V = 1;
   for (int i = 0; i < 4; ++i) {
     if (dims[i] < 2) {
@@ -165,10 +170,20 @@ extern "C" wd_status wd_dslash_noalloc(const int dims[4], double kappa, const in
       return WD_EINVAL;
     }
     V *= dims[i];
+    if (V > kMaxSites) {
+      wdk::set_last_error("volume exceeds the fixed scratch of wd_dslash_noalloc (at most 2^20 sites)");
+      return WD_EINVAL;
+    }
   }
-  if (V > kMaxSites) {
-    wdk::set_last_error("volume exceeds the fixed scratch of wd_dslash_noalloc (at most 2^20 sites)");
-    return WD_EINVAL;
+  // in and out are V * 12 complex128 each; any overlap would let a site read a neighbour the
+  // kernel has already overwritten
+  {
+    const unsigned long long n = (unsigned long long)V * 12 * sizeof(double2);
+    const unsigned long long a = (unsigned long long)(uintptr_t)in, b = (unsigned long long)(uintptr_t)out;
+    if (a < b + n && b < a + n) {
+      wdk::set_last_error("in and out overlap");
+      return WD_EINVAL;
+    }
   }
   if (!std::isfinite(kappa) || std::fabs(kappa) >= 1.0) {
     wdk::set_last_error("kappa must be finite with |kappa| < 1");

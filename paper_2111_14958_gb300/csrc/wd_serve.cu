@@ -69,6 +69,7 @@ struct Job {
 // A context kept on the device between requests, with the slot's source/solution buffers.
 struct Resident {
   int dims[4] = {0, 0, 0, 0};
+  int bc[4] = {1, 1, 1, -1};  // boundary phases the context was created with
   int precision = 0;
   wd_ctx* ctx = nullptr;
   double* src = nullptr;
@@ -86,9 +87,22 @@ struct Slot {
   std::thread th;
 };
 
-bool same_key(const Resident& r, const wd_request& q) {
-  return r.ctx && r.precision == q.precision && memcmp(r.dims, q.dims, sizeof(r.dims)) == 0;
+// The boundary phases a request asks for (wd_request.boundary_set = 0 means (1, 1, 1, -1)).
+void request_bc(const wd_request& q, int (&bc)[4]) {
+  const int def[4] = {1, 1, 1, -1};
+  for (int i = 0; i < 4; ++i) bc[i] = q.boundary_set ? q.boundary[i] : def[i];
 }
+
+// A resident context (or the placeholder reserved for one) serves a request only when the operator
+// is the same: volume, precision and boundary phases (kappa is set per request).
+bool same_operator(const Resident& r, const wd_request& q) {
+  int bc[4];
+  request_bc(q, bc);
+  return r.precision == q.precision && memcmp(r.dims, q.dims, sizeof(r.dims)) == 0 &&
+         memcmp(r.bc, bc, sizeof(bc)) == 0;
+}
+
+bool same_key(const Resident& r, const wd_request& q) { return r.ctx && same_operator(r, q); }
 
 }  // namespace
 
@@ -129,7 +143,7 @@ wd_status prepare(Slot* s, const wd_request& r, Resident** out) {
   }
   Resident* e = nullptr;
   for (auto& c : s->cache)
-    if (!c.ctx && c.precision == r.precision && memcmp(c.dims, r.dims, sizeof(c.dims)) == 0) e = &c;
+    if (!c.ctx && same_operator(c, r)) e = &c;
   if (!e) {
     wdk::set_last_error("internal: no reserved resident for the job");
     return WD_ECUDA;
@@ -278,6 +292,7 @@ void schedule(wd_server* srv) {
       }
       Resident fresh;
       memcpy(fresh.dims, j->req.dims, sizeof(fresh.dims));
+      request_bc(j->req, fresh.bc);
       fresh.precision = j->req.precision;
       fresh.bytes = j->bytes;
       fresh.last_used = ++srv->tick;
@@ -340,6 +355,12 @@ wd_status wd_server_submit(wd_server* srv, const wd_request* r, long long* id) {
       wdk::set_last_error("every lattice extent must be >= 2");
       return WD_EINVAL;
     }
+  if (r->boundary_set)
+    for (int i = 0; i < 4; ++i)
+      if (r->boundary[i] != 1 && r->boundary[i] != -1) {
+        wdk::set_last_error("boundary entries must be +1 or -1");
+        return WD_EINVAL;
+      }
   if (!(r->tol > 0) || r->maxit < 0) {
     wdk::set_last_error("bad tol or maxit");
     return WD_EINVAL;

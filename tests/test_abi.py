@@ -66,3 +66,27 @@ def test_argument_validation_without_device(lib):
     bc = (ctypes.c_int * 4)(1, 1, 1, 0)
     assert lib.wd_create(good, ctypes.c_double(0.12), bc, 64, None, ctypes.byref(out)) == wd.WD_EINVAL
     assert lib.wd_create(good, ctypes.c_double(0.12), None, 64, None, None) == wd.WD_EINVAL
+
+
+def test_noalloc_rejects_bad_sizes_and_overlap_before_any_device_call(lib):
+    """wd_dslash_noalloc validates on the host first: extents whose product would overflow, a volume
+    beyond its fixed scratch, and overlapping in/out ranges are rejected before any CUDA call (the
+    addresses below are never dereferenced)."""
+    import ctypes
+    from paper_2111_14958_gb300 import wd
+
+    def call(dims, U, a, b):
+        d = (ctypes.c_int * 4)(*dims)
+        return lib.wd_dslash_noalloc(d, ctypes.c_double(0.12), None, ctypes.c_void_p(U), ctypes.c_void_p(a),
+                                     ctypes.c_void_p(b), 0, None, None)
+
+    big = 1 << 30
+    assert call((big, big, big, big), 0x100000, 0x200000, 0x300000) == wd.WD_EINVAL
+    assert "2^20" in wd.wd_last_error()
+    assert call((32, 32, 32, 33), 0x100000, 0x200000, 0x300000) == wd.WD_EINVAL
+    n = 4 ** 4 * 12 * 16  # bytes of one 4^4 complex128 spinor field
+    base = 1 << 40
+    assert call((4, 4, 4, 4), 0x100000, base, base + 16) == wd.WD_EINVAL
+    assert "overlap" in wd.wd_last_error()
+    assert call((4, 4, 4, 4), 0x100000, base + 16, base) == wd.WD_EINVAL
+    assert call((4, 4, 4, 4), 0x100000, base, base) == wd.WD_EINVAL

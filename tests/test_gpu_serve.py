@@ -127,3 +127,35 @@ def test_same_volume_request_runs_on_the_resident_context():
     assert a["status"] == b["status"] == wd.WD_OK
     assert st["warm_hits"] == 1 and b["slot"] == a["slot"]
     assert b["true_rel_residual"] <= 1e-10
+
+
+def test_requests_differing_only_in_boundary_use_their_own_operator():
+    """A resident context matches a request only with the same boundary phases (periodic time and
+    antiperiodic time are different operators of Eq. (1)): each result meets its own operator."""
+    wd = require_gpu()
+    dims = (4, 4, 4, 6)
+    q = dict(dims=dims, kappa=0.12, eps=0.4, gauge_seed=5, source_seed=6, tol=1e-10, precision=wd.WD_PREC_MIXED_F32)
+    U = synthetic.gauge_field_philox(dims, 0.4, 5)
+    eta = synthetic.gaussian_source_philox(dims, 6)
+    srv = wd.Server(budget_bytes=1e9, slots=1)   # one slot: the second request finds the first's context
+    out = {}
+    for bc in ((1, 1, 1, -1), (1, 1, 1, 1), (1, 1, 1, -1)):
+        lx, ly, lz, lt = dims
+        x = torch.empty((lt, lz, ly, lx, 4, 3), dtype=torch.complex128)
+        r = srv.wait(srv.submit(boundary=bc, x_host=x, **q))
+        assert r["status"] == wd.WD_OK, (bc, r)
+        xs = x.numpy()
+        assert ocg.true_residual(U, eta, xs, 0.12, bc) <= 1e-10 * 1.01, bc
+        other = (1, 1, 1, 1) if bc[3] < 0 else (1, 1, 1, -1)
+        assert ocg.true_residual(U, eta, xs, 0.12, other) > 1e-6, bc
+        op = wd.WilsonDirac(dims, 0.12, bc, wd.WD_PREC_MIXED_F32)
+        op.generate_gauge(0.4, 5, compress12=True)
+        xa, ia, ra, sa = op.solve(op.generate_source(6), tol=1e-10, maxit=20000)
+        op.close()
+        assert sa == wd.WD_OK and ia == r["iterations"] and np.array_equal(to_np(xa), xs), bc
+        out.setdefault(bc, []).append(xs)
+    st = srv.stats()
+    srv.close()
+    # the third request (antiperiodic again) found the first one's context still resident
+    assert st["warm_hits"] >= 1
+    assert np.array_equal(out[(1, 1, 1, -1)][0], out[(1, 1, 1, -1)][1])

@@ -3,8 +3,8 @@
 Such callers (code under an allocator that must own every device allocation, plug-ins handed
 fixed buffers) cannot create a context, so this entry point takes all inputs and outputs from
 the caller and keeps its reduction scratch in a fixed array inside the library. The test calls it
-through the C ABI twice in a row and checks both results against the context-based wd_apply.
-This file is collected last on purpose.
+through the C ABI twice in a row and checks both results against the context-based wd_apply and
+against the CPU oracle's operator of Eq. (1). This file is collected last on purpose.
 """
 import ctypes
 
@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import wilson
 from tests.gpu_util import fields, rel, require_gpu, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -40,13 +41,18 @@ def test_noalloc_matches_wd_apply_on_two_calls(dims):
     for dagger in (False, True):
         ref = op.apply(psid, dagger=dagger)
         ref_norm = float((ref.abs() ** 2).sum())
+        orc = wilson.apply_D(U, psi, 0.12, BC, dagger=dagger)
+        orc_norm = wilson.norm2(orc)
         for _ in range(2):  # the shared scratch keeps the previous call's contents
             out = torch.full_like(psid, float("nan"))
             norm = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
             assert _call(lib, dims, 0.12, Ud, psid, out, dagger, norm, stream) == wd.WD_OK
             torch.cuda.synchronize()
-            assert rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-13
+            got = out.cpu().numpy()
+            assert rel(got, ref.cpu().numpy()) < 1e-13
             assert abs(float(norm.item()) - ref_norm) <= 1e-12 * ref_norm
+            assert wilson.rel_diff(got, orc) < 1e-13
+            assert abs(float(norm.item()) - orc_norm) <= 1e-12 * orc_norm
     op.close()
 
 
@@ -73,5 +79,6 @@ def test_noalloc_without_norm_and_through_binding():
     wd.wd_dslash_noalloc(dims, 0.13, Ud, psid, out)
     torch.cuda.synchronize()
     assert rel(out.cpu().numpy(), ref) < 1e-13
+    assert wilson.rel_diff(out.cpu().numpy(), wilson.apply_D(U, psi, 0.13, BC)) < 1e-13
     op.close()
     assert np.isfinite(ref).all()
