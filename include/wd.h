@@ -108,9 +108,15 @@ enum {
                                 up and cg_solve returns WD_ECUDA ("a grid barrier wait gave
                                 up"), leaving the context usable; 0 or 2^26 (default, about
                                 4 s). Small values exercise that failure path.                  */
-  WD_OPT_RESIDUAL_HISTORY = 13 /* cg_solve records the recursive residual of its first N
+  WD_OPT_RESIDUAL_HISTORY = 13,/* cg_solve records the recursive residual of its first N
                                 iterations (N = value, 0 = off, the default) for
                                 wd_get_residual_history                                          */
+  WD_OPT_APPLY_INNER = 14    /* mixed precision: 1 makes wd_apply and wd_apply_multi run the inner
+                                solver's operator (complex128 in and out): the input is rounded
+                                into the working precision (FP32, or FP16 with a per-site FP32
+                                norm), D is applied with the FP32 links (12-real if loaded so)
+                                and the working-precision result is widened to complex128; 0
+                                (default) the FP64 operator                                      */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */
@@ -180,7 +186,8 @@ wd_status wd_load_gauge(wd_ctx* ctx, const double* U, int on_device, int compres
 /*
  * out = D in (dagger == 0) or D^dagger in (dagger != 0), Eq. (1).
  *   in, out : device spinor fields in the canonical layout; complex128 for WD_PREC_F64 and the
- *             mixed modes (FP64 operator), complex64 for WD_PREC_F32. in != out.
+ *             mixed modes (FP64 operator, or the inner one under WD_OPT_APPLY_INNER), complex64
+ *             for WD_PREC_F32. in != out.
  * Errors: WD_EINVAL, WD_ENOGAUGE, WD_ECUDA.
  */
 wd_status wd_apply(wd_ctx* ctx, const void* in, void* out, int dagger);
@@ -208,7 +215,8 @@ wd_status cg_solve(wd_ctx* ctx, const void* src, void* x, double tol, int maxit,
  * nrhs (timed with CUDA events on the context stream) unless fixed with WD_OPT_MULTI_*.
  *
  * wd_apply_multi: out_r = D in_r (or D^dagger), in the context's operator precision (FP64 for
- *   WD_PREC_F64 and the mixed modes, FP32 arithmetic on rounded inputs for WD_PREC_F32).
+ *   WD_PREC_F64 and the mixed modes, FP32 arithmetic on rounded inputs for WD_PREC_F32; the inner
+ *   FP32 / FP16 operator of a mixed context under WD_OPT_APPLY_INNER).
  * cg_solve_multi: solves D x_r = src_r for every r with the context's solver (plain FP64, plain
  *   FP32, or mixed precision with FP64 reliable updates applied to all right-hand sides at once
  *   whenever one of them has dropped by delta), each right-hand side stopping on its own

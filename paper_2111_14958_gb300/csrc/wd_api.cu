@@ -66,6 +66,7 @@ struct wd_ctx {
   // mixed precision: reliable updates in double-float (FP32-pipe) arithmetic
   int use_df;
   int apply_df;  // wd_apply on a mixed context uses the double-float operator (for checks)
+  int apply_inner;  // wd_apply / wd_apply_multi on a mixed context use the inner FP32 / FP16 operator
   FieldPtr xdf, rdf, etadf, tdf;
   void* gauge_df;
   FieldPtr x, r, p, q, s, eta;  // plain modes: all in wprec; mixed: r, p, q, s in wprec, x = x_lo (SP32)
@@ -1438,6 +1439,11 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float operator exists on mixed-precision contexts");
       c->apply_df = value != 0.0;
       return WD_OK;
+    case WD_OPT_APPLY_INNER:
+      if (!is_mixed(c->precision)) return fail(WD_EINVAL, "the inner operator exists on mixed-precision contexts");
+      if (value != 0.0 && value != 1.0) return fail(WD_EINVAL, "apply-inner option must be 0 or 1");
+      c->apply_inner = value != 0.0;
+      return WD_OK;
     case WD_OPT_DSLASH_VARIANT: {
       const int v = (int)value;
       if (value != (double)v || v < 0 || v > 2) return fail(WD_EINVAL, "dslash variant must be 0, 1 or 2");
@@ -1567,6 +1573,12 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
     WD_CUDA(launch_pack_c64((const float*)in, c->q, c->V, eo_geom(c), bb, c->stream));
     WD_CUDA(full_D(c, c->q, c->s, dagger ? 1 : 0, c->stream));
     WD_CUDA(launch_unpack_c64(c->s, (float*)out, c->V, eo_geom(c), bb, c->stream));
+  } else if (c->apply_inner) {
+    // the inner solver's operator: complex128 rounded into the working precision (FP32, or FP16
+    // with its per-site norm), the dslash on the FP32 links, the result widened back
+    WD_CUDA(launch_pack((const double*)in, c->p, c->V, eo_geom(c), no_red(), bb, c->stream));
+    WD_CUDA(full_D(c, c->p, c->q, dagger ? 1 : 0, c->stream));
+    WD_CUDA(launch_unpack(c->q, (double*)out, c->V, eo_geom(c), bb, c->stream));
   } else {
     FieldPtr a = c->wprec == SP64 ? c->q : c->x64;
     FieldPtr b = c->wprec == SP64 ? c->s : c->r64;
@@ -1727,9 +1739,10 @@ wd_status wd_apply_multi(wd_ctx* c, const double* in, double* out, int nrhs, int
   if ((st = ensure_multi(c, nrhs)) != WD_OK) return st;
   if ((st = ensure_multi_tuned(c)) != WD_OK) return st;
   const bool mixed = is_mixed(c->precision);
-  FieldPtr a = mixed ? c->mx64 : c->mq;
-  FieldPtr b = mixed ? c->mr64 : c->ms;
-  const int grid = mixed ? c->mgrid64 : c->mgrid;
+  const bool f64op = mixed && !c->apply_inner;  // mixed: FP64 operator unless the inner one is asked for
+  FieldPtr a = f64op ? c->mx64 : (mixed ? c->mp : c->mq);
+  FieldPtr b = f64op ? c->mr64 : (mixed ? c->mq : c->ms);
+  const int grid = f64op ? c->mgrid64 : c->mgrid;
   WD_CUDA(launch_mpack(in, a, c->V, nrhs, grid, nullptr, nullptr, nullptr, c->stream));
   WD_CUDA(mdslash(c, a, b, dagger ? 1 : 0, EPI_PLAIN, none_field(), nullptr, TKM_MISC, nullptr, c->stream));
   WD_CUDA(launch_munpack(b, out, c->V, nrhs, grid, c->stream));

@@ -57,6 +57,7 @@ WD_OPT_CG_FORM = 10
 WD_OPT_DSLASH_VARIANT = 11
 WD_OPT_LOOP_WAIT_LIMIT = 12
 WD_OPT_RESIDUAL_HISTORY = 13
+WD_OPT_APPLY_INNER = 14
 
 
 class WdMultiStats(ctypes.Structure):
