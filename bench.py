@@ -9,11 +9,14 @@ One step = load the gauge field into the device layout + one complete solve from
 residual recomputation, with inputs resident in HBM. The L2 (129 MB) is flushed before every step
 by writing a 512 MB buffer outside the timed interval.
 
-Extra measurements on the same line: the dominant kernel against its roofline, the same solve
-end to end from host buffers, plain FP32 CG and mixed precision, a dslash bandwidth sweep, and the
-CPU oracle timed on the host cores (a bounded sample, extrapolated; a baseline, not a target).
+Extra measurements on the same line: the dominant kernel against its roofline (the FP64 ceiling
+measured in the same run), the same solve end to end from host buffers, plain FP32 CG and mixed
+precision, a dslash bandwidth sweep, and the CPU oracle's whole solve of the same system on one host
+core (a baseline, not a target).
 
-``--impl reference`` times the FP64 CPU oracle (the plain definition of the method) instead.
+``--impl reference`` times the FP64 CPU oracle (the plain definition of the method) instead, one
+whole solve per timed step. ``--profile-case ...`` runs one small workload for an ncu capture (see
+profile_case below) instead of the benchmark.
 Multi-GPU: the solver does not shard here, so ``--gpus N`` runs N independent replicas (one per
 rank, weak scaling) and reports the slowest rank's time.
 """
@@ -52,9 +55,17 @@ def _peaks():
         return {}
 
 
-# FP64 FMA throughput measured on this machine's GB300 by a DFMA probe (nominal 152 SMs x 2 DFMA/clk x 2 flop
-# x 2.07 GHz = 1.259 TFLOP/s)
-FP64_PEAK_TFLOPS = 1.202
+# FP64 FMA rate from the unit count (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz), for context only: the
+# roofline's denominator is measured in the same run by the library's probe (wd_measure_fp64_peak)
+FP64_NOMINAL_TFLOPS = 1.259
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the line
+# reports, from one ncu capture each; the summary file holds the full command. None = not captured
+# for the kernel as it now stands.
+NCU_TRAFFIC = {
+    "cg_loop_f64_14x4": (57830144, "profiles/cg_loop_f64_14x4.md"),
+    "dslash_f64_14x4": (None, "profiles/dslash_f64_14x4.md"),
+}
 
 
 class ClockSampler:
@@ -119,54 +130,47 @@ def make_inputs(dims, eps=EPS, gseed=GAUGE_SEED, sseed=SOURCE_SEED):
 
 # ---------------------------------------------------------------------------- reference arm
 
+REFERENCE_MAX_TIMED_SOLVES = 3  # full oracle solves of the 14^4 workload timed per run (~30 s each)
+
+
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
+    """The FP64 CPU oracle, as it stands, solving the same workload to the same tolerance.
+
+    Each timed step is one whole oracle solve of the 14^4 system (CGLS to a 1e-10 true residual,
+    about 30 s on one host core), so the value is a measurement, not an extrapolation. To end within
+    a few minutes the run times at most REFERENCE_MAX_TIMED_SOLVES of them: the line's `steps` is
+    the number timed and `steps_requested` the number asked for. Warm-up steps run one CGLS
+    iteration each (numpy has no JIT or cache to warm; they only page in the code and the fields).
+    """
     if rank != 0:
         return 0
     from oracle import cg as ocg
-    from oracle import wilson
     U, eta = make_inputs(DIMS)
-    sample_iters = 3
-    times = []
-
-    def one_step():
-        t0 = time.perf_counter()
-        _, k, _, _ = ocg.cgls(U, eta, KAPPA, 0.0, sample_iters)
-        t1 = time.perf_counter()
-        return (t1 - t0), k
-
     for _ in range(args.warmup):
-        one_step()
-    # iterations the oracle needs to reach the tolerance (the GPU solve's count is the same
-    # within +-2; taken from the stored oracle record of this workload when present)
-    full_iters = _oracle_iterations()
-    for _ in range(args.steps):
-        dt, k = one_step()
-        # setup (2 operator applications) + k iterations (2 each) + true residual (1)
-        per_apply = dt / (2 * k + 3)
-        times.append(per_apply * (2 * full_iters + 3))
-    ms = 1e3 * statistics.mean(times)
+        ocg.cgls(U, eta, KAPPA, 0.0, 1)
+    n_timed = max(1, min(args.steps, REFERENCE_MAX_TIMED_SOLVES))
+    times, iters, res = [], None, None
+    c0 = time.process_time()
+    for _ in range(n_timed):
+        t0 = time.perf_counter()
+        _, iters, res, _ = ocg.cgls(U, eta, KAPPA, TOL, MAXIT)
+        times.append(1e3 * (time.perf_counter() - t0))
+    busy = (time.process_time() - c0) / (1e-3 * sum(times))
+    ms = statistics.mean(times)
+    sample = (f"{n_timed} whole oracle solves of the 14^4 workload (FP64 numpy CGLS, {iters} iterations, "
+              f"true residual {res:.2e}); {args.steps} steps requested; numpy's dot products run on "
+              f"OpenBLAS threads over the host's {os.cpu_count()} cores, {busy:.1f} cores busy on average")
     line = {
         "impl": "reference", "metric": "CG time-to-1e-10 residual", "value": ms, "unit": "ms",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(),
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample_iters} CGLS iterations of the 14^4 solve per step, "
-                                   f"scaled to {full_iters} iterations + setup"},
+        "n_gpus": world, "steps": n_timed, "steps_requested": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(), "iterations": iters, "true_rel_residual": res,
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": os.cpu_count(), "avg_busy_cores": busy,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
-
-
-def _oracle_iterations():
-    path = os.path.join(ROOT, "tests", "golden", "bench_workload.json")
-    try:
-        with open(path) as f:
-            return int(json.load(f)["iterations"])
-    except (OSError, KeyError, ValueError):
-        return 95
 
 
 def _config():
@@ -252,14 +256,19 @@ def run_native(args, rank, world):
     achieved_tflops = flops / (dslash_ms * 1e-3) / 1e12
     achieved_gbs = BYTES_SITE_F64_18 * V / (dslash_ms * 1e-3) / 1e9
     share = 2 * iters * dslash_ms / ms
-    traffic = _profile_traffic("dslash_f64_14x4")
-    dslash_roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                   "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+    # the FP64 compute ceiling, measured now (same process, same clocks)
+    fp64_peak = wd.wd_measure_fp64_peak(stream, 5)
+    peak_source = (f"FP64 FMA rate measured in this run by the library's DFMA probe (wd_measure_fp64_peak, "
+                   f"best of 5 launches, CUDA events): {fp64_peak:.3f} TFLOP/s; unit-count nominal "
+                   f"{FP64_NOMINAL_TFLOPS} TFLOP/s")
+    traffic, traffic_src = NCU_TRAFFIC["dslash_f64_14x4"]
+    dslash_roof = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                   "frac": achieved_tflops / fp64_peak, "traffic": traffic, "traffic_source": traffic_src,
                    "kernel": "dslash_kernel<FP64, 18r> (q = D p with fused |q|^2), the launch shape the "
                              "solver uses",
                    "algorithmic": f"{FLOPS_PER_SITE} flop/site x {V} sites per launch; "
                                   f"{BYTES_SITE_F64_18} B/site",
-                   "peak_source": "FP64 FMA throughput measured on GB300 (1.202 TFLOP/s)",
+                   "peak_source": peak_source, "frac_of_nominal": achieved_tflops / FP64_NOMINAL_TFLOPS,
                    "achieved_hbm_gbs": achieved_gbs, "launch_ms": dslash_ms,
                    "share_of_step": share}
     if stats["loop_mode"] == 2:
@@ -269,13 +278,14 @@ def run_native(args, rank, world):
         loop_ms = statistics.mean(loop_ms_seen)
         loop_flops = (2 * FLOPS_PER_SITE + BLAS_FLOPS_PER_SITE_ITER) * V * iters
         ach = loop_flops / (loop_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": _profile_traffic("cg_loop_f64_14x4"),
+        traffic, traffic_src = NCU_TRAFFIC["cg_loop_f64_14x4"]
+        roofline = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak, "traffic": traffic, "traffic_source": traffic_src,
                     "kernel": f"cg_loop_kernel<FP64> (the whole CG loop in one cooperative launch: {iters} "
                               f"iterations of q = D p, r update, s = D^dag r, x and p update)",
                     "algorithmic": f"(2 x {FLOPS_PER_SITE} dslash + {BLAS_FLOPS_PER_SITE_ITER} BLAS-1) flop/site x "
                                    f"{V} sites x {iters} iterations per launch",
-                    "peak_source": "FP64 FMA throughput measured on GB300 (1.202 TFLOP/s)",
+                    "peak_source": peak_source, "frac_of_nominal": ach / FP64_NOMINAL_TFLOPS,
                     "launch_ms": loop_ms, "share_of_step": loop_ms / ms,
                     "dslash_standalone": dslash_roof}
     else:
@@ -311,20 +321,6 @@ def run_native(args, rank, world):
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
-
-
-def _profile_traffic(name):
-    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel, read from
-    its ncu summary in profiles/ (the `traffic_bytes_per_launch:` line), or None."""
-    path = os.path.join(ROOT, "profiles", name + ".md")
-    try:
-        with open(path) as f:
-            for line in f:
-                if line.startswith("traffic_bytes_per_launch:"):
-                    return int(line.split(":", 1)[1])
-    except (OSError, ValueError):
-        return None
-    return None
 
 
 def _e2e(args, op, U, eta, dev, stream):
@@ -437,7 +433,9 @@ def _mixed_32x64(wd, dev, stream):
     import torch
     dims, kappa = (32, 32, 32, 64), 0.124
     out = {"workload": "32^3x64, kappa 0.124, eps 0.4, tol 1e-10, 1 RHS, FP32 12-real inner links",
-           "reliable_delta": 0.1}
+           "reliable_delta": 0.1,
+           "updates": "mixed_*: reliable-update residual and solution in double-float (FP32 pairs, ~48 bits); "
+                      "mixed_*_fp64_updates: the same in native FP64; the final true residual is FP64 in both"}
     ref = wd.WilsonDirac(dims, kappa, BC, wd.WD_PREC_F64, stream=stream)
     ref.generate_gauge(EPS, GAUGE_SEED)
     eta = ref.generate_source(SOURCE_SEED)
@@ -454,6 +452,14 @@ def _mixed_32x64(wd, dev, stream):
         _, rec = _timed_solve(op, wd, eta, TOL, repeats=2)
         rec["speedup_vs_f64"] = out["plain_f64"]["ms"] / rec["ms"]
         out[name + "_delta_0.01"] = rec
+        # reliable updates in native FP64 (residual recomputation and solution accumulation), as the
+        # mixed-precision workload states them; the default above uses double-float for both
+        op.set_option(wd.WD_OPT_RELIABLE_DELTA, 0.1)
+        op.set_option(wd.WD_OPT_DF_UPDATES, 0)
+        x, rec = _timed_solve(op, wd, eta, TOL, repeats=2)
+        rec["rel_diff_vs_f64_solution"] = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
+        rec["speedup_vs_f64"] = out["plain_f64"]["ms"] / rec["ms"]
+        out[name + "_fp64_updates"] = rec
         op.close()
     ref.close()
     return out
@@ -634,22 +640,24 @@ def _serving(wd, n_req=60, rate=200.0, seed=7):
 
 
 def _cpu_baseline(gpu_iters):
+    """The oracle on the host cores: the whole 14^4 solve (the headline workload, ~30 s), the whole
+    4^4 solve, and one oracle dslash per sweep volume (unit links: the oracle's arithmetic does not
+    depend on the link values)."""
     import synthetic
     from oracle import cg as ocg
     from oracle import wilson as owil
     U, eta = make_inputs(DIMS)
-    k = 3
+    c0 = time.process_time()
     t0 = time.perf_counter()
-    ocg.cgls(U, eta, KAPPA, 0.0, k)
-    dt = time.perf_counter() - t0
-    per_apply = dt / (2 * k + 3)
-    ms = 1e3 * per_apply * (2 * gpu_iters + 3)
-    out = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "host_cores": os.cpu_count(),
-           "sample": f"{k} CGLS iterations of the 14^4 FP64 solve (numpy, one thread: the oracle's "
-                     f"einsum contractions do not call a threaded BLAS), scaled to the {gpu_iters} "
-                     f"iterations + setup of the full solve"}
-    # the whole 4^4 solve, and one oracle dslash per sweep volume (unit links: the oracle's
-    # arithmetic does not depend on the link values)
+    _, it, res, _ = ocg.cgls(U, eta, KAPPA, TOL, MAXIT)
+    wall = time.perf_counter() - t0
+    busy = (time.process_time() - c0) / wall
+    ms = 1e3 * wall
+    out = {"value": ms, "unit": "ms", "cores": os.cpu_count(), "avg_busy_cores": busy, "kind": "oracle",
+           "sample": f"one whole oracle solve of the 14^4 workload (FP64 numpy CGLS: einsum contractions on "
+                     f"one thread, dot products on OpenBLAS threads; {busy:.1f} of {os.cpu_count()} cores busy "
+                     f"on average): {it} iterations (GPU: {gpu_iters}), true residual {res:.2e}",
+           "iterations": int(it), "true_rel_residual": float(res)}
     U4, eta4 = make_inputs((4, 4, 4, 4))
     t0 = time.perf_counter()
     _, it4, res4 = ocg.cgls(U4, eta4, KAPPA, TOL, 2000)[:3]
@@ -668,7 +676,128 @@ def _cpu_baseline(gpu_iters):
     return out
 
 
+# ---------------------------------------------------------------------------- profiling cases
+
+# Small, self-contained workloads for capturing one kernel under ncu (the commands in profiles/):
+#   python bench.py --profile-case --prec 64 --dims 14,14,14,14 --launches 5
+#   python bench.py --profile-case --prec 32 --c12 --dims 32,32,32,32 --launches 3
+#   python bench.py --profile-case --prec 64 --dims 14,14,14,14 --launches 0 --solve
+#   python bench.py --profile-case --prec 6432 --c12 --dims 16,16,16,16 --launches 0 --apply 3 --apply-df
+#   python bench.py --profile-case --prec 6432 --c12 --dims 16,16,16,32 --launches 0 --multi 12
+#   python bench.py --profile-case --prec 6432 --c12 --dims 24,24,24,48 --launches 0 --device-fields --msolve 12
+# Fields come from the seeded generators (links exp(i 0.4 H), Gaussian source; on the host, or with
+# --device-fields from the library's own generators on the device); the program prints the timing
+# of the dslash as the solver launches it (CUDA events) and, with --solve, one CG solve.
+
+def profile_case(argv):
+    ap = argparse.ArgumentParser(prog="bench.py --profile-case")
+    ap.add_argument("--prec", type=int, default=64, help="64, 32, 6432 or 6416")
+    ap.add_argument("--dims", default="14,14,14,14")
+    ap.add_argument("--c12", action="store_true")
+    ap.add_argument("--launches", type=int, default=5)
+    ap.add_argument("--dagger", action="store_true")
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--kappa", type=float, default=0.12)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--apply", type=int, default=0, help="wd_apply calls on a Gaussian field")
+    ap.add_argument("--apply-df", action="store_true",
+                    help="mixed-precision contexts: wd_apply through the double-float operator")
+    ap.add_argument("--even-odd", action="store_true")
+    ap.add_argument("--multi", type=int, default=0, help="wd_apply_multi calls on this many Gaussian fields")
+    ap.add_argument("--mgroup", type=int, default=0, help="multi-RHS group size K (0 = tuned)")
+    ap.add_argument("--msites", type=int, default=0, help="multi-RHS sites per block (0 = tuned)")
+    ap.add_argument("--msolve", type=int, default=0, help="one cg_solve_multi on this many Gaussian sources")
+    ap.add_argument("--device-fields", action="store_true", help="generate links and sources on the device")
+    ap.add_argument("--graph", type=int, default=-1,
+                    help="WD_OPT_USE_GRAPH for the solves (0 = plain launches, which ncu lists one by one)")
+    ap.add_argument("--apply-inner", action="store_true",
+                    help="mixed-precision contexts: wd_apply through the inner FP32 / FP16 operator")
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import synthetic
+    from paper_2111_14958_gb300 import wd
+
+    dims = tuple(int(v) for v in args.dims.split(","))
+    prec = args.prec | (wd.WD_EVEN_ODD if args.even_odd else 0)
+    op = wd.WilsonDirac(dims, args.kappa, (1, 1, 1, -1), prec)
+    if args.device_fields:
+        op.generate_gauge(0.4, 1, compress12=args.c12)
+    else:
+        op.load_gauge(torch.from_numpy(synthetic.gauge_field(dims, 0.4, 1)).cuda(), compress12=args.c12)
+
+    def source(seed):
+        if args.device_fields:
+            return op.generate_source(seed)
+        return torch.from_numpy(synthetic.gaussian_source(dims, seed)).cuda()
+    if args.block:
+        op.set_option(wd.WD_OPT_BLOCK_DSLASH, args.block)
+    if args.graph >= 0:
+        op.set_option(wd.WD_OPT_USE_GRAPH, args.graph)
+    if args.launches:
+        ms = op.time_dslash(args.dagger, args.launches)
+        print(f"dslash dims={dims} prec={args.prec} c12={args.c12}: {ms * 1e3:.2f} us per launch")
+    if args.apply:
+        if args.apply_df:
+            op.set_option(wd.WD_OPT_APPLY_DF, 1)
+        if args.apply_inner:
+            op.set_option(wd.WD_OPT_APPLY_INNER, 1)
+        psi = source(3)
+        if args.prec == wd.WD_PREC_F32:
+            psi = psi.to(torch.complex64)
+        out = torch.empty_like(psi)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.apply):
+            op.apply(psi, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        print(f"wd_apply x{args.apply}: {a.elapsed_time(b) / args.apply * 1e3:.2f} us per call (with packing)")
+    if args.multi:
+        if args.mgroup:
+            op.set_option(wd.WD_OPT_MULTI_GROUP, args.mgroup)
+        if args.msites:
+            op.set_option(wd.WD_OPT_MULTI_SITES, args.msites)
+        psi = torch.stack([source(10 + i) for i in range(args.multi)])
+        out = op.apply_multi(psi)  # tunes the launch shape
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            out = op.apply_multi(psi)
+        b.record()
+        torch.cuda.synchronize()
+        st = op.multi_stats()
+        print(f"wd_apply_multi x3 ({args.multi} RHS): {a.elapsed_time(b) / 3 * 1e3:.1f} us per call with packing; "
+              f"tuned group {st['group']} sites/block {st['sites_per_block']} dslash {st['dslash_ms'] * 1e3:.1f} us")
+    if args.msolve:
+        eta = torch.stack([source(100 + i) for i in range(args.msolve)])
+        x = torch.zeros_like(eta)
+        wd.cg_solve_multi(op.ctx, eta, x, args.tol, 20000)  # tunes the launch shapes
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, iters, res = wd.cg_solve_multi(op.ctx, eta, x, args.tol, 20000)
+        t1 = time.perf_counter()
+        ms = wd.wd_get_multi_stats(op.ctx)
+        print(f"cg_solve_multi ({args.msolve} RHS): status {st} iterations {max(iters)} "
+              f"max true residual {max(res):.3e} reliable updates {ms['reliable_updates']} "
+              f"group {ms['group']} sites/block {ms['sites_per_block']} ms {1e3 * (t1 - t0):.1f}")
+    if args.solve:
+        eta = source(2)
+        x, iters, res, status = op.solve(eta, tol=args.tol, maxit=4000)
+        s = op.stats()
+        print(f"solve: status {status} iterations {iters} true residual {res:.3e} "
+              f"reliable updates {s['reliable_updates']} host ms {s['solve_ms']:.3f}")
+    op.close()
+    return 0
+
+
+
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--profile-case":
+        return profile_case(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -118,6 +118,7 @@ _sig = {
     "wd_coo_build": (_I, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
     "wd_coo_spmv": (_I, [_P, ctypes.c_longlong, _P, _P, _P, _P, _P]),
     "wd_dslash_noalloc": (_I, [ctypes.POINTER(_I), _D, ctypes.POINTER(_I), _P, _P, _P, _I, _P, _P]),
+    "wd_measure_fp64_peak": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "wd_server_create": (_I, [_D, _I, ctypes.POINTER(_P)]),
     "wd_server_submit": (_I, [_P, ctypes.POINTER(WdRequest), ctypes.POINTER(ctypes.c_longlong)]),
     "wd_server_wait": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(WdResult)]),
@@ -305,6 +306,14 @@ def wd_get_residual_history(ctx, max_entries: int = 1 << 16) -> list:
     n = _I(0)
     _check(_lib.wd_get_residual_history(_P(ctx), buf, int(max_entries), ctypes.byref(n)), "wd_get_residual_history")
     return list(buf[: n.value])
+
+
+def wd_measure_fp64_peak(stream=None, repeats: int = 5) -> float:
+    """FP64 FMA throughput of the current device in TFLOP/s (the FP64 compute ceiling)."""
+    tf = _D(0.0)
+    _check(_lib.wd_measure_fp64_peak(_P(_stream_handle(stream)), int(repeats), ctypes.byref(tf)),
+           "wd_measure_fp64_peak")
+    return tf.value
 
 
 def wd_time_dslash(ctx, dagger: bool = False, launches: int = 20) -> float:
