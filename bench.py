@@ -587,55 +587,81 @@ def _even_odd(wd, dev, stream):
     return out
 
 
-def _serving(wd, n_req=60, rate=200.0, seed=7):
-    """Poisson stream of single-RHS solves through the serving runtime (continuous admission).
+SERVE_SIZES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (24, 24, 24, 48),
+               (32, 32, 32, 64)]
 
-    Sizes uniform over {8^4, 12^4, 16^4, 16^3x32, 24^3x48, 32^3x64}, kappa U[0.115, 0.124], tol in
-    {1e-8, 1e-10}, eps U[0.3, 0.5], a seeded gauge field and source per request, 150 GB budget.
-    Mixed precision on 4 concurrent slots (also with even-odd preconditioning) against plain FP64 one
-    request at a time (1 slot), same requests and arrival times. One untimed request per size first warms the resident contexts.
-    """
+
+def _serve_requests(n_req, rate, seed):
+    """A seeded Poisson stream: sizes uniform over SERVE_SIZES, kappa U[0.115, 0.124], tol in
+    {1e-8, 1e-10}, eps U[0.3, 0.5], a seeded gauge field and source per request."""
     rng = np.random.default_rng(seed)
-    sizes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (24, 24, 24, 48), (32, 32, 32, 64)]
     reqs, t = [], 0.0
     for i in range(n_req):
         t += rng.exponential(1.0 / rate)
-        reqs.append(dict(t=t, dims=sizes[int(rng.integers(6))], kappa=float(rng.uniform(0.115, 0.124)),
+        reqs.append(dict(t=t, dims=SERVE_SIZES[int(rng.integers(6))], kappa=float(rng.uniform(0.115, 0.124)),
                          tol=float([1e-8, 1e-10][int(rng.integers(2))]), eps=float(rng.uniform(0.3, 0.5)),
                          gauge_seed=10000 + i, source_seed=20000 + i))
+    return reqs
 
-    def run(precision, slots):
-        srv = wd.Server(150e9, slots)
-        warm = [srv.submit(dims=d, kappa=0.12, eps=0.4, gauge_seed=1, source_seed=2, tol=1e-8, precision=precision)
-                for d in sizes for _ in range(slots)]
-        for w in warm:
-            srv.wait(w)
-        t0 = time.perf_counter()
-        ids = []
-        for q in reqs:
-            dt = q["t"] - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            ids.append(srv.submit(dims=q["dims"], kappa=q["kappa"], eps=q["eps"], gauge_seed=q["gauge_seed"],
-                                  source_seed=q["source_seed"], tol=q["tol"], precision=precision))
-        res = [srv.wait(i) for i in ids]
-        t1 = time.perf_counter()
-        st = srv.stats()
-        srv.close()
-        lat = np.array([r["latency_ms"] for r in res])
-        ok = [r for r in res if r["status"] == 0]
-        worst = max((r["true_rel_residual"] / q["tol"]) for r, q in zip(res, reqs))
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_solve_ms": float(np.mean([r["solve_ms"] for r in res])),
-                "solves_per_s": len(res) / (t1 - t0), "completed_ok": len(ok), "requests": len(res),
-                "max_true_residual_over_tol": float(worst), "slots": slots,
-                "warm_hits": st["warm_hits"], "evictions": st["evictions"], "peak_gb": st["peak_bytes"] / 1e9}
 
-    out = {"workload": f"{n_req} requests, Poisson arrivals at {rate:g}/s (offered), sizes 8^4..32^3x64, "
+def _serve_run(wd, reqs, precision, slots, max_batch):
+    srv = wd.Server(150e9, slots, max_batch=max_batch)
+    # one untimed request per size and slot first: the resident contexts, tuned launch shapes, graphs
+    warm = [srv.submit(dims=d, kappa=0.12, eps=0.4, gauge_seed=1, source_seed=2, tol=1e-8, precision=precision)
+            for d in SERVE_SIZES for _ in range(slots)]
+    for w in warm:
+        srv.wait(w)
+    base = srv.stats()
+    t0 = time.perf_counter()
+    ids = []
+    for q in reqs:
+        dt = q["t"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(dims=q["dims"], kappa=q["kappa"], eps=q["eps"], gauge_seed=q["gauge_seed"],
+                              source_seed=q["source_seed"], tol=q["tol"], precision=precision))
+    res = [srv.wait(i) for i in ids]
+    t1 = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    worst = max((r["true_rel_residual"] / q["tol"]) for r, q in zip(res, reqs))
+    by_size = {}
+    for d in SERVE_SIZES:
+        sel = [r for r, q in zip(res, reqs) if q["dims"] == d]
+        if sel:
+            ls = np.array([r["latency_ms"] for r in sel])
+            by_size["x".join(str(v) for v in d)] = {
+                "requests": len(sel), "p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+                "mean_solve_ms": float(np.mean([r["solve_ms"] for r in sel])),
+                "mean_batch": float(np.mean([r["batch"] for r in sel]))}
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_solve_ms": float(np.mean([r["solve_ms"] for r in res])),
+            "solves_per_s": len(res) / (t1 - t0), "wall_s": t1 - t0,
+            "completed_ok": sum(1 for r in res if r["status"] == 0), "requests": len(res),
+            "max_true_residual_over_tol": float(worst), "slots": slots, "max_batch": max_batch,
+            "batches": st["batches"] - base["batches"],
+            "batched_requests": st["batched_requests"] - base["batched_requests"],
+            "warm_hits": st["warm_hits"] - base["warm_hits"], "evictions": st["evictions"],
+            "peak_gb": st["peak_bytes"] / 1e9, "by_size": by_size}
+
+
+def _serving(wd, seed=7):
+    """Poisson streams of single-RHS solves through the serving runtime (continuous admission, batches of
+    same-operator requests where the persistent loop serves them: 8^4 and 12^4 in mixed precision).
+    Above saturation (200 requests/s offered, 500 requests) and below it (15/s, 300 requests); mixed
+    precision on 4 slots with and without batching, on 1 slot, with even-odd preconditioning, and
+    plain FP64 one at a time (a 100-request sample: it serves about 4 solves/s). 150 GB budget."""
+    hi = _serve_requests(500, 200.0, seed)
+    lo = _serve_requests(300, 15.0, seed + 1)
+    out = {"workload": "Poisson arrivals, sizes uniform over 8^4, 12^4, 16^4, 16^3x32, 24^3x48, 32^3x64, "
                        "kappa U[0.115,0.124], tol {1e-8,1e-10}, eps U[0.3,0.5], 150 GB budget"}
-    out["mixed_f32_4_slots"] = run(wd.WD_PREC_MIXED_F32, 4)
-    out["mixed_f32_even_odd_4_slots"] = run(wd.WD_PREC_MIXED_F32 | wd.WD_EVEN_ODD, 4)
-    out["plain_f64_one_at_a_time"] = run(wd.WD_PREC_F64, 1)
+    out["mixed_f32_4_slots_batched_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32, 4, 8)
+    out["mixed_f32_4_slots_unbatched_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32, 4, 1)
+    out["mixed_f32_1_slot_batched_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32, 1, 8)
+    out["mixed_f32_4_slots_batched_15_per_s"] = _serve_run(wd, lo, wd.WD_PREC_MIXED_F32, 4, 8)
+    out["mixed_f32_even_odd_4_slots_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32 | wd.WD_EVEN_ODD, 4, 8)
+    out["plain_f64_1_slot_200_per_s_100_requests"] = _serve_run(wd, hi[:100], wd.WD_PREC_F64, 1, 1)
     return out
 
 
@@ -700,6 +726,7 @@ def profile_case(argv):
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--kappa", type=float, default=0.12)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0, help="WD_OPT_DSLASH_VARIANT (FP64: 1..5 = 1..16 lanes per site)")
     ap.add_argument("--apply", type=int, default=0, help="wd_apply calls on a Gaussian field")
     ap.add_argument("--apply-df", action="store_true",
                     help="mixed-precision contexts: wd_apply through the double-float operator")
@@ -734,6 +761,8 @@ def profile_case(argv):
         return torch.from_numpy(synthetic.gaussian_source(dims, seed)).cuda()
     if args.block:
         op.set_option(wd.WD_OPT_BLOCK_DSLASH, args.block)
+    if args.variant:
+        op.set_option(wd.WD_OPT_DSLASH_VARIANT, args.variant)
     if args.graph >= 0:
         op.set_option(wd.WD_OPT_USE_GRAPH, args.graph)
     if args.launches:

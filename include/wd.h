@@ -77,9 +77,11 @@ enum {
                                 precision returns to the host for each reliable update; mixed
                                 even-odd contexts and the paper's CG form use the graph); 3
                                 (default) automatic: the persistent kernel for plain FP32 on
-                                the lexicographic layout at every volume, and for the other
-                                cases it serves up to 48,000 sites, where it measured faster on
-                                GB300; the graph otherwise                                       */
+                                the lexicographic layout at every volume, for plain FP64 on it up
+                                to 65,536 sites (its launch shape, 1 to 16 threads per site,
+                                timed on the loop itself on first use), and for the other cases
+                                it serves up to 48,000 sites, where it measured faster on GB300;
+                                the graph otherwise                                              */
   WD_OPT_BLOCK_DSLASH = 3,   /* threads per block of the dslash kernel, 32..256 (0 = 256)       */
   WD_OPT_BLOCK_BLAS = 4,     /* threads per block of the BLAS-1 kernels (0 = default)            */
   WD_OPT_MAX_RESTARTS = 5,   /* max restarts from the true residual (default 5)                  */
@@ -100,10 +102,13 @@ enum {
                                 guess in both forms. Same two operator applications, stopping
                                 rule and true residual; mixed-precision contexts reject 1.       */
   WD_OPT_DSLASH_VARIANT = 11,/* FP64 single-RHS dslash (FP64 contexts, and the reliable updates
-                                of mixed ones): 0 (default) chosen with the block size on first
-                                use; 1 one thread per site; 2 two threads per site (each owns one
-                                half-spinor row). Lexicographic layout only: even-odd contexts
-                                ignore it.                                                       */
+                                of mixed ones), also inside the persistent CG loop: 0 (default)
+                                chosen with the block size on first use (the wider splits are
+                                tried up to 65,536 sites); 1 one thread per site; 2 two threads
+                                per site (each owns one half-spinor row); 3, 4, 5: 4, 8 or 16
+                                threads per site (one direction, one hop, or one hop and one
+                                half-spinor row each, summed by shuffles). Lexicographic layout
+                                only: even-odd contexts ignore it.                               */
   WD_OPT_LOOP_WAIT_LIMIT = 12,/* persistent loop: polls of 64 ns before a grid-barrier wait gives
                                 up and cg_solve returns WD_ECUDA ("a grid barrier wait gave
                                 up"), leaving the context usable; 0 or 2^26 (default, about
@@ -111,12 +116,16 @@ enum {
   WD_OPT_RESIDUAL_HISTORY = 13,/* cg_solve records the recursive residual of its first N
                                 iterations (N = value, 0 = off, the default) for
                                 wd_get_residual_history                                          */
-  WD_OPT_APPLY_INNER = 14    /* mixed precision: 1 makes wd_apply and wd_apply_multi run the inner
+  WD_OPT_APPLY_INNER = 14,   /* mixed precision: 1 makes wd_apply and wd_apply_multi run the inner
                                 solver's operator (complex128 in and out): the input is rounded
                                 into the working precision (FP32, or FP16 with a per-site FP32
                                 norm), D is applied with the FP32 links (12-real if loaded so)
                                 and the working-precision result is widened to complex128; 0
                                 (default) the FP64 operator                                      */
+  WD_OPT_MULTI_RHS_PER_THREAD = 15 /* multi-RHS, FP32 / FP16 working precision: right-hand sides
+                                held by one thread of the dslash, which loads and rebuilds each link
+                                once for all of them (1, 2 or 4; must divide the group K and not
+                                exceed the sites per block); 0 (default) = chosen by the autotuner */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */
@@ -128,7 +137,7 @@ typedef struct {
   int dslash_calls_f64;    /* of which in FP64                                                  */
   int status;              /* wd_status of the solve                                            */
   int loop_mode;           /* how the CG loop ran: 0 host loop, 1 CUDA graph, 2 persistent kernel */
-  int reserved;
+  int loop_lanes;          /* persistent FP64 loop: threads per lattice site (1, 2, 4, 8 or 16)   */
   double true_rel_residual;/* ||eta - D x|| / ||eta||, recomputed in the outer precision         */
   double solve_ms;         /* host wall time of cg_solve                                          */
   double loop_ms;          /* persistent kernel (loop_mode 2): its device time (CUDA events), all
@@ -144,6 +153,7 @@ typedef struct {
   int group;               /* K: right-hand sides per thread group sharing one link load         */
   int sites_per_block;
   int status;
+  int rhs_per_thread;      /* KT: right-hand sides per thread of the working-precision dslash     */
   double solve_ms;         /* host wall time of the solve                                       */
   double dslash_ms;        /* one multi-RHS dslash launch at the tuned shape (working precision) */
 } wd_multi_stats;
@@ -208,6 +218,29 @@ wd_status cg_solve(wd_ctx* ctx, const void* src, void* x, double tol, int maxit,
                    double* true_rel_res);
 
 /*
+ * cg_solve_batch -- n independent solves (one per context) as cg_solve would run each alone.
+ *
+ * No counterpart in the paper, which runs one solve at a time: this is the batching of the serving
+ * runtime below, open to callers with several problems of one shape. When every context has the
+ * same lattice, boundary, precision (mixed, plain FP32, or plain FP64 on the lexicographic layout)
+ * and launch shape, and its CG loop is the persistent kernel (WD_OPT_USE_GRAPH), each pass runs the
+ * contexts' prologues, ONE cooperative launch of the loop for all of them (problem i on its own
+ * blocks, with its own fields, links, kappa, tolerance, scalars and grid barrier, and the grid its
+ * solve alone uses) and their epilogues, all on ctxs[0]'s stream; reliable updates and restarts are
+ * per problem. Every result (x, iterations, residual) is therefore bitwise the result of cg_solve
+ * on that context alone. Otherwise the problems are solved one after another with cg_solve's path.
+ *   ctxs[n], srcs[n], xs[n] : n distinct contexts (1 <= n <= 64) and their device fields as in
+ *                             cg_solve (x: initial guess in, solution out);
+ *   tols[n]                 : per-problem tolerance; maxit: shared iteration limit;
+ *   iters, true_rel_res, statuses : optional host arrays of n (statuses: each problem's wd_status).
+ * Returns WD_OK if every problem converged, WD_BREAKDOWN if any broke down, else WD_NOT_CONVERGED if
+ * any reached maxit; WD_EINVAL, WD_ENOGAUGE, WD_ECUDA as cg_solve. Each context is used by this call
+ * alone while it runs.
+ */
+wd_status cg_solve_batch(wd_ctx* const* ctxs, int n, const void* const* srcs, void* const* xs, const double* tols,
+                         int maxit, int* iters, double* true_rel_res, int* statuses);
+
+/*
  * Multiple right-hand sides sharing the operator (a propagator's 12 spin-colour sources, say).
  * Fields are nrhs canonical complex128 spinor fields back to back ([nrhs][Lt][Lz][Ly][Lx][4][3]),
  * 1 <= nrhs <= 16. The multi-RHS dslash maps the K right-hand sides of a group to consecutive
@@ -246,20 +279,25 @@ wd_status wd_generate_gauge(wd_ctx* ctx, double eps, unsigned long long seed, in
 wd_status wd_generate_source(wd_ctx* ctx, unsigned long long seed, double* out);
 
 /*
- * Serving: a persistent request loop with continuous admission (no counterpart in the paper,
- * which runs one solve at a time). Each request is one single-RHS solve with its own lattice,
- * kappa, tolerance, seeded gauge field (wd_generate_gauge with eps, gauge_seed) and source
- * (seeded Gaussian, or src_host). A scheduler admits queued requests into `slots` execution
- * slots as slots free up and as device memory allows (an estimate of each request's footprint
- * is charged against budget_bytes). Every slot has its own CUDA stream and host thread, so admitted
- * solves overlap on the device; a slot keeps the contexts it created resident (least recently used
- * ones are evicted when a new volume does not fit), and a request whose volume and precision match
- * an idle slot's resident context goes there first (no allocation or graph rebuild). Results agree
- * with a solve alone up to the tolerance (same fields, same solver).
+ * Serving: a persistent request loop with continuous admission and batching (no counterpart in the
+ * paper, which runs one solve at a time). Each request is one single-RHS solve with its own
+ * lattice, kappa, tolerance, seeded gauge field (wd_generate_gauge with eps, gauge_seed) and source
+ * (seeded Gaussian, or src_host). A scheduler admits queued requests into `slots` execution slots
+ * as slots free up and as device memory allows (an estimate of each request's footprint is charged
+ * against budget_bytes): the oldest waiting request first, together with up to max_batch - 1 later
+ * requests of the same operator (lattice, precision, boundary, maxit) whose CG loop is the
+ * persistent kernel (plain FP32; plain FP64 up to 65,536 sites; mixed precision up to 48,000 sites
+ * on the lexicographic layout), which the slot solves with cg_solve_batch. Every slot has its own
+ * CUDA stream and host thread, so admitted work overlaps on the device; a slot keeps the contexts it
+ * created resident (least recently used ones are evicted when new ones do not fit), and requests
+ * whose operator matches an idle slot's resident contexts go there first (no allocation or graph
+ * rebuild). Every result is bitwise the result of the same solve alone (same fields, same solver,
+ * same launch shapes), batched or not.
  *
  * wd_server_submit queues a request (returns its id at once); wd_server_wait blocks until it is
  * done; wd_server_poll returns immediately (*done = 0/1). A finished result is returned once and
- * then forgotten. wd_server_destroy finishes running solves, drops queued ones and frees all.
+ * then forgotten. wd_server_set_max_batch sets the batch limit (1..16; 1 = no batching; default 8).
+ * wd_server_destroy finishes running solves, drops queued ones and frees all.
  * Errors: WD_EINVAL (bad request), WD_ENOMEM (a request larger than the whole budget), WD_ECUDA.
  */
 typedef struct wd_server wd_server;
@@ -288,6 +326,7 @@ typedef struct {
   double queue_ms;                 /* submit -> start                                           */
   double solve_ms;                 /* start -> done (fields generated, solved, copied out)      */
   double latency_ms;               /* submit -> done                                            */
+  int batch;                       /* requests solved together in its batch (1 = alone)         */
 } wd_result;
 
 typedef struct {
@@ -296,12 +335,15 @@ typedef struct {
   long long evictions;             /* resident contexts freed to make room                      */
   int pending;
   double used_bytes, peak_bytes;   /* device memory charged to resident contexts                */
+  long long batches;               /* batches of two or more requests run                        */
+  long long batched_requests;      /* requests that ran in such batches                          */
 } wd_server_stats;
 
 wd_status wd_server_create(double budget_bytes, int slots, wd_server** out);
 wd_status wd_server_submit(wd_server* srv, const wd_request* req, long long* id);
 wd_status wd_server_wait(wd_server* srv, long long id, wd_result* out);
 wd_status wd_server_poll(wd_server* srv, long long id, wd_result* out, int* done);
+wd_status wd_server_set_max_batch(wd_server* srv, int max_batch);
 wd_status wd_server_get_stats(wd_server* srv, wd_server_stats* out);
 void wd_server_destroy(wd_server* srv);
 

@@ -6,6 +6,7 @@
 // kernel sets the loop condition, so the host never polls inside a solve), and an epilogue that
 // recomputes the true residual. The host launches the graph, waits once, and relaunches only if
 // the recomputed residual has not reached the tolerance (a restart from the true residual).
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -14,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/wd.h"
 #include "wd_internal.h"
@@ -114,14 +116,19 @@ struct wd_ctx {
   double* mpartials;
   size_t mpartials_len;
   int mK, mspb, mgrid;        // tuned launch shape of the working-precision multi-RHS dslash
+  int mKT;                    // ... and its right-hand sides per thread (1, 2 or 4)
   int mK64, mspb64, mgrid64;  // ... of the FP64 one (mixed modes)
   cudaGraph_t mgraph;
   cudaGraphExec_t mexec;
   bool mgraph_ready;
   int force_mK, force_mspb;   // launch shape fixed by options (0 = autotuned)
+  int force_mKT;
   int tuned_block[4];         // autotuned single-RHS dslash block size per storage precision
   int tuned_var[4];           // ... and kernel variant (FP64: 1 = two threads per site)
-  int force_var;              // WD_OPT_DSLASH_VARIANT: 0 tuned, 1 one thread per site, 2 two (FP64)
+  int force_var;              // WD_OPT_DSLASH_VARIANT: 0 tuned, else 1 + variant (FP64)
+  int loop_block, loop_var;   // launch shape of the persistent FP64 loop (timed on the loop itself)
+  bool loop_tuned;
+  FieldPtr p2, r2;            // second p and r buffers of the FP64 loop with 4, 8 or 16 lanes per site
   wd_multi_stats mstats;
 };
 
@@ -187,7 +194,7 @@ int dslash_block(const wd_ctx* c, int prec) {
   return 256;
 }
 
-// FP64 single-RHS dslash: one (0) or two (1) threads per site
+// FP64 single-RHS dslash: lanes per site 1, 2, 4, 8, 16 for variant 0..4
 int dslash_variant(const wd_ctx* c, int prec) {
   if (prec != SP64) return 0;
   if (c->force_var) return c->force_var - 1;
@@ -558,16 +565,63 @@ wd_status build_graph(wd_ctx* c) {
 // (14^4: 4 %; 16^4 and above: the graph, by 1-5 %) and mixed precision (8^4: 5-8 %, 14^4: 2-3 %;
 // 24^3x48 and above: level or the graph). Plain FP32 was faster at every volume (8^4 to 32^4).
 constexpr int kPersistentMaxSites = 48000;
+// Plain FP64 on the lexicographic layout: up to 16^4, where the loop's launch shape is timed on the
+// loop itself (the split of a site over 1 to 16 lanes included) and measured level with the graph or
+// faster.
+constexpr int kPersistentMaxSitesF64 = 65536;
 
 bool persistent_loop(const wd_ctx* c) {
   if (c->cg_form || (c->eo && is_mixed(c->precision))) return false;
   if (c->use_graph == 2) return true;
   // even-odd (FP64 14^4: 4 %; FP64 24^4: the graph by 25 %) keeps to the volume limit in FP32 too
   const bool plain32 = !is_mixed(c->precision) && c->wprec == SP32 && !c->eo;
-  return c->use_graph == 3 && (plain32 || c->V <= kPersistentMaxSites);
+  const bool plain64 = c->precision == WD_PREC_F64 && !c->eo;
+  return c->use_graph == 3 && (plain32 || c->V <= (plain64 ? kPersistentMaxSitesF64 : kPersistentMaxSites));
+}
+
+}  // namespace
+
+namespace wdk {
+// The operators whose default CG loop (WD_OPT_USE_GRAPH = 3) is the persistent kernel, which
+// cg_solve_batch shares between problems (mirrors persistent_loop for a context with default options).
+bool batch_capable(const int dims[4], int precision) {
+  if (precision & WD_EVEN_ODD) return false;
+  const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  switch (precision) {
+    case WD_PREC_F32: return true;
+    case WD_PREC_F64: return V <= kPersistentMaxSitesF64;
+    case WD_PREC_MIXED_F32:
+    case WD_PREC_MIXED_F16: return V <= kPersistentMaxSites;
+  }
+  return false;
+}
+}  // namespace wdk
+
+namespace {
+
+// Shape of the persistent FP64 loop: options first, then the loop's own timing, else the dslash's.
+int loop_block_of(const wd_ctx* c) {
+  if (c->block_dslash > 0) return c->block_dslash;
+  return c->loop_tuned ? c->loop_block : dslash_block(c, c->wprec);
+}
+int loop_variant_of(const wd_ctx* c) {
+  if (c->wprec != SP64 || c->eo) return 0;
+  if (c->force_var) return c->force_var - 1;
+  return c->loop_tuned ? c->loop_var : dslash_variant(c, c->wprec);
+}
+
+// The lane loops alternate p and r between two buffers each.
+wd_status ensure_lane_buffers(wd_ctx* c) {
+  wd_status st;
+  if (!c->p2.p && (st = alloc_field(c, &c->p2, SP64)) != WD_OK) return st;
+  if (!c->r2.p && (st = alloc_field(c, &c->r2, SP64)) != WD_OK) return st;
+  return WD_OK;
 }
 
 wd_status run_persistent(wd_ctx* c, double* loop_ms) {
+  const int variant = loop_variant_of(c);
+  wd_status st;
+  if (variant >= 2 && (st = ensure_lane_buffers(c)) != WD_OK) return st;
   WD_CUDA(plain_prologue(c, c->stream, 0, 0));
   CgLoopCall L;
   memset(&L, 0, sizeof(L));
@@ -584,11 +638,13 @@ wd_status run_persistent(wd_ctx* c, double* loop_ms) {
   L.partials = c->loop_partials;
   L.bar = c->loop_sync;
   L.err = reinterpret_cast<int*>(c->loop_sync + 2);
-  L.block = dslash_block(c, c->wprec);
+  L.block = loop_block_of(c);
   L.max_grid = kLoopMaxGrid;
   L.wait_limit = c->loop_wait_limit;
-  L.variant = dslash_variant(c, c->wprec);
+  L.variant = variant;
   L.t = c->t;
+  L.p2 = c->p2;
+  L.r2 = c->r2;
   WD_CUDA(cudaEventRecord(c->ev0, c->stream));
   WD_CUDA(c->eo ? launch_cg_eo_loop(L, c->stream) : launch_cg_loop(L, c->stream));
   WD_CUDA(cudaEventRecord(c->ev1, c->stream));
@@ -736,9 +792,12 @@ wd_status autotune_single(wd_ctx* c) {
     if (tune_lookup(key, &c->tuned_block[prec], &c->tuned_var[prec])) continue;
     FieldPtr in = prec == c->wprec ? c->p : (prec == SPDF ? c->xdf : c->x64);
     FieldPtr out = prec == c->wprec ? c->q : (prec == SPDF ? c->rdf : c->r64);
-    // (block, variant); FP64 on the lexicographic layout also tries two threads per site
-    const int cands[6][2] = {{64, 0}, {128, 0}, {256, 0}, {64, 1}, {128, 1}, {256, 1}};
-    const int nc = prec == SP64 && !c->eo ? 6 : 3;
+    // (block, variant); FP64 on the lexicographic layout also tries two threads per site, and up to
+    // 65,536 sites 4, 8 and 16 lanes per site (beyond that every SM sub-partition already holds
+    // several warps of the one-thread kernel, which needs the fewest FP64 instructions per site)
+    const int cands[15][2] = {{64, 0}, {128, 0}, {256, 0}, {64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2},
+                              {256, 2}, {64, 3}, {128, 3}, {256, 3}, {64, 4}, {128, 4}, {256, 4}};
+    const int nc = prec == SP64 && !c->eo ? (c->V <= 65536 ? 15 : 6) : 3;
     const int saved_force = c->force_var;
     c->force_var = 0;
     float best = 1e30f, plain = 1e30f;  // plain: the default shape, 256 threads, one per site
@@ -773,6 +832,73 @@ wd_status autotune_single(wd_ctx* c) {
     c->tuned_block[prec] = best_b;
     c->tuned_var[prec] = best_v;
   }
+  return WD_OK;
+}
+
+// The persistent FP64 loop's launch shape (block, lanes per site), timed on the loop itself: a few
+// iterations per candidate on the solve's own fields (tolerance 0, so none stops early), CUDA events
+// around the loop kernel. The dslash timed alone ranks the candidates differently (at 12^4 the best
+// stand-alone kernel made the loop 30 % slower), because the loop's vector phases and barriers
+// follow the same grid. Remembered per problem shape like the other choices. The caller restores
+// the solve's parameters and its initial guess afterwards.
+constexpr int kLoopTuneIters = 6;
+
+wd_status autotune_loop(wd_ctx* c, bool* ran) {
+  NvtxRange nvtx_("wd:autotune_loop");
+  *ran = false;
+  if (c->loop_tuned || c->block_dslash > 0 || c->force_var) return WD_OK;
+  const TuneKey key = tune_key(c, 2, SP64, 0, 0);
+  int b = 0, v = 0;
+  if (tune_lookup(key, &b, &v)) {
+    c->loop_block = b;
+    c->loop_var = v;
+    c->loop_tuned = true;
+    return WD_OK;
+  }
+  const int def_b = dslash_block(c, SP64), def_v = dslash_variant(c, SP64);
+  const int nvar = c->V <= kPersistentMaxSitesF64 ? kMaxDslashVariant + 1 : 1;
+  float best = 1e30f, dflt = 1e30f;
+  int best_b = def_b, best_v = def_v;
+  wd_status st;
+  *ran = true;  // from here on the context's vectors and scalars are the tuner's
+  for (int var = 0; var < nvar; ++var) {
+    if (var >= 2 && (st = ensure_lane_buffers(c)) != WD_OK) return st;
+    for (int blk = 64; blk <= 256; blk *= 2) {
+      c->loop_block = blk;
+      c->loop_var = var;
+      c->loop_tuned = true;
+      float t = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        set_params_kernel<<<1, 32, 0, c->stream>>>(c->sc, 0.0, c->delta * c->delta, kLoopTuneIters, nullptr, 0);
+        WD_CUDA(cudaGetLastError());
+        double ms = 0.0;
+        if ((st = run_persistent(c, &ms)) != WD_OK) {
+          c->loop_tuned = false;
+          return st;
+        }
+        if (c->sc_host->iter != kLoopTuneIters) {  // a source the loop cannot iterate on (zero, say)
+          c->loop_tuned = false;
+          return WD_OK;
+        }
+        if ((float)ms < t) t = (float)ms;
+      }
+      if (blk == def_b && var == def_v) dflt = t;
+      if (t < best) {
+        best = t;
+        best_b = blk;
+        best_v = var;
+      }
+    }
+  }
+  // another shape must beat the stand-alone dslash's choice by 3 %, as in autotune_single
+  if (dflt <= best * 1.03f) {
+    best_b = def_b;
+    best_v = def_v;
+  }
+  tune_store(key, &best_b, &best_v);
+  c->loop_block = best_b;
+  c->loop_var = best_v;
+  c->loop_tuned = true;
   return WD_OK;
 }
 
@@ -883,6 +1009,7 @@ MDslashCall mcall(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fie
   const bool f64 = (in.prec == SP64 || in.prec == SPDF) && c->wprec != SP64;
   d.group = f64 ? c->mK64 : c->mK;
   d.sites_per_block = f64 ? c->mspb64 : c->mspb;
+  d.rhs_per_thread = f64 ? 1 : (c->mKT > 0 ? c->mKT : 1);
   d.grid_x = f64 ? c->mgrid64 : c->mgrid;
   d.status = status;
   d.partials = c->mpartials;
@@ -897,11 +1024,12 @@ cudaError_t mdslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, F
   return launch_dslash_multi(mcall(c, in, out, dagger, epi, b, result, slot, status), st);
 }
 
-// Mean time of one multi-RHS dslash launch of shape (K, spb) on the context's fields.
-wd_status time_multi_shape(wd_ctx* c, FieldPtr in, FieldPtr out, int K, int spb, int reps, float* ms) {
+// Mean time of one multi-RHS dslash launch of shape (K, spb, KT) on the context's fields.
+wd_status time_multi_shape(wd_ctx* c, FieldPtr in, FieldPtr out, int K, int spb, int kt, int reps, float* ms) {
   MDslashCall d = mcall(c, in, out, 0, EPI_PLAIN, none_field(), nullptr, TKM_MISC, nullptr);
   d.group = K;
   d.sites_per_block = spb;
+  d.rhs_per_thread = kt;
   d.grid_x = mgrid_for(c, spb);
   WD_CUDA(launch_dslash_multi(d, c->stream));  // warm-up
   WD_CUDA(cudaEventRecord(c->ev0, c->stream));
@@ -915,18 +1043,26 @@ wd_status time_multi_shape(wd_ctx* c, FieldPtr in, FieldPtr out, int K, int spb,
 
 // Time candidate launch shapes of the multi-RHS dslash on the context's fields; keep the fastest
 // (shared with later contexts of the same problem shape, like the single-RHS block size).
+// Candidates: K (right-hand sides of a group sharing each link load) among the divisors of nrhs,
+// sites per block, and for the FP32 / FP16 working precision KT = 1, 2 or 4 right-hand sides per
+// thread (each thread loads and rebuilds a link once for KT of them). K * sites per block <= 256
+// (the vector-update kernels run one thread per site and right-hand side on the same shape).
 wd_status autotune_multi(wd_ctx* c, FieldPtr in, FieldPtr out, bool f64) {
   NvtxRange nvtx_("wd:autotune_multi");
   const int N = c->mN;
-  int bestK = N, bestS = 256 / N;
+  int bestK = N, bestS = 256 / N, bestT = 1;
   float best = 1e30f;
-  const int fixK = c->force_mK, fixS = c->force_mspb;
+  const int fixK = c->force_mK, fixS = c->force_mspb, fixT = f64 ? 1 : c->force_mKT;
   const int reps = f64 ? 1 : 3;
   wd_status st;
-  const TuneKey key = tune_key(c, 1, in.prec, N, fixK * 1024 + fixS);
-  if (tune_lookup(key, &bestK, &bestS)) {
-    if (!f64 && (st = time_multi_shape(c, in, out, bestK, bestS, reps, &best)) != WD_OK) return st;
+  const TuneKey key = tune_key(c, 1, in.prec, N, (fixT * 1024 + fixK) * 1024 + fixS);
+  int packed = 0;  // sites per block | KT << 16 in the shape cache
+  if (tune_lookup(key, &bestK, &packed)) {
+    bestS = packed & 0xffff;
+    bestT = packed >> 16;
+    if (!f64 && (st = time_multi_shape(c, in, out, bestK, bestS, bestT, reps, &best)) != WD_OK) return st;
   } else {
+    const bool blocked = !f64 && (in.prec == SP32 || in.prec == SP16);
     for (int K = 1; K <= N; ++K) {
       if (N % K) continue;
       if (fixK && K != fixK) continue;
@@ -935,17 +1071,25 @@ wd_status autotune_multi(wd_ctx* c, FieldPtr in, FieldPtr out, bool f64) {
         if (fixS && spb != fixS) continue;
         const int block = K * spb;
         if (block > 256 || block < 64) continue;
-        float ms = 0.f;
-        if ((st = time_multi_shape(c, in, out, K, spb, reps, &ms)) != WD_OK) return st;
-        if (ms < best) {
-          best = ms;
-          bestK = K;
-          bestS = spb;
+        for (int kt = 1; kt <= 4; kt *= 2) {
+          if (fixT && kt != fixT) continue;
+          if (kt > 1 && (!blocked || K % kt || spb < kt)) continue;
+          float ms = 0.f;
+          if ((st = time_multi_shape(c, in, out, K, spb, kt, reps, &ms)) != WD_OK) return st;
+          if (ms < best) {
+            best = ms;
+            bestK = K;
+            bestS = spb;
+            bestT = kt;
+          }
         }
       }
     }
     if (best >= 1e29f) return fail(WD_EINVAL, "no valid multi-RHS launch shape for this nrhs and options");
-    tune_store(key, &bestK, &bestS);
+    packed = bestS | (bestT << 16);
+    tune_store(key, &bestK, &packed);
+    bestS = packed & 0xffff;
+    bestT = packed >> 16;
   }
   if (f64) {
     c->mK64 = bestK;
@@ -954,6 +1098,7 @@ wd_status autotune_multi(wd_ctx* c, FieldPtr in, FieldPtr out, bool f64) {
   } else {
     c->mK = bestK;
     c->mspb = bestS;
+    c->mKT = bestT;
     c->mgrid = mgrid_for(c, bestS);
     c->mstats.dslash_ms = best;
   }
@@ -971,6 +1116,7 @@ wd_status ensure_multi_tuned(wd_ctx* c) {
   }
   c->mstats.group = c->mK;
   c->mstats.sites_per_block = c->mspb;
+  c->mstats.rhs_per_thread = c->mKT;
   return WD_OK;
 }
 
@@ -1363,6 +1509,8 @@ void wd_destroy(wd_ctx* c) {
   free_field(&c->rdf);
   free_field(&c->etadf);
   free_field(&c->tdf);
+  free_field(&c->p2);
+  free_field(&c->r2);
   if (c->gauge_df) cudaFree(c->gauge_df);
   if (c->gauge64) cudaFree(c->gauge64);
   if (c->gauge32) cudaFree(c->gauge32);
@@ -1402,19 +1550,25 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (key == WD_OPT_BLOCK_DSLASH) {
         c->block_dslash = b;
         c->tuned_block[0] = c->tuned_block[1] = c->tuned_block[2] = c->tuned_block[3] = 0;
+        c->loop_tuned = false;
       } else
         c->block_blas = b ? b : 256;
       destroy_graph(c);  // launch shapes are baked into the graph
       return WD_OK;
     }
     case WD_OPT_MULTI_GROUP:
-    case WD_OPT_MULTI_SITES: {
+    case WD_OPT_MULTI_SITES:
+    case WD_OPT_MULTI_RHS_PER_THREAD: {
       const int v = (int)value;
       if (value != (double)v || v < 0 || v > 256) return fail(WD_EINVAL, "multi-RHS shape option out of range");
+      if (key == WD_OPT_MULTI_RHS_PER_THREAD && !(v == 0 || v == 1 || v == 2 || v == 4))
+        return fail(WD_EINVAL, "right-hand sides per thread must be 0 (tuned), 1, 2 or 4");
       if (key == WD_OPT_MULTI_GROUP)
         c->force_mK = v;
-      else
+      else if (key == WD_OPT_MULTI_SITES)
         c->force_mspb = v;
+      else
+        c->force_mKT = v;
       c->mK = c->mK64 = 0;  // re-tune (or apply the forced shape) on next use
       if (c->mexec) cudaGraphExecDestroy(c->mexec);
       if (c->mgraph) cudaGraphDestroy(c->mgraph);
@@ -1446,10 +1600,12 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       return WD_OK;
     case WD_OPT_DSLASH_VARIANT: {
       const int v = (int)value;
-      if (value != (double)v || v < 0 || v > 2) return fail(WD_EINVAL, "dslash variant must be 0, 1 or 2");
-      if (v == 2 && !(c->precision == WD_PREC_F64 || is_mixed(c->precision)))
-        return fail(WD_EINVAL, "two threads per site is an FP64 dslash variant");
+      if (value != (double)v || v < 0 || v > kMaxDslashVariant + 1)
+        return fail(WD_EINVAL, "dslash variant must be in 0..5");
+      if (v >= 2 && !(c->precision == WD_PREC_F64 || is_mixed(c->precision)))
+        return fail(WD_EINVAL, "several threads per site is an FP64 dslash variant");
       c->force_var = v;
+      c->loop_tuned = false;
       destroy_graph(c);
       return WD_OK;
     }
@@ -1596,25 +1752,49 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
   return WD_OK;
 }
 
-wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, int* iters, double* true_rel_res) {
-  NvtxRange nvtx_("wd:cg_solve");
+}  // extern "C"
+
+namespace {
+
+// One solve's progress, shared by cg_solve and cg_solve_batch.
+struct Solve {
+  const void* src;
+  void* x;
+  double tol;
+  int maxit;
+  bool persistent;
+  bool done;
+  int status;
+  int restarts;
+  double rel;
+  double loop_ms;
+  std::chrono::steady_clock::time_point t0;
+};
+
+// Checks, the inputs into the device layout (eta with ||eta||^2, x = initial guess), launch-shape
+// tuning and the graph.
+wd_status solve_begin(wd_ctx* c, Solve& v) {
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
-  if (!src || !x) return fail(WD_EINVAL, "null field pointer");
-  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(WD_EINVAL, "tol must be a positive finite number");
-  if (maxit < 0 || maxit > 10000000) return fail(WD_EINVAL, "maxit must be in [0, 10^7]");
+  if (!v.src || !v.x) return fail(WD_EINVAL, "null field pointer");
+  if (!(v.tol > 0.0) || !std::isfinite(v.tol)) return fail(WD_EINVAL, "tol must be a positive finite number");
+  if (v.maxit < 0 || v.maxit > 10000000) return fail(WD_EINVAL, "maxit must be in [0, 10^7]");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
-  const auto t0 = std::chrono::steady_clock::now();
+  v.t0 = std::chrono::steady_clock::now();
+  v.done = false;
+  v.status = ST_RUNNING;
+  v.restarts = 0;
+  v.rel = 0.0;
+  v.loop_ms = 0.0;
   const bool mixed = is_mixed(c->precision);
   const int bb = c->block_blas;
   CgScalars* sc = c->sc;
-  // inputs into the device layout: eta with ||eta||^2, x = initial guess
   FieldPtr eta = mixed ? c->eta64 : c->eta;
   FieldPtr xs = mixed ? c->x64 : c->x;
-  set_params_kernel<<<1, 32, 0, c->stream>>>(sc, tol * tol, c->delta * c->delta, maxit, c->hist_dev, c->hist_cap);
+  set_params_kernel<<<1, 32, 0, c->stream>>>(sc, v.tol * v.tol, c->delta * c->delta, v.maxit, c->hist_dev, c->hist_cap);
   WD_CUDA(cudaGetLastError());
-  WD_CUDA(launch_pack((const double*)src, eta, c->V, eo_geom(c), red_to(c, TK_PACK, &sc->eta2), bb, c->stream));
-  WD_CUDA(launch_pack((const double*)x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
+  WD_CUDA(launch_pack((const double*)v.src, eta, c->V, eo_geom(c), red_to(c, TK_PACK, &sc->eta2), bb, c->stream));
+  WD_CUDA(launch_pack((const double*)v.x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
   if (c->eo) {
     // Schur source on the even sites, in place: b_e = eta_e + kappa H_eo eta_o (eta_o is kept for
     // the reconstruction x_o = eta_o + kappa H_oe x_e)
@@ -1625,50 +1805,76 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
     WD_CUDA(launch_convert_f64_df(c->x64, c->xdf, c->V, c->V, 1, bb, c->stream));
   }
   if ((st = autotune_single(c)) != WD_OK) return st;
-  const bool persistent = persistent_loop(c);
-  if (c->use_graph && !persistent) {
+  v.persistent = persistent_loop(c);
+  if (v.persistent && c->precision == WD_PREC_F64 && !c->eo && !c->cg_form) {
+    bool ran = false;
+    if ((st = autotune_loop(c, &ran)) != WD_OK) return st;
+    if (ran) {  // the tuner iterated on this solve's fields: restore its parameters and initial guess
+      set_params_kernel<<<1, 32, 0, c->stream>>>(sc, v.tol * v.tol, c->delta * c->delta, v.maxit, c->hist_dev,
+                                                 c->hist_cap);
+      WD_CUDA(cudaGetLastError());
+      WD_CUDA(launch_pack((const double*)v.x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
+    }
+  }
+  if (c->use_graph && !v.persistent) {
     if ((st = build_graph(c)) != WD_OK) return st;
   }
-  int restarts = 0;
-  double rel = 0.0, loop_ms = 0.0;
-  int status = ST_RUNNING;
-  for (;;) {
-    if (persistent) {
-      if ((st = mixed ? run_mixed_persistent(c, &loop_ms) : run_persistent(c, &loop_ms)) != WD_OK) return st;
-    } else if (c->use_graph) {
-      WD_CUDA(cudaGraphLaunch(c->exec, c->stream));
-      WD_CUDA(cudaStreamSynchronize(c->stream));
-    } else {
-      if ((st = run_host_loop(c)) != WD_OK) return st;
-    }
-    const CgScalars& h = *c->sc_host;
-    status = h.status;
-    rel = h.eta2 > 0.0 ? std::sqrt(h.rr_true / h.eta2) : std::sqrt(h.rr_true);
-    if (!std::isfinite(h.eta2) || !std::isfinite(rel)) status = ST_BREAKDOWN;
-    if (status == ST_BREAKDOWN || status == ST_MAXIT) break;
-    if (rel <= tol) {
-      status = ST_CONVERGED;
-      break;
-    }
-    // recursive residual converged but the true one did not: restart from the true residual
-    if (h.iter >= maxit || restarts >= c->max_restarts) {
-      status = ST_MAXIT;
-      break;
-    }
-    ++restarts;
+  return WD_OK;
+}
+
+// After a pass (the scalars are in sc_host): converged, out of iterations, broken down, or a restart
+// from the true residual.
+void solve_judge(wd_ctx* c, Solve& v) {
+  const CgScalars& h = *c->sc_host;
+  int status = h.status;
+  v.rel = h.eta2 > 0.0 ? std::sqrt(h.rr_true / h.eta2) : std::sqrt(h.rr_true);
+  if (!std::isfinite(h.eta2) || !std::isfinite(v.rel)) status = ST_BREAKDOWN;
+  v.done = true;
+  if (status == ST_BREAKDOWN || status == ST_MAXIT) {
+    v.status = status;
+  } else if (v.rel <= v.tol) {
+    v.status = ST_CONVERGED;
+  } else if (h.iter >= v.maxit || v.restarts >= c->max_restarts) {
+    // recursive residual converged but the true one did not, and no restart is left
+    v.status = ST_MAXIT;
+  } else {
+    ++v.restarts;  // restart from the true residual
+    v.done = false;
   }
-  WD_CUDA(launch_unpack(xs, (double*)x, c->V, eo_geom(c), bb, c->stream));
+}
+
+wd_status solve_pass(wd_ctx* c, Solve& v) {
+  wd_status st;
+  if (v.persistent) {
+    if ((st = is_mixed(c->precision) ? run_mixed_persistent(c, &v.loop_ms) : run_persistent(c, &v.loop_ms)) != WD_OK)
+      return st;
+  } else if (c->use_graph) {
+    WD_CUDA(cudaGraphLaunch(c->exec, c->stream));
+    WD_CUDA(cudaStreamSynchronize(c->stream));
+  } else {
+    if ((st = run_host_loop(c)) != WD_OK) return st;
+  }
+  solve_judge(c, v);
+  return WD_OK;
+}
+
+// The solution back to the caller's layout, statistics, the status.
+wd_status solve_end(wd_ctx* c, Solve& v, int* iters, double* true_rel_res) {
+  const bool mixed = is_mixed(c->precision);
+  FieldPtr xs = mixed ? c->x64 : c->x;
+  WD_CUDA(launch_unpack(xs, (double*)v.x, c->V, eo_geom(c), c->block_blas, c->stream));
   WD_CUDA(cudaStreamSynchronize(c->stream));
   const CgScalars& h = *c->sc_host;
   const auto t1 = std::chrono::steady_clock::now();
   c->stats.iterations = h.iter;
-  c->stats.restarts = restarts;
-  c->stats.loop_mode = persistent ? 2 : (c->use_graph ? 1 : 0);
-  c->stats.loop_ms = loop_ms;
+  c->stats.restarts = v.restarts;
+  c->stats.loop_mode = v.persistent ? 2 : (c->use_graph ? 1 : 0);
+  c->stats.loop_lanes = v.persistent ? lanes_of_variant(loop_variant_of(c)) : 0;
+  c->stats.loop_ms = v.loop_ms;
   c->stats.reliable_updates = h.updates;
-  c->stats.true_rel_residual = rel;
-  c->stats.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-  const int launches = restarts + 1;
+  c->stats.true_rel_residual = v.rel;
+  c->stats.solve_ms = std::chrono::duration<double, std::milli>(t1 - v.t0).count();
+  const int launches = v.restarts + 1;
   if (mixed) {
     c->stats.dslash_calls_f64 = 2 * launches + h.updates;
     c->stats.dslash_calls = c->stats.dslash_calls_f64 + launches + 2 * h.iter;
@@ -1677,13 +1883,214 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
     c->stats.dslash_calls_f64 = c->wprec == SP64 ? c->stats.dslash_calls : 0;
   }
   if (iters) *iters = h.iter;
-  if (true_rel_res) *true_rel_res = rel;
+  if (true_rel_res) *true_rel_res = v.rel;
   wd_status ret = WD_OK;
-  if (status == ST_BREAKDOWN)
+  if (v.status == ST_BREAKDOWN)
     ret = fail(WD_BREAKDOWN, "CG breakdown: non-finite or non-positive scalar (NaN/Inf in the source or links?)");
-  else if (status != ST_CONVERGED)
+  else if (v.status != ST_CONVERGED)
     ret = fail(WD_NOT_CONVERGED, "maximum iterations reached before the true residual met tol");
   c->stats.status = ret;
+  return ret;
+}
+
+// ---------------------------------------------------------------- batched solves
+//
+// Several contexts of one problem shape (lattice, boundary, precision, launch shape) whose CG loop
+// is the persistent kernel: each pass runs their prologues, ONE cooperative launch of the loop for
+// all of them (each problem on its own blocks, with its own barrier counter, scalars and fields,
+// and the grid it has alone), then their epilogues. Every problem thus computes exactly what its
+// solve alone computes, in the same order. Launches that cannot keep all blocks resident are split.
+
+CgLoopCall loop_call(wd_ctx* c, int start_b) {
+  CgLoopCall L;
+  memset(&L, 0, sizeof(L));
+  L.g = c->geom;
+  L.u = gauge_for(c, c->wprec);
+  L.x = c->x;
+  L.r = c->r;
+  L.p = c->p;
+  L.q = c->q;
+  L.s = c->s;
+  L.kappa = c->kappa;
+  L.kappa_dev = &c->sc->kappa;
+  L.sc = c->sc;
+  L.partials = c->loop_partials;
+  L.bar = c->loop_sync;
+  L.err = reinterpret_cast<int*>(c->loop_sync + 2);
+  L.block = is_mixed(c->precision) ? dslash_block(c, c->wprec) : loop_block_of(c);
+  L.max_grid = kLoopMaxGrid;
+  L.wait_limit = c->loop_wait_limit;
+  L.variant = is_mixed(c->precision) ? 0 : loop_variant_of(c);
+  L.t = c->t;
+  L.p2 = c->p2;
+  L.r2 = c->r2;
+  L.start_b = start_b;
+  return L;
+}
+
+// Launch the loops of calls[0 .. n), in batches of at most kMaxBatch, halving any batch whose blocks
+// cannot all be resident.
+cudaError_t launch_loops(const CgLoopCall* calls, int n, bool mixed, cudaStream_t st) {
+  for (int i = 0; i < n;) {
+    int m = std::min(n - i, kMaxBatch);
+    for (;;) {
+      cudaError_t e = mixed ? launch_cg_mixed_loop_n(calls + i, m, st) : launch_cg_loop_n(calls + i, m, st);
+      if (e == cudaErrorCooperativeLaunchTooLarge && m > 1) {
+        cudaGetLastError();
+        m = (m + 1) / 2;
+        continue;
+      }
+      if (e != cudaSuccess) return e;
+      break;
+    }
+    i += m;
+  }
+  return cudaSuccess;
+}
+
+wd_status check_loop_errors(wd_ctx* const* cs, int n) {
+  bool failed = false;
+  for (int i = 0; i < n; ++i) {
+    unsigned flags[4];
+    WD_CUDA(cudaMemcpy(flags, cs[i]->loop_sync, sizeof(flags), cudaMemcpyDeviceToHost));
+    if (flags[2] != 0) {
+      WD_CUDA(cudaMemset(cs[i]->loop_sync, 0, sizeof(flags)));
+      failed = true;
+    }
+  }
+  if (failed) return fail(WD_ECUDA, "persistent CG loop: a grid barrier wait gave up");
+  return WD_OK;
+}
+
+// One pass over the contexts cs[0 .. n) (all persistent, same shape) on stream st.
+wd_status batch_pass(wd_ctx* const* cs, int n, cudaStream_t st, double* loop_ms) {
+  const bool mixed = is_mixed(cs[0]->precision);
+  wd_status r;
+  std::vector<CgLoopCall> calls(n);
+  for (int i = 0; i < n; ++i) {
+    wd_ctx* c = cs[i];
+    if (!mixed && loop_variant_of(c) >= 2 && (r = ensure_lane_buffers(c)) != WD_OK) return r;
+    WD_CUDA(mixed ? mixed_prologue(c, st, 0, 0) : plain_prologue(c, st, 0, 0));
+    calls[i] = loop_call(c, 0);
+  }
+  cudaEvent_t e0 = cs[0]->ev0, e1 = cs[0]->ev1;
+  std::vector<wd_ctx*> active(cs, cs + n);
+  for (int launch = 0; !active.empty(); ++launch) {
+    std::vector<CgLoopCall> now;
+    for (wd_ctx* c : active) now.push_back(loop_call(c, launch > 0));
+    WD_CUDA(cudaEventRecord(e0, st));
+    WD_CUDA(launch_loops(now.data(), (int)now.size(), mixed, st));
+    WD_CUDA(cudaEventRecord(e1, st));
+    for (wd_ctx* c : active) WD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    WD_CUDA(cudaStreamSynchronize(st));
+    if ((r = check_loop_errors(active.data(), (int)active.size())) != WD_OK) return r;
+    float ms = 0.f;
+    WD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    *loop_ms += ms;
+    if (!mixed) break;
+    // mixed precision: the problems whose reliable update is due get it and resume together
+    std::vector<wd_ctx*> next;
+    for (wd_ctx* c : active)
+      if (c->sc_host->need_update) {
+        WD_CUDA(mixed_update(c, st));
+        next.push_back(c);
+      }
+    active.swap(next);
+  }
+  for (int i = 0; i < n; ++i) {
+    wd_ctx* c = cs[i];
+    WD_CUDA(mixed ? mixed_epilogue(c, st) : plain_epilogue(c, st));
+    WD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+  }
+  WD_CUDA(cudaStreamSynchronize(st));
+  return WD_OK;
+}
+
+// Contexts that can share loop launches: persistent loop on the lexicographic layout (mixed
+// precision) or any layout the plain loop serves, identical problem shape and launch shape.
+bool batchable(wd_ctx* const* cs, const Solve* vs, int n) {
+  const wd_ctx* a = cs[0];
+  if (!vs[0].persistent || a->eo || a->cg_form) return false;
+  for (int i = 1; i < n; ++i) {
+    const wd_ctx* b = cs[i];
+    if (!vs[i].persistent || b->eo || b->cg_form || b->precision != a->precision || b->c12 != a->c12 ||
+        memcmp(&b->geom, &a->geom, sizeof(GeomH)) != 0 || b->use_df != a->use_df ||
+        dslash_block(b, b->wprec) != dslash_block(a, a->wprec) || loop_block_of(b) != loop_block_of(a) ||
+        loop_variant_of(b) != loop_variant_of(a) || b->device != a->device)
+      return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, int* iters, double* true_rel_res) {
+  NvtxRange nvtx_("wd:cg_solve");
+  Solve v;
+  v.src = src;
+  v.x = x;
+  v.tol = tol;
+  v.maxit = maxit;
+  wd_status st;
+  if ((st = solve_begin(c, v)) != WD_OK) return st;
+  while (!v.done)
+    if ((st = solve_pass(c, v)) != WD_OK) return st;
+  return solve_end(c, v, iters, true_rel_res);
+}
+
+wd_status cg_solve_batch(wd_ctx* const* ctxs, int n, const void* const* srcs, void* const* xs, const double* tols,
+                         int maxit, int* iters, double* true_rel_res, int* statuses) {
+  NvtxRange nvtx_("wd:cg_solve_batch");
+  if (!ctxs || !srcs || !xs || !tols || n < 1 || n > 64) return fail(WD_EINVAL, "null array or n outside [1, 64]");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(WD_EINVAL, "null context");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(WD_EINVAL, "a context appears twice in the batch");
+  }
+  std::vector<Solve> vs(n);
+  wd_status st;
+  for (int i = 0; i < n; ++i) {
+    vs[i].src = srcs[i];
+    vs[i].x = xs[i];
+    vs[i].tol = tols[i];
+    vs[i].maxit = maxit;
+    if ((st = solve_begin(ctxs[i], vs[i])) != WD_OK) return st;
+  }
+  wd_status ret = WD_OK;
+  if (n > 1 && batchable(ctxs, vs.data(), n)) {
+    // every context's own queued work (inputs, tuning) first, then the batch on the first one's stream
+    for (int i = 0; i < n; ++i) WD_CUDA(cudaStreamSynchronize(ctxs[i]->stream));
+    cudaStream_t s0 = ctxs[0]->stream;
+    for (;;) {
+      std::vector<wd_ctx*> run;
+      std::vector<int> idx;
+      for (int i = 0; i < n; ++i)
+        if (!vs[i].done) {
+          run.push_back(ctxs[i]);
+          idx.push_back(i);
+        }
+      if (run.empty()) break;
+      double ms = 0.0;
+      if ((st = batch_pass(run.data(), (int)run.size(), s0, &ms)) != WD_OK) return st;
+      for (size_t k = 0; k < run.size(); ++k) {
+        vs[idx[k]].loop_ms += ms;
+        solve_judge(run[k], vs[idx[k]]);
+      }
+    }
+  } else {  // one after another, each as cg_solve would run it
+    for (int i = 0; i < n; ++i)
+      while (!vs[i].done)
+        if ((st = solve_pass(ctxs[i], vs[i])) != WD_OK) return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    const wd_status r = solve_end(ctxs[i], vs[i], iters ? iters + i : nullptr, true_rel_res ? true_rel_res + i : nullptr);
+    if (statuses) statuses[i] = r;
+    if (r == WD_BREAKDOWN || (r == WD_NOT_CONVERGED && ret == WD_OK)) ret = r;
+  }
+  if (ret == WD_BREAKDOWN) fail(WD_BREAKDOWN, "CG breakdown in at least one problem of the batch");
+  else if (ret == WD_NOT_CONVERGED) fail(WD_NOT_CONVERGED, "at least one problem of the batch did not converge");
   return ret;
 }
 

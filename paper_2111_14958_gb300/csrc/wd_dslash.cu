@@ -42,6 +42,27 @@ __global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_pair_kernel(const
   }
 }
 
+template <int L, bool DAG, int EPI, bool NORM>
+__global__ void __launch_bounds__(kDslashMaxThreads) dslash_lanes_kernel(const DslashArgs<P64, false> a) {
+  if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
+  const double n2 = lanes_sites<L, DAG, EPI>(a);
+  if (NORM) {
+    double v[1] = {n2}, tot[1];
+    if (grid_reduce<OpSum, 1>(v, a.partials, a.ticket, tot) && threadIdx.x == 0) *a.result = tot[0];
+  }
+}
+
+template <int L, bool DAG, int EPI>
+static void launch_lanes(const DslashArgs<P64, false>& a, const DslashCall& c, cudaStream_t st) {
+  if (c.red.result) {
+    auto k = dslash_lanes_kernel<L, DAG, EPI, true>;
+    k<<<stride_grid(k, L * c.g.V, c.block), c.block, 0, st>>>(a);
+  } else {
+    auto k = dslash_lanes_kernel<L, DAG, EPI, false>;
+    k<<<stride_grid(k, L * c.g.V, c.block), c.block, 0, st>>>(a);
+  }
+}
+
 template <int SP, bool C12, bool DAG, int EPI>
 static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   DslashArgs<SP, C12> a;
@@ -58,6 +79,12 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   a.ticket = c.red.ticket;
   a.result = c.red.result;
   if constexpr (SP == P64 && !C12) {
+    if (c.variant >= 2) {  // 4, 8 or 16 lanes per site
+      if (c.variant == 2) launch_lanes<4, DAG, EPI>(a, c, st);
+      else if (c.variant == 3) launch_lanes<8, DAG, EPI>(a, c, st);
+      else launch_lanes<16, DAG, EPI>(a, c, st);
+      return cudaGetLastError();
+    }
     if (c.variant == 1) {  // two lanes per site
       if (c.red.result) {
         auto k = dslash_pair_kernel<C12, DAG, EPI, true>;
@@ -89,7 +116,8 @@ static cudaError_t launch_p(const DslashCall& c, cudaStream_t st) {
 
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32) return cudaErrorInvalidValue;
-  if (c.variant != 0 && (c.variant != 1 || c.in.prec != SP64)) return cudaErrorInvalidValue;
+  if (c.variant != 0 && (c.variant < 0 || c.variant > kMaxDslashVariant || c.in.prec != SP64))
+    return cudaErrorInvalidValue;
   if (c.in.prec == SPDF) {
     if (c.u.prec != SPDF) return cudaErrorInvalidValue;
     return launch_p<PDF, false>(c, st);

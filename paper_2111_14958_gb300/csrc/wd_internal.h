@@ -110,8 +110,10 @@ struct DslashCall {
   Red red;          // optional |out|^2
   int block;
   const double* kappa_dev;  // optional: kappa read from device memory (overrides `kappa`)
-  int variant;              // FP64 only: 0 one thread per site, 1 two threads per site
+  int variant;              // FP64 only: lanes per site 1, 2, 4, 8, 16 for variant 0..4
 };
+constexpr int kMaxDslashVariant = 4;
+inline int lanes_of_variant(int v) { return v <= 0 ? 1 : (1 << v); }
 
 // Launchers. Each returns cudaGetLastError() after the launch.
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st);
@@ -126,20 +128,27 @@ struct CgLoopCall {
   const double* kappa_dev;
   CgScalars* sc;
   double* partials;  // >= 3 * max_grid
-  unsigned* bar;     // two counters, zero at the first launch (the kernel leaves them reusable)
+  unsigned* bar;     // 64-bit barrier counter (8-byte aligned); each launcher zeroes it first
   int* err;          // zero; set to 1 if a barrier wait gave up
   int block;
   int max_grid;
   int variant;  // FP64: 1 = the dslash phases use two lanes per site
   int start_b;  // mixed loop: resume at the D^dag half of an iteration (after a reliable update)
   FieldPtr t;   // even-odd loop: the odd-site temporary
+  FieldPtr p2, r2;  // FP64 loop with 4, 8 or 16 lanes per site: second buffers of p and r
   long long wait_limit;  // grid-barrier polls (64 ns sleep each) before a wait gives up
 };
 constexpr long long kLoopWaitLimit = 1LL << 26;  // about 4 s
 cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st);
+// Up to kMaxBatch loops of the same shape (lattice, precision, launch shape) in one cooperative
+// launch, each problem on its own blocks (blockIdx.y) with the grid it has alone; returns
+// cudaErrorCooperativeLaunchTooLarge when the batch's blocks cannot all be resident.
+constexpr int kMaxBatch = 8;
+cudaError_t launch_cg_loop_n(const CgLoopCall* cs, int n, cudaStream_t st);
 // The inner loop of the mixed-precision solver (x = x_lo in FP32; r, p, q, s in the working
 // precision) as one cooperative launch that returns when a reliable update is due or the loop ends.
 cudaError_t launch_cg_mixed_loop(const CgLoopCall& c, cudaStream_t st);
+cudaError_t launch_cg_mixed_loop_n(const CgLoopCall* cs, int n, cudaStream_t st);
 // The plain CGLS loop on the even-site Schur complement of a parity-ordered context.
 cudaError_t launch_cg_eo_loop(const CgLoopCall& c, cudaStream_t st);
 constexpr int kLoopMaxGrid = 8192;
@@ -222,7 +231,9 @@ struct MDslashCall {
   int dagger, epi;
   int nrhs;             // right-hand sides in the fields
   int group;            // K: right-hand sides per thread group (divides nrhs)
-  int sites_per_block;  // block = group * sites_per_block <= 256
+  int sites_per_block;  // group * sites_per_block <= 256
+  int rhs_per_thread;   // KT: 0 or 1, or (FP32 / FP16) 2 or 4 right-hand sides per thread, sharing
+                        // each link load; block = group / KT * sites_per_block
   int grid_x;           // blocks per group (grid-stride over sites)
   const int* status;    // optional per-RHS status mask (only ST_RUNNING computed)
   double* partials;     // >= nrhs * grid_x

@@ -14,28 +14,28 @@ namespace wdk {
 // completes; its wait is still bounded: past the limit the kernel records an error and stops.
 
 struct LoopSync {
-  unsigned* bar;    // [0] arrivals, [1] generation
-  int* err;         // set to 1 when a barrier wait gave up
-  long long limit;  // polls (64 ns sleep each) before a wait gives up
+  unsigned long long* ctr;  // arrivals since the launch began (zeroed by the host before each launch)
+  int* err;                 // set to 1 when a barrier wait gave up
+  long long limit;          // polls (64 ns sleep each) before a wait gives up
 };
 
 // All blocks arrive, then continue. Returns false (everywhere, eventually) if a wait gave up.
+// One monotonic 64-bit counter: barrier number k of the launch completes when the counter reaches
+// k * gridDim.x, so a waiter sees the last arrival's own atomic (no second release step), and the
+// last block to arrive does not wait at all.
 __device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = y.bar + 1;
-    const unsigned g0 = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(y.bar, 1u);
+    const unsigned long long G = gridDim.x;
+    __threadfence();  // this block's writes are visible before its arrival is
+    const unsigned long long arrived = atomicAdd(y.ctr, 1ull);
+    const unsigned long long target = (arrived / G + 1) * G;
     int good = 1;
-    if (arrived == gridDim.x - 1) {
-      y.bar[0] = 0u;
-      __threadfence();
-      atomicAdd(y.bar + 1, 1u);
-    } else {
+    if (arrived + 1 != target) {
+      volatile unsigned long long* ctr = y.ctr;
       long long spins = 0;
-      while (*gen == g0) {
+      while (*ctr < target) {
         if (++spins > y.limit || *(volatile int*)y.err) {
           atomicExch(y.err, 1);
           good = 0;
@@ -75,6 +75,42 @@ __device__ __forceinline__ bool loop_sum(double v, double* partials, const LoopS
   return true;
 }
 
+// Two sums behind one barrier (partials: two regions of gridDim.x).
+__device__ __forceinline__ bool loop_sum2(double v0, double v1, double* partials, const LoopSync& y, double* o0,
+                                          double* o1) {
+  __shared__ double smem[64];
+  __shared__ double total[2];
+  const int G = gridDim.x;
+  double w[2] = {v0, v1};
+  block_reduce<OpSum, 2>(w, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = w[0];
+    partials[G + blockIdx.x] = w[1];
+    __threadfence();
+  }
+  if (!grid_barrier(y)) return false;
+  if (threadIdx.x < 32) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = threadIdx.x; b < G; b += 32) {
+      a0 += __ldcg(partials + b);
+      a1 += __ldcg(partials + G + b);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, off);
+      a1 += __shfl_down_sync(0xffffffffu, a1, off);
+    }
+    if (threadIdx.x == 0) {
+      total[0] = a0;
+      total[1] = a1;
+    }
+  }
+  __syncthreads();
+  *o0 = total[0];
+  *o1 = total[1];
+  return true;
+}
+
 template <int SP, bool C12>
 struct LoopArgs {
   DslashArgs<SP, C12> dq;  // q = D p
@@ -86,10 +122,10 @@ struct LoopArgs {
   LoopSync y;
 };
 
-// The dslash phases of the loop: one thread per site, or (FP64, PAIR) two lanes per site.
-template <int SP, bool C12, bool DAG, bool PAIR>
+// The dslash phases of the loop: one thread per site, or (FP64) two lanes per site.
+template <int SP, bool C12, bool DAG, int LANES>
 __device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int n, int t0, int tstep) {
-  if constexpr (SP == P64 && PAIR) {
+  if constexpr (SP == P64 && LANES == 2) {
     return pair_sites<C12, DAG, EPI_PLAIN>(d);
   } else {
     double v = 0.0;
@@ -98,8 +134,24 @@ __device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int 
   }
 }
 
-template <int SP, bool C12, bool PAIR>
-__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value) cg_loop_kernel(const LoopArgs<SP, C12> a) {
+// A batch of independent loops in one cooperative launch: blockIdx.y selects the problem, whose
+// blocks run exactly the body (and the grid, gridDim.x) of its launch alone, with its own barrier
+// counter, scalars and fields, so each result is bitwise the one of a launch of its own.
+constexpr int kLoopBatch = kMaxBatch;
+template <typename Args>
+struct LoopBatch {
+  Args a[kLoopBatch];
+};
+// The batch kernels read their arguments with a runtime index (blockIdx.y), so the pointers and
+// geometry live in registers rather than in the constant bank: they get the register budget of
+// two blocks per SM instead of three (FP32 / FP16), which the small volumes they serve leave free.
+template <int SP>
+struct BatchMinBlocks {
+  static constexpr int value = SP == P64 ? 1 : 2;
+};
+
+template <int SP, bool C12, int LANES>
+__device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
   typedef typename RealOf<SP>::type R;
   CgScalars* sc = a.sc;
   if (sc->status != ST_RUNNING) return;  // uniform over the grid
@@ -112,7 +164,7 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
   double alpha = 0.0, beta = 0.0;
   for (;;) {
     // q = D p, |q|^2
-    double v = loop_dslash<SP, C12, false, PAIR>(a.dq, n, t0, tstep);
+    double v = loop_dslash<SP, C12, false, LANES>(a.dq, n, t0, tstep);
     double qq;
     if (!loop_sum(v, a.partials, a.y, &qq)) break;
     if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
@@ -145,7 +197,7 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
     // s = D^dag r, |s|^2 (not needed once converged)
     double gnew = 0.0;
     if (!conv) {
-      v = loop_dslash<SP, C12, true, PAIR>(a.ds, n, t0, tstep);
+      v = loop_dslash<SP, C12, true, LANES>(a.ds, n, t0, tstep);
       if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
     }
     const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
@@ -200,6 +252,17 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
   }
 }
 
+template <int SP, bool C12, int LANES>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value) cg_loop_kernel(const LoopArgs<SP, C12> a) {
+  cg_loop_body<SP, C12, LANES>(a);
+}
+
+template <int SP, bool C12, int LANES>
+__global__ void __launch_bounds__(kDslashMaxThreads, BatchMinBlocks<SP>::value)
+    cg_loop_batch_kernel(const __grid_constant__ LoopBatch<LoopArgs<SP, C12>> b) {
+  cg_loop_body<SP, C12, LANES>(b.a[blockIdx.y]);
+}
+
 // The inner loop of the mixed-precision solver (FP32 or FP16 vectors, x_lo in FP32) in one
 // cooperative launch. Phase A: q = D p, |q|^2; r_lo -= alpha q, x_lo += alpha p, |r_lo|^2, and
 // the reliable-update test. Phase B: s = D^dag r_lo, |s|^2; p = s + beta p. The kernel starts at A
@@ -219,8 +282,7 @@ struct MixedLoopArgs {
 };
 
 template <int SPW, bool C12>
-__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SPW>::value)
-    cg_mixed_loop_kernel(const MixedLoopArgs<SPW, C12> a) {
+__device__ __forceinline__ void cg_mixed_loop_body(const MixedLoopArgs<SPW, C12>& a) {
   CgScalars* sc = a.sc;
   const int st_in = sc->status;
   if (st_in != ST_RUNNING && !(a.start_b && st_in == ST_CONVERGED)) return;  // uniform over the grid
@@ -327,7 +389,19 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SPW>::value
 }
 
 template <int SPW, bool C12>
-static cudaError_t mixed_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SPW>::value)
+    cg_mixed_loop_kernel(const MixedLoopArgs<SPW, C12> a) {
+  cg_mixed_loop_body<SPW, C12>(a);
+}
+
+template <int SPW, bool C12>
+__global__ void __launch_bounds__(kDslashMaxThreads, BatchMinBlocks<SPW>::value)
+    cg_mixed_loop_batch_kernel(const __grid_constant__ LoopBatch<MixedLoopArgs<SPW, C12>> b) {
+  cg_mixed_loop_body<SPW, C12>(b.a[blockIdx.y]);
+}
+
+template <int SPW, bool C12>
+static MixedLoopArgs<SPW, C12> mixed_loop_args(const CgLoopCall& c) {
   MixedLoopArgs<SPW, C12> a;
   for (DslashArgs<SPW, C12>* d : {&a.dq, &a.ds}) {
     memcpy(&d->g, &c.g, sizeof(Geom));
@@ -354,29 +428,88 @@ static cudaError_t mixed_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   a.start_b = c.start_b;
   a.sc = c.sc;
   a.partials = c.partials;
-  a.y.bar = c.bar;
+  a.y.ctr = reinterpret_cast<unsigned long long*>(c.bar);
   a.y.limit = c.wait_limit;
   a.y.err = c.err;
-  auto k = cg_mixed_loop_kernel<SPW, C12>;
-  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
-  const int need = grid_for(c.g.V, c.block);
-  if (need < grid) grid = need;
-  if (grid > c.max_grid) grid = c.max_grid;
-  void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+  return a;
 }
 
-cudaError_t launch_cg_mixed_loop(const CgLoopCall& c, cudaStream_t st) {
+// Grid of the loop over `threads` threads: one wave of resident blocks of the single-problem kernel,
+// or fewer when the sites do not fill it. A batch uses the same grid per problem.
+static int loop_grid(const void* single_kernel, int threads, const CgLoopCall& c) {
+  int grid = resident_blocks(single_kernel, c.block);
+  const int need = grid_for(threads, c.block);
+  if (need < grid) grid = need;
+  if (grid > c.max_grid) grid = c.max_grid;
+  return grid;
+}
+
+// One problem: the single kernel with its arguments in parameter space. Several: the batch kernel
+// on a (grid, n) grid, when all n * grid blocks can be resident at once (else the launch is refused
+// with cudaErrorCooperativeLaunchTooLarge and the caller splits the batch).
+template <typename Args, typename KS, typename KB>
+static cudaError_t loop_launch(KS single, KB batch, Args (*make)(const CgLoopCall&), const CgLoopCall* cs, int n,
+                               int threads, cudaStream_t st) {
+  const CgLoopCall& c0 = cs[0];
+  const int grid = loop_grid(reinterpret_cast<const void*>(single), threads, c0);
+  for (int i = 0; i < n; ++i) {  // barrier count of this launch
+    cudaError_t e = cudaMemsetAsync(cs[i].bar, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (n == 1) {
+    Args a = make(c0);
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(single), dim3(grid), dim3(c0.block), args, 0, st);
+  }
+  if (n > kLoopBatch) return cudaErrorInvalidValue;
+  if ((long long)grid * n > resident_blocks(reinterpret_cast<const void*>(batch), c0.block))
+    return cudaErrorCooperativeLaunchTooLarge;
+  LoopBatch<Args> b;
+  memset(&b, 0, sizeof(b));
+  for (int i = 0; i < n; ++i) b.a[i] = make(cs[i]);
+  void* args[] = {&b};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(batch), dim3(grid, n), dim3(c0.block), args, 0, st);
+}
+
+// Every call of a batch must describe the same problem shape (lattice, precisions, launch shape).
+static bool same_shape(const CgLoopCall* cs, int n) {
+  for (int i = 1; i < n; ++i) {
+    const CgLoopCall &a = cs[0], &b = cs[i];
+    if (memcmp(&a.g, &b.g, sizeof(GeomH)) != 0 || a.block != b.block || a.variant != b.variant ||
+        a.max_grid != b.max_grid || a.u.prec != b.u.prec || a.u.c12 != b.u.c12 || a.r.prec != b.r.prec ||
+        a.x.prec != b.x.prec)
+      return false;
+  }
+  return true;
+}
+
+cudaError_t launch_cg_mixed_loop_n(const CgLoopCall* cs, int n, cudaStream_t st) {
+  if (n < 1 || !same_shape(cs, n)) return cudaErrorInvalidValue;
+  const CgLoopCall& c = cs[0];
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1) return cudaErrorInvalidValue;
-  if (c.x.prec != SP32 || c.u.prec != SP32 || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec)
-    return cudaErrorInvalidValue;
-  if (c.r.prec == SP32) return c.u.c12 ? mixed_loop_launch_t<P32, true>(c, st) : mixed_loop_launch_t<P32, false>(c, st);
-  if (c.r.prec == SP16) return c.u.c12 ? mixed_loop_launch_t<P16, true>(c, st) : mixed_loop_launch_t<P16, false>(c, st);
+  for (int i = 0; i < n; ++i) {
+    const CgLoopCall& d = cs[i];
+    if (d.x.prec != SP32 || d.u.prec != SP32 || d.p.prec != d.r.prec || d.q.prec != d.r.prec || d.s.prec != d.r.prec)
+      return cudaErrorInvalidValue;
+  }
+  const int th = c.g.V;
+  if (c.r.prec == SP32) {
+    if (c.u.c12)
+      return loop_launch(cg_mixed_loop_kernel<P32, true>, cg_mixed_loop_batch_kernel<P32, true>, mixed_loop_args<P32, true>, cs, n, th, st);
+    return loop_launch(cg_mixed_loop_kernel<P32, false>, cg_mixed_loop_batch_kernel<P32, false>, mixed_loop_args<P32, false>, cs, n, th, st);
+  }
+  if (c.r.prec == SP16) {
+    if (c.u.c12)
+      return loop_launch(cg_mixed_loop_kernel<P16, true>, cg_mixed_loop_batch_kernel<P16, true>, mixed_loop_args<P16, true>, cs, n, th, st);
+    return loop_launch(cg_mixed_loop_kernel<P16, false>, cg_mixed_loop_batch_kernel<P16, false>, mixed_loop_args<P16, false>, cs, n, th, st);
+  }
   return cudaErrorInvalidValue;
 }
 
-template <int SP, bool C12, bool PAIR>
-static cudaError_t loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
+cudaError_t launch_cg_mixed_loop(const CgLoopCall& c, cudaStream_t st) { return launch_cg_mixed_loop_n(&c, 1, st); }
+
+template <int SP, bool C12>
+static LoopArgs<SP, C12> plain_loop_args(const CgLoopCall& c) {
   LoopArgs<SP, C12> a;
   for (DslashArgs<SP, C12>* d : {&a.dq, &a.ds}) {
     memcpy(&d->g, &c.g, sizeof(Geom));
@@ -402,30 +535,177 @@ static cudaError_t loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   a.n = c.g.V;
   a.sc = c.sc;
   a.partials = c.partials;
-  a.y.bar = c.bar;
+  a.y.ctr = reinterpret_cast<unsigned long long*>(c.bar);
   a.y.limit = c.wait_limit;
   a.y.err = c.err;
-  auto k = cg_loop_kernel<SP, C12, PAIR>;
-  int grid = resident_blocks(reinterpret_cast<const void*>(k), c.block);
-  const int need = grid_for(PAIR ? 2 * c.g.V : c.g.V, c.block);
-  if (need < grid) grid = need;
-  if (grid > c.max_grid) grid = c.max_grid;
-  void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
+  return a;
 }
 
-cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st) {
+template <int SP, bool C12, int LANES>
+static cudaError_t loop_launch_t(const CgLoopCall* cs, int n, cudaStream_t st) {
+  return loop_launch(cg_loop_kernel<SP, C12, LANES>, cg_loop_batch_kernel<SP, C12, LANES>, plain_loop_args<SP, C12>, cs,
+                     n, LANES * cs[0].g.V, st);
+}
+
+// ---------------------------------------------------------------- persistent CG loop, FP64 lanes
+//
+// At the paper's small volumes (up to 16^4) the FP64 loop is bound by latency: each grid barrier
+// costs a few microseconds, as much as a phase's arithmetic. With 4, 8 or 16 lanes per site the
+// iteration is fused into two passes and two barriers instead of four:
+//   A: p_k = s + beta p_{k-1} formed at every neighbour it is read at (p_0 as the prologue left it),
+//      q = D p_k, |q|^2; the site's p_k is stored;                          barrier, alpha = gamma/|q|^2
+//   B: r_k = r_{k-1} - alpha q formed likewise, s = D^dag r_k, |s|^2, |r_k|^2; x += alpha p_k;
+//      the site's r_k is stored;                                            barrier, beta, convergence
+// p and r alternate between two buffers, so no pass overwrites a field another lane still reads at a
+// neighbour; the vector arithmetic (fma(beta, p, s), fma(-alpha, q, r)) is that of the four-phase
+// loop, and the scalars and stopping rule are the same.
+struct LanesLoopArgs {
+  Geom g;
+  GaugeRef<double, false> u;
+  const double* kappa_dev;
+  double2 *x, *p0, *p1, *r0, *r1, *q, *s;
+  CgScalars* sc;
+  double* partials;  // 3 x gridDim.x
+  LoopSync y;
+};
+
+template <int L>
+__device__ __forceinline__ void cg_loop_lanes_body(const LanesLoopArgs& a) {
+  CgScalars* sc = a.sc;
+  if (sc->status != ST_RUNNING) return;  // uniform over the grid
+  const int G = gridDim.x;
+  double gamma = sc->gamma, rr = sc->rr;
+  const double tol2e = sc->tol2 * sc->eta2;
+  int iter = sc->iter, status = ST_RUNNING;
+  const int maxit = sc->maxit;
+  double alpha = 0.0, beta = 0.0;
+  const double mk = -*a.kappa_dev;
+  int pi = 0, ri = 0;  // which of the two buffers holds p_{k-1} / r_{k-1} (selects, not indexing)
+  bool first = true;
+  for (;;) {
+    // A: q = D p_k, |q|^2
+    double nq = 0.0, nw = 0.0;
+    if (first) {
+      const FusedPass f = {pi ? a.p1 : a.p0, nullptr, 0.0, nullptr, a.q, nullptr, nullptr, 0.0};
+      lanes_fused_sites<L, false, false>(a.g, a.u, mk, f, nq, nw);
+    } else {
+      const FusedPass f = {a.s, pi ? a.p1 : a.p0, beta, pi ? a.p0 : a.p1, a.q, nullptr, nullptr, 0.0};
+      lanes_fused_sites<L, false, true>(a.g, a.u, mk, f, nq, nw);
+      pi ^= 1;
+    }
+    first = false;
+    double qq;
+    if (!loop_sum(nq, a.partials, a.y, &qq)) break;
+    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / qq;
+    // B: s = D^dag r_k, |s|^2, |r_k|^2; x += alpha p_k
+    double ns = 0.0, nr = 0.0;
+    {
+      const FusedPass f = {ri ? a.r1 : a.r0, a.q, -alpha, ri ? a.r0 : a.r1, a.s, a.x, pi ? a.p1 : a.p0, alpha};
+      lanes_fused_sites<L, true, true>(a.g, a.u, mk, f, ns, nr);
+      ri ^= 1;
+    }
+    double gnew;
+    if (!loop_sum2(ns, nr, a.partials + G, a.y, &gnew, &rr)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr);
+    if (!isfinite(rr)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    iter += 1;
+    if (rr <= tol2e) {
+      status = ST_CONVERGED;
+      break;
+    }
+    if (!(isfinite(gnew) && gamma > 0.0)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    beta = gnew / gamma;
+    gamma = gnew;
+    if (iter >= maxit) {
+      status = ST_MAXIT;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->alpha = alpha;
+    sc->beta = beta;
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kDslashMaxThreads) cg_loop_lanes_kernel(const LanesLoopArgs a) {
+  cg_loop_lanes_body<L>(a);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kDslashMaxThreads) cg_loop_lanes_batch_kernel(const __grid_constant__ LoopBatch<LanesLoopArgs> b) {
+  cg_loop_lanes_body<L>(b.a[blockIdx.y]);
+}
+
+static LanesLoopArgs lanes_loop_args(const CgLoopCall& c) {
+  LanesLoopArgs a;
+  memcpy(&a.g, &c.g, sizeof(Geom));
+  a.u.p = reinterpret_cast<const double2*>(c.u.p);
+  a.kappa_dev = c.kappa_dev;
+  a.x = reinterpret_cast<double2*>(c.x.p);
+  a.p0 = reinterpret_cast<double2*>(c.p.p);
+  a.p1 = reinterpret_cast<double2*>(c.p2.p);
+  a.r0 = reinterpret_cast<double2*>(c.r.p);
+  a.r1 = reinterpret_cast<double2*>(c.r2.p);
+  a.q = reinterpret_cast<double2*>(c.q.p);
+  a.s = reinterpret_cast<double2*>(c.s.p);
+  a.sc = c.sc;
+  a.partials = c.partials;
+  a.y.ctr = reinterpret_cast<unsigned long long*>(c.bar);
+  a.y.limit = c.wait_limit;
+  a.y.err = c.err;
+  return a;
+}
+
+template <int L>
+static cudaError_t lanes_loop_launch_t(const CgLoopCall* cs, int n, cudaStream_t st) {
+  return loop_launch(cg_loop_lanes_kernel<L>, cg_loop_lanes_batch_kernel<L>, lanes_loop_args, cs, n, L * cs[0].g.V, st);
+}
+
+cudaError_t launch_cg_loop_n(const CgLoopCall* cs, int n, cudaStream_t st) {
+  if (n < 1 || !same_shape(cs, n)) return cudaErrorInvalidValue;
+  const CgLoopCall& c = cs[0];
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32 || c.max_grid < 1) return cudaErrorInvalidValue;
-  if (c.x.prec != c.r.prec || c.p.prec != c.r.prec || c.q.prec != c.r.prec || c.s.prec != c.r.prec)
-    return cudaErrorInvalidValue;
+  for (int i = 0; i < n; ++i) {
+    const CgLoopCall& d = cs[i];
+    if (d.x.prec != d.r.prec || d.p.prec != d.r.prec || d.q.prec != d.r.prec || d.s.prec != d.r.prec)
+      return cudaErrorInvalidValue;
+    if (d.r.prec == SP64 && d.variant >= 2 &&
+        (!d.p2.p || !d.r2.p || d.p2.prec != SP64 || d.r2.prec != SP64))
+      return cudaErrorInvalidValue;
+  }
   if (c.r.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;
-    return c.variant == 1 ? loop_launch_t<P64, false, true>(c, st) : loop_launch_t<P64, false, false>(c, st);
+    switch (c.variant) {
+      case 0: return loop_launch_t<P64, false, 1>(cs, n, st);
+      case 1: return loop_launch_t<P64, false, 2>(cs, n, st);
+      case 2: return lanes_loop_launch_t<4>(cs, n, st);
+      case 3: return lanes_loop_launch_t<8>(cs, n, st);
+      case 4: return lanes_loop_launch_t<16>(cs, n, st);
+    }
+    return cudaErrorInvalidValue;
   }
   if (c.r.prec == SP32 && c.u.prec == SP32)
-    return c.u.c12 ? loop_launch_t<P32, true, false>(c, st) : loop_launch_t<P32, false, false>(c, st);
+    return c.u.c12 ? loop_launch_t<P32, true, 1>(cs, n, st) : loop_launch_t<P32, false, 1>(cs, n, st);
   return cudaErrorInvalidValue;
 }
+
+cudaError_t launch_cg_loop(const CgLoopCall& c, cudaStream_t st) { return launch_cg_loop_n(&c, 1, st); }
 
 // ---------------------------------------------------------------- persistent CG loop, even-odd
 //
@@ -581,7 +861,7 @@ static cudaError_t eo_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   a.n = c.g.V / 2;
   a.sc = c.sc;
   a.partials = c.partials;
-  a.y.bar = c.bar;
+  a.y.ctr = reinterpret_cast<unsigned long long*>(c.bar);
   a.y.limit = c.wait_limit;
   a.y.err = c.err;
   auto k = cg_eo_loop_kernel<SP, C12>;
@@ -590,6 +870,8 @@ static cudaError_t eo_loop_launch_t(const CgLoopCall& c, cudaStream_t st) {
   if (need < grid) grid = need;
   if (grid > c.max_grid) grid = c.max_grid;
   void* args[] = {&a};
+  cudaError_t e = cudaMemsetAsync(c.bar, 0, sizeof(unsigned long long), st);  // barrier count of this launch
+  if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(c.block), args, 0, st);
 }
 

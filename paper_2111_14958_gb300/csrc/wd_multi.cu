@@ -198,8 +198,11 @@ struct MReal<PDF> {
 // memory) then holds the group's totals for rl < K, valid after the function returns (it ends
 // with a barrier). Layout of `partials` (fixed offsets): block partials [r][gridDim.x], run
 // partials [kMaxRhs][kMaxMultiRuns], run tickets [kMaxRhs][kMaxMultiRuns] (zero between launches).
-__device__ bool mreduce(double v, int K, double* partials, unsigned* tickets, double* sh /* >= blockDim + 2*kMaxRhs */,
-                        double* out) {
+//
+// mreduce_sh takes the block's values already in sh[0 .. nv) (value i belongs to right-hand side
+// i % K; nv = K * sites per block, which may exceed blockDim.x when a thread holds several
+// right-hand sides); the block needs at least K threads.
+__device__ bool mreduce_sh(int nv, int K, double* partials, unsigned* tickets, double* sh, double* out) {
   const int t = threadIdx.x, nt = blockDim.x, G = gridDim.x, y = blockIdx.y, b = blockIdx.x;
   double* p1 = partials;
   double* p2 = partials + (size_t)kMaxRhs * kMaxMultiGrid;
@@ -207,11 +210,9 @@ __device__ bool mreduce(double v, int K, double* partials, unsigned* tickets, do
   const int nruns = (G + kRedGroup - 1) / kRedGroup, run = b / kRedGroup;
   const int rsize = min(kRedGroup, G - run * kRedGroup);
   __shared__ int flag;
-  sh[t] = v;
-  __syncthreads();
   if (t < K) {
     double a = 0.0;
-    for (int i = t; i < nt; i += K) a += sh[i];
+    for (int i = t; i < nv; i += K) a += sh[i];
     p1[(size_t)(y * K + t) * G + b] = a;
     __threadfence();  // each writer publishes its partial before the ticket is taken
   }
@@ -264,6 +265,13 @@ __device__ bool mreduce(double v, int K, double* partials, unsigned* tickets, do
   if (t == 0) tickets[y] = 0u;
   __syncthreads();
   return true;
+}
+
+__device__ bool mreduce(double v, int K, double* partials, unsigned* tickets, double* sh /* >= blockDim + 2*kMaxRhs */,
+                        double* out) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  return mreduce_sh(blockDim.x, K, partials, tickets, sh, out);
 }
 
 // ---------------------------------------------------------------- multi-RHS dslash
@@ -333,10 +341,129 @@ __device__ __forceinline__ void mhops_rt(const MArgs<SP, C12>& a, R mk, int s, i
   }
 }
 
+// Both hops of direction mu for KT right-hand sides r0 .. r0 + KT - 1 of one site: each link is
+// loaded (and, with 12 reals, its third row rebuilt) once and applied to the KT half-spinors, so the
+// link's instructions are shared and only the projection, SU(3) product and reconstruction are
+// per right-hand side. The per-right-hand-side arithmetic is that of mhop, in the same order.
+template <int MU, int SF, int KT, int SP, bool C12, typename R>
+__device__ __forceinline__ void mhop_kt(const MArgs<SP, C12>& a, R mk, int s, int r0, const int (&c)[4],
+                                        Cx<R> (&acc)[KT][12]) {
+  const int V = a.g.V, N = a.N;
+  {
+    const bool wrap = c[MU] == a.g.L[MU] - 1;
+    const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
+    const R k0 = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
+    Cx<R> u[9];
+    load_link(a.u, MU, s, V, u);
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+      Cx<R> psi[12], h[6], chi[6];
+      const R k = mload_hop(a.in, nb, r0 + j, V, N, psi, k0);
+      spin_project<MU, SF>(psi, h);
+      su3_mul(u, h, chi);
+      spin_reconstruct<MU, SF>(acc[j], chi, k);
+    }
+  }
+  {
+    const bool wrap = c[MU] == 0;
+    const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
+    const R k0 = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
+    Cx<R> u[9];
+    load_link(a.u, MU, nb, V, u);
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+      Cx<R> psi[12], h[6], chi[6];
+      const R k = mload_hop(a.in, nb, r0 + j, V, N, psi, k0);
+      spin_project<MU, -SF>(psi, h);
+      su3_dag_mul(u, h, chi);
+      spin_reconstruct<MU, -SF>(acc[j], chi, k);
+    }
+  }
+}
+
 template <int SP>
 struct MMinBlocks {
   static constexpr int value = SP == P64 ? 2 : (SP == PDF ? 1 : 3);
 };
+
+// A thread holding KT = 2 or 4 right-hand sides keeps KT accumulators live. Its blocks have at most
+// 256 / KT threads (K * sites per block <= 256): bounds of 3 x 128 and 2 x 64 threads per SM leave up
+// to 170 and 255 registers a thread.
+template <int KT>
+struct MKtBounds {
+  static constexpr int threads = 256 / KT;
+  static constexpr int blocks = KT == 2 ? 3 : 2;
+};
+
+// KT right-hand sides per thread (FP32 / FP16 working precision): thread (sl, tl) of a block takes
+// site sl's right-hand sides blockIdx.y * K + tl * KT + j, j < KT; a block is K / KT threads per site
+// times sites per block. The norms go through the same per-right-hand-side reduction as with one
+// right-hand side per thread (values laid out as if each had its own thread).
+template <int SP, bool C12, bool DAG, int EPI, bool NORM, int KT>
+__global__ void __launch_bounds__(MKtBounds<KT>::threads, MKtBounds<KT>::blocks)
+    dslash_multi_kt_kernel(const MArgs<SP, C12> a) {
+  typedef typename MReal<SP>::type R;
+  extern __shared__ double msh[];
+  const int K = a.K, V = a.g.V, TK = K / KT;
+  const int tl = threadIdx.x % TK, sl = threadIdx.x / TK;
+  const int spb = blockDim.x / TK;
+  const int r0 = blockIdx.y * K + tl * KT;
+  bool live[KT];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    live[j] = sl < spb && (a.status == nullptr || a.status[r0 + j] == ST_RUNNING);
+    any = any || live[j];
+  }
+  double n2[KT];
+#pragma unroll
+  for (int j = 0; j < KT; ++j) n2[j] = 0.0;
+  const R mk = a.kappa_dev ? (R)(-*a.kappa_dev) : a.mkappa;
+  if (any) {
+    for (int s = blockIdx.x * spb + sl; s < V; s += gridDim.x * spb) {
+      int c[4];
+      int q = s;
+      c[0] = q % a.g.L[0];
+      q /= a.g.L[0];
+      c[1] = q % a.g.L[1];
+      q /= a.g.L[1];
+      c[2] = q % a.g.L[2];
+      c[3] = q / a.g.L[2];
+      Cx<R> acc[KT][12];
+#pragma unroll
+      for (int j = 0; j < KT; ++j) mload(a.in, s, r0 + j, V, a.N, acc[j]);
+      constexpr int SF = DAG ? +1 : -1;
+      mhop_kt<0, SF, KT>(a, mk, s, r0, c, acc);
+      mhop_kt<1, SF, KT>(a, mk, s, r0, c, acc);
+      mhop_kt<2, SF, KT>(a, mk, s, r0, c, acc);
+      mhop_kt<3, SF, KT>(a, mk, s, r0, c, acc);
+#pragma unroll
+      for (int j = 0; j < KT; ++j) {
+        if (EPI == EPI_RESID) {
+          Cx<R> bv[12];
+          mload(a.b, s, r0 + j, V, a.N, bv);
+#pragma unroll
+          for (int i = 0; i < 12; ++i) acc[j][i] = cx<R>(bv[i].re - acc[j][i].re, bv[i].im - acc[j][i].im);
+        }
+        if (live[j]) {  // converged right-hand sides were computed alongside but are not stored
+          mstore(a.out, s, r0 + j, V, a.N, acc[j]);
+          if (NORM) n2[j] += norm2_site(acc[j]);
+        }
+      }
+    }
+  }
+  if (NORM) {
+    const int nv = spb * K;
+    double* out = msh + nv;
+#pragma unroll
+    for (int j = 0; j < KT; ++j) msh[sl * K + tl * KT + j] = n2[j];
+    __syncthreads();
+    if (mreduce_sh(nv, K, a.partials, a.tickets, msh, out) && threadIdx.x < K) {
+      const int rr = blockIdx.y * K + threadIdx.x;
+      if (a.status == nullptr || a.status[rr] == ST_RUNNING) a.result[rr] = out[threadIdx.x];
+    }
+  }
+}
 
 template <int SP, bool C12, bool DAG, int EPI, bool NORM>
 __global__ void __launch_bounds__(256, MMinBlocks<SP>::value) dslash_multi_kernel(const MArgs<SP, C12> a) {
@@ -413,6 +540,21 @@ static cudaError_t mlaunch_t(const MDslashCall& c, cudaStream_t st) {
   a.result = c.result;
   const int spb = c.sites_per_block;
   dim3 grid(c.grid_x, c.nrhs / c.group);
+  const int kt = c.rhs_per_thread;
+  if constexpr (SP == P32 || SP == P16) {
+    if (kt == 2 || kt == 4) {
+      const int block = c.group / kt * spb;
+      const size_t smem = sizeof(double) * (c.group * spb + 32);
+      if (kt == 2) {
+        if (c.result) dslash_multi_kt_kernel<SP, C12, DAG, EPI, true, 2><<<grid, block, smem, st>>>(a);
+        else dslash_multi_kt_kernel<SP, C12, DAG, EPI, false, 2><<<grid, block, smem, st>>>(a);
+      } else {
+        if (c.result) dslash_multi_kt_kernel<SP, C12, DAG, EPI, true, 4><<<grid, block, smem, st>>>(a);
+        else dslash_multi_kt_kernel<SP, C12, DAG, EPI, false, 4><<<grid, block, smem, st>>>(a);
+      }
+      return cudaGetLastError();
+    }
+  }
   const int block = c.group * spb;
   const size_t smem = sizeof(double) * (block + 32);
   if (c.result)
@@ -434,6 +576,14 @@ cudaError_t launch_dslash_multi(const MDslashCall& c, cudaStream_t st) {
   if (c.nrhs < 1 || c.nrhs > kMaxRhs || c.group < 1 || c.nrhs % c.group || c.sites_per_block < 1 ||
       c.group * c.sites_per_block > 256 || c.grid_x < 1)
     return cudaErrorInvalidValue;
+  // KT right-hand sides per thread: KT divides K, the block keeps at least K threads (the reduction
+  // needs them), and only the FP32 / FP16 working precisions have the blocked kernel
+  const int kt = c.rhs_per_thread;
+  if (kt != 0 && kt != 1) {
+    if ((kt != 2 && kt != 4) || c.group % kt || c.sites_per_block < kt ||
+        (c.in.prec != SP32 && c.in.prec != SP16))
+      return cudaErrorInvalidValue;
+  }
   if (c.in.prec == SPDF) {
     if (c.u.prec != SPDF) return cudaErrorInvalidValue;
     return mlaunch_p<PDF, false>(c, st);

@@ -1,14 +1,17 @@
-// Serving runtime: a persistent request loop with continuous admission.
+// Serving runtime: a persistent request loop with continuous admission and batching.
 //
 // Requests (one single-RHS solve each, with its own lattice, kappa, tolerance, seeded gauge field
-// and source) enter a FIFO queue. The scheduler (run by whichever thread submits, waits or
-// finishes a job) admits them into execution slots as slots and device memory free up; memory is
-// charged against the budget given at creation. Every slot has its own CUDA stream and worker
-// thread, so admitted solves run concurrently and their kernels overlap on the device. A slot
-// keeps the contexts it created (links, Krylov workspace, CUDA graphs) resident between requests,
-// so a request whose volume and precision match an idle slot's resident context runs warm: no
-// allocation, no graph rebuild, only wd_set_kappa and the new fields. Least recently used
-// residents are evicted when a new volume does not fit in the budget.
+// and source) enter a queue. The scheduler (run by whichever thread submits, waits or finishes a
+// job) admits them into execution slots as slots and device memory free up; memory is charged
+// against the budget given at creation. Every slot has its own CUDA stream and worker thread, so
+// admitted work runs concurrently and its kernels overlap on the device. The oldest waiting
+// request is admitted first, together with up to max_batch - 1 later requests of the same operator
+// (lattice, precision, boundary, iteration limit) when that operator's CG loop is the persistent
+// kernel: the slot solves them with cg_solve_batch, one loop launch for all of them per pass, each
+// result bitwise the one of its solve alone. A slot keeps the contexts it created (links, Krylov
+// workspace, CUDA graphs) resident between requests, so a request whose operator matches an idle
+// slot's resident context runs warm: no allocation, no graph rebuild, only wd_set_kappa and the
+// new fields. Least recently used residents of idle slots are evicted when new ones do not fit.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -28,6 +31,8 @@
 
 namespace wdk {
 void set_last_error(const std::string& msg);
+// true when cg_solve_batch shares loop launches for this operator (its CG loop is the persistent kernel)
+bool batch_capable(const int dims[4], int precision);
 }
 
 namespace {
@@ -48,7 +53,8 @@ size_t request_bytes(const int d[4], int precision) {
   precision &= ~WD_EVEN_ODD;
   const size_t f64 = V * 192, f32 = V * 96, f16 = V * 52;
   switch (precision) {
-    case WD_PREC_F64: return extra + V * 576 + 9 * f64 + 2 * f64 + (V / 32 + 64) * 8 * 12;
+    // FP64: + two more p, r buffers of the small-volume loop
+    case WD_PREC_F64: return extra + V * 576 + 11 * f64 + 2 * f64 + (V / 32 + 64) * 8 * 12;
     case WD_PREC_F32: return extra + V * 288 + 6 * f32 + 2 * f64 + V * 12;
     // mixed: + double-float solution, residual, source (3 x 192 B) and links (576 B) per site
     case WD_PREC_MIXED_F32: return extra + V * 576 + V * 192 + 5 * f32 + 3 * f64 + 2 * f64 + V * 12 + V * 1152;
@@ -64,6 +70,7 @@ struct Job {
   wd_result res;
   bool done = false;
   size_t bytes = 0;
+  int res_idx = -1;  // the slot resident reserved for it
 };
 
 // A context kept on the device between requests, with the slot's source/solution buffers.
@@ -76,6 +83,7 @@ struct Resident {
   double* x = nullptr;
   size_t bytes = 0;
   unsigned long long last_used = 0;
+  bool taken = false;  // reserved for a job of the batch being admitted or running
 };
 
 struct Slot {
@@ -83,7 +91,7 @@ struct Slot {
   cudaStream_t stream = nullptr;
   std::vector<Resident> cache;  // resident contexts of this slot (guarded by the server mutex
                                 // while the slot is idle; owned by the slot thread while busy)
-  Job* job = nullptr;
+  std::vector<Job*> batch;      // the jobs it runs; empty = idle
   std::thread th;
 };
 
@@ -102,7 +110,14 @@ bool same_operator(const Resident& r, const wd_request& q) {
          memcmp(r.bc, bc, sizeof(bc)) == 0;
 }
 
-bool same_key(const Resident& r, const wd_request& q) { return r.ctx && same_operator(r, q); }
+// Requests that may share a batch: same operator and iteration limit.
+bool same_batch_key(const wd_request& a, const wd_request& b) {
+  int ba[4], bb[4];
+  request_bc(a, ba);
+  request_bc(b, bb);
+  return a.precision == b.precision && a.maxit == b.maxit && memcmp(a.dims, b.dims, sizeof(a.dims)) == 0 &&
+         memcmp(ba, bb, sizeof(ba)) == 0;
+}
 
 }  // namespace
 
@@ -116,6 +131,7 @@ struct wd_server {
   size_t budget = 0, used = 0;
   long long next_id = 1;
   unsigned long long tick = 0;
+  int max_batch = 8;
   bool stopping = false;
   int device = 0;
   wd_server_stats stats;
@@ -131,22 +147,18 @@ void free_resident(Resident& r) {
   r.src = r.x = nullptr;
 }
 
-// Runs on the slot thread: find the job's resident context, or create it in the placeholder the
-// scheduler reserved. Only this thread touches the slot's cache while it holds a job.
-wd_status prepare(Slot* s, const wd_request& r, Resident** out) {
-  for (auto& e : s->cache) {
-    if (same_key(e, r)) {
-      wd_status st = wd_set_kappa(e.ctx, r.kappa);
-      *out = &e;
-      return st;
-    }
-  }
-  Resident* e = nullptr;
-  for (auto& c : s->cache)
-    if (!c.ctx && same_operator(c, r)) e = &c;
-  if (!e) {
+// Runs on the slot thread: the job's reserved resident, created now if it is a placeholder. Only
+// this thread touches the slot's cache while the slot is busy.
+wd_status prepare(Slot* s, const Job* j, Resident** out) {
+  if (j->res_idx < 0 || j->res_idx >= (int)s->cache.size()) {
     wdk::set_last_error("internal: no reserved resident for the job");
     return WD_ECUDA;
+  }
+  Resident* e = &s->cache[j->res_idx];
+  const wd_request& r = j->req;
+  if (e->ctx) {
+    *out = e;
+    return wd_set_kappa(e->ctx, r.kappa);
   }
   wd_status st = wd_create(r.dims, r.kappa, r.boundary_set ? r.boundary : nullptr, r.precision, s->stream, &e->ctx);
   if (st != WD_OK) return st;
@@ -161,42 +173,82 @@ wd_status prepare(Slot* s, const wd_request& r, Resident** out) {
   return WD_OK;
 }
 
-void run_job(Slot* s, Job* j) {
-  nvtxRangePushA("wd:serve_job");
+// The slot's batch: every job's fields on its own context, then one cg_solve_batch for all of them
+// (a batch of one is the plain solve), then the solutions out.
+void run_batch(Slot* s, std::vector<Job*>& batch) {
+  nvtxRangePushA("wd:serve_batch");
   struct PopRange {
     ~PopRange() { nvtxRangePop(); }
   } pop_;
-  const wd_request& r = j->req;
-  wd_result& out = j->res;
-  memset(&out, 0, sizeof(out));
-  Resident* e = nullptr;
-  wd_status st = prepare(s, r, &e);
-  const size_t V = (size_t)volume_of(r.dims);
-  if (st == WD_OK) st = wd_generate_gauge(e->ctx, r.eps, r.gauge_seed, (r.precision & ~WD_EVEN_ODD) == WD_PREC_F64 ? 0 : 1, nullptr);
-  if (st == WD_OK) {
-    if (r.src_host) {
-      if (cudaMemcpyAsync(e->src, r.src_host, V * 192, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) st = WD_ECUDA;
-    } else {
-      st = wd_generate_source(e->ctx, r.source_seed, e->src);
+  const int n = (int)batch.size();
+  std::vector<Resident*> res(n, nullptr);
+  std::vector<wd_status> st(n, WD_OK);
+  for (int i = 0; i < n; ++i) {
+    Job* j = batch[i];
+    const wd_request& r = j->req;
+    memset(&j->res, 0, sizeof(j->res));
+    Resident* e = nullptr;
+    wd_status t = prepare(s, j, &e);
+    const size_t V = (size_t)volume_of(r.dims);
+    if (t == WD_OK)
+      t = wd_generate_gauge(e->ctx, r.eps, r.gauge_seed, (r.precision & ~WD_EVEN_ODD) == WD_PREC_F64 ? 0 : 1, nullptr);
+    if (t == WD_OK) {
+      if (r.src_host) {
+        if (cudaMemcpyAsync(e->src, r.src_host, V * 192, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) t = WD_ECUDA;
+      } else {
+        t = wd_generate_source(e->ctx, r.source_seed, e->src);
+      }
     }
+    if (t == WD_OK && cudaMemsetAsync(e->x, 0, V * 192, s->stream) != cudaSuccess) t = WD_ECUDA;
+    res[i] = e;
+    st[i] = t;
   }
-  if (st == WD_OK && cudaMemsetAsync(e->x, 0, V * 192, s->stream) != cudaSuccess) st = WD_ECUDA;
-  int iters = 0;
-  double res = 0.0;
-  if (st == WD_OK) st = cg_solve(e->ctx, e->src, e->x, r.tol, r.maxit, &iters, &res);
-  if ((st == WD_OK || st == WD_NOT_CONVERGED) && r.x_host) {
-    if (cudaMemcpyAsync(r.x_host, e->x, V * 192, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
-        cudaStreamSynchronize(s->stream) != cudaSuccess)
-      st = WD_ECUDA;
+  std::vector<wd_ctx*> ctxs;
+  std::vector<const void*> srcs;
+  std::vector<void*> xs;
+  std::vector<double> tols;
+  std::vector<int> idx;
+  for (int i = 0; i < n; ++i)
+    if (st[i] == WD_OK) {
+      ctxs.push_back(res[i]->ctx);
+      srcs.push_back(res[i]->src);
+      xs.push_back(res[i]->x);
+      tols.push_back(batch[i]->req.tol);
+      idx.push_back(i);
+    }
+  const int m = (int)ctxs.size();
+  std::vector<int> iters(m, 0), sts(m, WD_OK);
+  std::vector<double> rel(m, 0.0);
+  if (m > 0) {
+    const wd_status all = cg_solve_batch(ctxs.data(), m, srcs.data(), xs.data(), tols.data(), batch[idx[0]]->req.maxit,
+                                         iters.data(), rel.data(), sts.data());
+    if (all != WD_OK && all != WD_NOT_CONVERGED && all != WD_BREAKDOWN)
+      for (int k = 0; k < m; ++k) sts[k] = (int)all;  // an argument or device failure of the whole batch
   }
-  wd_stats ws;
-  memset(&ws, 0, sizeof(ws));
-  if (e && e->ctx) wd_get_stats(e->ctx, &ws);
-  out.status = st;
-  out.iterations = iters;
-  out.reliable_updates = ws.reliable_updates;
-  out.true_rel_residual = res;
-  out.slot = s->index;
+  for (int k = 0; k < m; ++k) {
+    const int i = idx[k];
+    st[i] = (wd_status)sts[k];
+    Job* j = batch[i];
+    const wd_request& r = j->req;
+    const size_t V = (size_t)volume_of(r.dims);
+    if ((st[i] == WD_OK || st[i] == WD_NOT_CONVERGED) && r.x_host) {
+      if (cudaMemcpyAsync(r.x_host, res[i]->x, V * 192, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+          cudaStreamSynchronize(s->stream) != cudaSuccess)
+        st[i] = WD_ECUDA;
+    }
+    j->res.iterations = iters[k];
+    j->res.true_rel_residual = rel[k];
+  }
+  for (int i = 0; i < n; ++i) {
+    Job* j = batch[i];
+    wd_stats ws;
+    memset(&ws, 0, sizeof(ws));
+    if (res[i] && res[i]->ctx) wd_get_stats(res[i]->ctx, &ws);
+    j->res.status = st[i];
+    j->res.reliable_updates = ws.reliable_updates;
+    j->res.slot = s->index;
+    j->res.batch = n;
+  }
 }
 
 void schedule(wd_server* srv);
@@ -205,26 +257,36 @@ void slot_main(wd_server* srv, Slot* s) {
   cudaSetDevice(srv->device);
   std::unique_lock<std::mutex> lk(srv->mu);
   for (;;) {
-    srv->cv_work.wait(lk, [&] { return srv->stopping || s->job != nullptr; });
-    if (s->job == nullptr && srv->stopping) break;
-    Job* j = s->job;
+    srv->cv_work.wait(lk, [&] { return srv->stopping || !s->batch.empty(); });
+    if (s->batch.empty() && srv->stopping) break;
+    std::vector<Job*> batch = s->batch;
     lk.unlock();
-    j->t_start = Clock::now();
-    run_job(s, j);
-    j->t_done = Clock::now();
+    const Clock::time_point t0 = Clock::now();
+    for (Job* j : batch) j->t_start = t0;
+    run_batch(s, batch);
+    const Clock::time_point t1 = Clock::now();
     lk.lock();
-    j->res.queue_ms = ms_between(j->t_submit, j->t_start);
-    j->res.solve_ms = ms_between(j->t_start, j->t_done);
-    j->res.latency_ms = ms_between(j->t_submit, j->t_done);
-    j->done = true;
-    if (j->res.status != WD_OK) srv->stats.failed += 1;
+    for (Job* j : batch) {
+      j->t_done = t1;
+      j->res.queue_ms = ms_between(j->t_submit, j->t_start);
+      j->res.solve_ms = ms_between(j->t_start, j->t_done);
+      j->res.latency_ms = ms_between(j->t_submit, j->t_done);
+      j->done = true;
+      if (j->res.status != WD_OK) srv->stats.failed += 1;
+      srv->stats.completed += 1;
+    }
+    if (batch.size() > 1) {
+      srv->stats.batches += 1;
+      srv->stats.batched_requests += (long long)batch.size();
+    }
     // a context whose creation failed holds nothing: drop it and its charge
-    for (auto& e : s->cache)
+    for (auto& e : s->cache) {
+      e.taken = false;
       if (!e.ctx) srv->used -= e.bytes;
+    }
     s->cache.erase(std::remove_if(s->cache.begin(), s->cache.end(), [](const Resident& e) { return e.ctx == nullptr; }),
                    s->cache.end());
-    s->job = nullptr;
-    srv->stats.completed += 1;
+    s->batch.clear();
     schedule(srv);  // admit waiting requests into the freed slot
     srv->cv_done.notify_all();
   }
@@ -233,75 +295,110 @@ void slot_main(wd_server* srv, Slot* s) {
   s->cache.clear();
 }
 
-// Assign pending jobs to idle slots (called with the mutex held), in FIFO order.
-// 1) An idle slot with a resident context of the request's volume and precision (warm).
-// 2) Else the idle slot holding the fewest resident bytes gets a new context, after the least
-//    recently used residents of idle slots are freed until the request fits in the budget. Only
-//    idle slots' residents are freed (here, under the lock: an idle slot's thread does not touch
-//    its cache), so device memory never exceeds what is charged.
+size_t slot_bytes(const Slot* s) {
+  size_t b = 0;
+  for (const auto& e : s->cache) b += e.bytes;
+  return b;
+}
+
+// Assign pending jobs to idle slots (called with the mutex held).
+// The oldest pending job goes first, with up to max_batch - 1 later jobs of the same operator when
+// its CG loop is the persistent kernel (a batch shares its loop launches); other jobs keep their
+// order. The slot: an idle one with resident contexts of the operator (the most of them), else the
+// idle slot holding the fewest resident bytes. Jobs without an idle resident get a placeholder
+// charged against the budget, after the least recently used residents of idle slots are freed until
+// they fit (the batch shrinks to what fits). Only idle slots' residents are freed (here, under the
+// lock: an idle slot's thread does not touch its cache), so device memory never exceeds what is
+// charged.
 void schedule(wd_server* srv) {
   while (!srv->pending.empty()) {
     Job* j = srv->pending.front();
     Slot* pick = nullptr;
-    Resident* warm = nullptr;
+    int pick_warm = 0;
     for (auto& sp : srv->slots) {
-      if (sp->job) continue;
+      if (!sp->batch.empty()) continue;
+      int w = 0;
       for (auto& e : sp->cache)
-        if (same_key(e, j->req)) {
-          pick = sp.get();
-          warm = &e;
-          break;
-        }
-      if (pick) break;
+        if (e.ctx && same_operator(e, j->req)) ++w;
+      if (w > pick_warm) {
+        pick = sp.get();
+        pick_warm = w;
+      }
     }
-    if (pick) {
-      srv->stats.warm_hits += 1;
-      warm->last_used = ++srv->tick;
-    } else {
-      size_t idle_bytes = 0;
+    if (!pick) {
       for (auto& sp : srv->slots) {
-        if (sp->job) continue;
-        size_t b = 0;
-        for (auto& e : sp->cache) b += e.bytes;
-        idle_bytes += b;
-        if (!pick) {
-          pick = sp.get();
-        } else {
-          size_t pb = 0;
-          for (auto& e : pick->cache) pb += e.bytes;
-          if (b < pb) pick = sp.get();
-        }
+        if (!sp->batch.empty()) continue;
+        if (!pick || slot_bytes(sp.get()) < slot_bytes(pick)) pick = sp.get();
       }
-      if (!pick || srv->used - idle_bytes + j->bytes > srv->budget) break;  // wait for a slot or memory
-      while (srv->used + j->bytes > srv->budget) {
-        Slot* vs = nullptr;
-        size_t vi = 0;
-        for (auto& sp : srv->slots) {
-          if (sp->job) continue;
-          for (size_t i = 0; i < sp->cache.size(); ++i)
-            if (!vs || sp->cache[i].last_used < vs->cache[vi].last_used) {
-              vs = sp.get();
-              vi = i;
-            }
-        }
-        if (!vs) break;
-        srv->used -= vs->cache[vi].bytes;
-        free_resident(vs->cache[vi]);
-        vs->cache.erase(vs->cache.begin() + vi);
-        srv->stats.evictions += 1;
+    }
+    if (!pick) break;  // every slot busy
+    // the batch: j and later jobs of its operator, up to max_batch
+    std::vector<Job*> members{j};
+    if (srv->max_batch > 1 && wdk::batch_capable(j->req.dims, j->req.precision)) {
+      for (size_t i = 1; i < srv->pending.size() && (int)members.size() < srv->max_batch; ++i)
+        if (same_batch_key(srv->pending[i]->req, j->req)) members.push_back(srv->pending[i]);
+    }
+    // residents: warm ones of the slot first, then placeholders charged against the budget
+    std::vector<int> slots_idx;
+    for (size_t i = 0; i < pick->cache.size() && slots_idx.size() < members.size(); ++i) {
+      Resident& e = pick->cache[i];
+      if (e.ctx && !e.taken && same_operator(e, j->req)) {
+        e.taken = true;
+        slots_idx.push_back((int)i);
       }
+    }
+    size_t evictable = 0;
+    for (auto& sp : srv->slots) {
+      if (!sp->batch.empty()) continue;
+      for (auto& e : sp->cache)
+        if (!e.taken) evictable += e.bytes;
+    }
+    size_t fresh_n = members.size() - slots_idx.size();
+    while (fresh_n > 0 && srv->used - evictable + fresh_n * j->bytes > srv->budget) --fresh_n;
+    if (slots_idx.empty() && fresh_n == 0) {  // not even the oldest job fits yet: wait for memory
+      for (int i : slots_idx) pick->cache[i].taken = false;
+      break;
+    }
+    members.resize(slots_idx.size() + fresh_n);
+    while (srv->used + fresh_n * j->bytes > srv->budget) {
+      Slot* vs = nullptr;
+      size_t vi = 0;
+      for (auto& sp : srv->slots) {
+        if (!sp->batch.empty()) continue;
+        for (size_t i = 0; i < sp->cache.size(); ++i)
+          if (!sp->cache[i].taken && (!vs || sp->cache[i].last_used < vs->cache[vi].last_used)) {
+            vs = sp.get();
+            vi = i;
+          }
+      }
+      if (!vs) break;
+      srv->used -= vs->cache[vi].bytes;
+      free_resident(vs->cache[vi]);
+      vs->cache.erase(vs->cache.begin() + vi);
+      if (vs == pick)  // indices of the slot's reserved residents shift past the erased one
+        for (int& k : slots_idx)
+          if (k > (int)vi) --k;
+      srv->stats.evictions += 1;
+    }
+    srv->stats.warm_hits += (long long)slots_idx.size();
+    for (size_t f = 0; f < fresh_n; ++f) {
       Resident fresh;
       memcpy(fresh.dims, j->req.dims, sizeof(fresh.dims));
       request_bc(j->req, fresh.bc);
       fresh.precision = j->req.precision;
       fresh.bytes = j->bytes;
-      fresh.last_used = ++srv->tick;
+      fresh.taken = true;
       pick->cache.push_back(fresh);
+      slots_idx.push_back((int)pick->cache.size() - 1);
       srv->used += j->bytes;
     }
-    srv->pending.pop_front();
-    pick->job = j;
-    srv->stats.admitted += 1;
+    for (size_t k = 0; k < members.size(); ++k) {
+      members[k]->res_idx = slots_idx[k];
+      pick->cache[slots_idx[k]].last_used = ++srv->tick;
+    }
+    for (Job* m : members) srv->pending.erase(std::find(srv->pending.begin(), srv->pending.end(), m));
+    pick->batch = members;
+    srv->stats.admitted += (long long)members.size();
   }
   if ((double)srv->used > srv->stats.peak_bytes) srv->stats.peak_bytes = (double)srv->used;
   srv->cv_work.notify_all();
@@ -427,6 +524,16 @@ wd_status wd_server_poll(wd_server* srv, long long id, wd_result* out, int* done
     *out = it->second->res;
     srv->jobs.erase(it);
   }
+  return WD_OK;
+}
+
+wd_status wd_server_set_max_batch(wd_server* srv, int max_batch) {
+  if (!srv || max_batch < 1 || max_batch > 16) {
+    wdk::set_last_error("null server or max_batch outside [1, 16]");
+    return WD_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->max_batch = max_batch;
   return WD_OK;
 }
 

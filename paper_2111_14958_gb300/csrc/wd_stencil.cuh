@@ -370,6 +370,293 @@ __device__ __forceinline__ double pair_sites(const DslashArgs<P64, C12>& a) {
   return n2;
 }
 
+// ---------------------------------------------------------------- FP64: L = 4, 8 or 16 lanes per site
+//
+// The FP64 pipe of GB300 retires about half a lane-operation per clock per SM sub-partition, so a
+// warp's FP64 instruction stream advances one instruction every ~64 cycles and a site's ~850 FP64
+// instructions on one thread take ~26 us. At the paper's small volumes (4^4: 256 sites, 8^4: 4,096)
+// there are too few warps to occupy the 608 sub-partitions, and the time is that chain. Here L
+// consecutive lanes share a site: with L = 4 a lane takes both hops of one direction mu; with L = 8
+// one hop; with L = 16 one hop and one of the two rows of its half-spinor. Every lane runs the same
+// instructions: the hop's direction, projector, dagger and boundary sign enter as runtime selects
+// and sign-bit flips (integer operations), never as branches. Each lane accumulates the
+// reconstructed spinor of its hops (24 reals, lower spins in a per-lane order made canonical by
+// selects); the site's lanes then reduce-scatter the 24 reals with shuffles, so each lane ends with
+// 24 / L of them (with L = 16 the two lanes of a row pair hold the same 3 and one stores), and only
+// then apply out = in - kappa * sum (one FMA per real) and the norm. FP64 instructions per lane:
+// L = 4: 2 x (12 + 72) + 18 + 6 + 6; L = 8: 84 + 21 + 3 + 3; L = 16: 42 + 24 + 3 + 3.
+
+// bits of a double's high word
+__device__ __forceinline__ double neg_if(double x, bool n) {
+  return __hiloint2double(__double2hiint(x) ^ (n ? (int)0x80000000 : 0), __double2loint(x));
+}
+
+// z * i^e for a runtime e, by selects and sign flips only
+__device__ __forceinline__ Cx<double> ipow_rt(Cx<double> z, int e) {
+  const bool sw = e & 1;
+  const double re = sw ? z.im : z.re, im = sw ? z.re : z.im;
+  const int m = e & 3;
+  return cx(neg_if(re, m == 1 || m == 2), neg_if(im, m == 2 || m == 3));
+}
+
+template <int L>
+struct LaneShape {
+  static_assert(L == 4 || L == 8 || L == 16, "lanes per site");
+  static constexpr int kHops = L == 4 ? 2 : 1;       // hops per lane
+  static constexpr int kRows = L == 16 ? 1 : 2;      // half-spinor rows per hop
+  static constexpr int kLevels = L == 4 ? 2 : 3;     // reduce-scatter levels (24 -> 24 >> levels reals)
+  static constexpr int kOwn = 24 >> kLevels;         // reals a lane owns after the reduce-scatter
+};
+
+// The spinor field a lane hop reads: a single field, or (HASB) w = A + c B formed on the fly at
+// every neighbour (the fused CG iteration of the persistent loop reads p = s + beta p and
+// r = r - alpha q this way). fma(c, B, A) is the exact arithmetic of the vector updates. NC selects
+// the read-only (non-coherent) load path, valid only for fields no thread writes during the launch;
+// the persistent loop, which rewrites its fields between grid barriers, uses plain loads.
+template <bool HASB, bool NC>
+struct LaneSrc {
+  const double2* A;
+  const double2* B;
+  double c;
+  __device__ __forceinline__ double2 ld(const double2* p) const { return NC ? __ldg(p) : *p; }
+  __device__ __forceinline__ double2 get(size_t i) const {
+    const double2 a = ld(A + i);
+    if (!HASB) return a;
+    const double2 b = ld(B + i);
+    return make_double2(fma(c, b.x, a.x), fma(c, b.y, a.y));
+  }
+};
+
+// One hop (mu, dir) of lane rows [r0, r0 + nrows) into the lane accumulator: up[r] (3 complex) for
+// upper spin r, lo[r] (3 complex) for the lower spin paired with row r (spin 2 + bcol(mu, r)). The
+// first hop of a lane assigns (ACC = false): adding to zero would cost an FP64 add per real.
+template <int NROWS, int SF, bool ACC, typename Src>
+__device__ __forceinline__ void lane_hop(const Geom& g, const GaugeRef<double, false>& gauge, const Src& in, int s,
+                                         const int (&c)[4], int mu, int dir, int r0, Cx<double> (&up)[2][3],
+                                         Cx<double> (&lo)[2][3]) {
+  const int V = g.V;
+  const int L = g.L[mu], st = g.stride[mu];
+  const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+  const bool wrap = dir == 0 ? cm == L - 1 : cm == 0;
+  const int nb = dir == 0 ? (wrap ? s - (L - 1) * st : s + st) : (wrap ? s + (L - 1) * st : s - st);
+  const bool flip = wrap && g.bc[mu] < 0;  // boundary phase -1, applied to the projected spinor
+  const int S = dir == 0 ? SF : -SF;       // projector (1 + S gamma_mu)
+  // link U_mu(s) (forward) or U_mu(nb)^dagger (backward)
+  Cx<double> u[9];
+  load_link(gauge, mu, dir == 0 ? s : nb, V, u);
+  Cx<double> ue[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const Cx<double> t = u[3 * j + i];
+      ue[3 * i + j] = dir == 0 ? u[3 * i + j] : cx(t.re, -t.im);
+    }
+#pragma unroll
+  for (int k = 0; k < NROWS; ++k) {
+    const int r = r0 + k;
+    const int col = bcol(mu, r);
+    const int e = bph(mu, r) + (S < 0 ? 2 : 0);  // h_r = psi_r + S B[r][col] psi_{2+col}
+    Cx<double> h[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const double2 pu = in.get((size_t)(3 * r + cc) * V + nb);
+      const double2 pl = in.get((size_t)(3 * (2 + col) + cc) * V + nb);
+      const Cx<double> l = ipow_rt(cx(pl.x, pl.y), e);
+      h[cc] = cx(neg_if(pu.x + l.re, flip), neg_if(pu.y + l.im, flip));
+    }
+    // chi = ue h; upper spin r += chi; lower spin 2 + col += S conj(B[r][col]) chi
+    const int el = (4 - bph(mu, r)) + (S < 0 ? 2 : 0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const Cx<double> u0 = ue[3 * i], u1 = ue[3 * i + 1], u2 = ue[3 * i + 2];
+      double re = u0.re * h[0].re;
+      re = fma(-u0.im, h[0].im, re);
+      re = fma(u1.re, h[1].re, re);
+      re = fma(-u1.im, h[1].im, re);
+      re = fma(u2.re, h[2].re, re);
+      re = fma(-u2.im, h[2].im, re);
+      double im = u0.re * h[0].im;
+      im = fma(u0.im, h[0].re, im);
+      im = fma(u1.re, h[1].im, im);
+      im = fma(u1.im, h[1].re, im);
+      im = fma(u2.re, h[2].im, im);
+      im = fma(u2.im, h[2].re, im);
+      const Cx<double> t = ipow_rt(cx(re, im), el);
+      if (ACC) {
+        up[k][i] = cx(up[k][i].re + re, up[k][i].im + im);
+        lo[k][i] = cx(lo[k][i].re + t.re, lo[k][i].im + t.im);
+      } else {
+        up[k][i] = cx(re, im);
+        lo[k][i] = t;
+      }
+    }
+  }
+}
+
+// The hopping sum of one site for this lane's share: on return v[0 .. kOwn) holds the lane's owned
+// reals j = base + i of sum_hops (projector, link and boundary phase applied; -kappa not yet), with
+// j = 2 (3 spin + colour) + (0 re, 1 im). All L lanes of the site must call it together.
+template <int L, bool DAG, typename Src>
+__device__ __forceinline__ void lanes_hopsum(const Geom& g, const GaugeRef<double, false>& gauge, const Src& in, int s,
+                                             int lane, double (&v)[24], int& base) {
+  typedef LaneShape<L> Sh;
+  constexpr int SF = DAG ? +1 : -1;
+  int c[4];
+  {
+    int r = s;
+    c[0] = r % g.L[0];
+    r /= g.L[0];
+    c[1] = r % g.L[1];
+    r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+  }
+  // the lane's hops all share one direction mu
+  const int mu = L == 4 ? lane : (L == 8 ? lane >> 1 : lane >> 2);
+  const int r0 = L == 16 ? (lane & 1) : 0;
+  Cx<double> up[2][3], lo[2][3];
+  if (L == 4) {  // both hops of direction mu
+    lane_hop<Sh::kRows, SF, false>(g, gauge, in, s, c, mu, 0, r0, up, lo);
+    lane_hop<Sh::kRows, SF, true>(g, gauge, in, s, c, mu, 1, r0, up, lo);
+  } else {
+    const int dir = L == 8 ? (lane & 1) : ((lane >> 1) & 1);
+    lane_hop<Sh::kRows, SF, false>(g, gauge, in, s, c, mu, dir, r0, up, lo);
+  }
+  // canonical order. Row r's upper spin is r; its lower spin is 2 + bcol(mu, r) = 2 + (r ^ (mu < 2)).
+  const bool swp = mu < 2;
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Cx<double> z;
+      if (Sh::kRows == 2) {
+        if (sp < 2) z = up[sp][i];
+        else z = ((sp - 2) ^ (int)swp) ? lo[1][i] : lo[0][i];
+      } else {  // one row r0: upper spin r0 and lower spin 2 + (r0 ^ swp); zero elsewhere
+        const bool here = sp < 2 ? sp == r0 : (sp - 2) == (r0 ^ (int)swp);
+        const Cx<double> src = sp < 2 ? up[0][i] : lo[0][i];
+        z = here ? src : cx(0.0, 0.0);
+      }
+      v[2 * (3 * sp + i)] = z.re;
+      v[2 * (3 * sp + i) + 1] = z.im;
+    }
+  // reduce-scatter over the site's lanes: at each level keep the half selected by one lane bit
+  base = 0;
+#pragma unroll
+  for (int lev = 0; lev < Sh::kLevels; ++lev) {
+    const int half = 12 >> lev;
+    const int m = (L >> 1) >> lev;  // lane bit of this level (highest first)
+    const bool hi = lane & m;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double send = hi ? v[i] : v[i + half];
+      const double keep = hi ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+    base += hi ? half : 0;
+  }
+  if (L == 16) {  // lanes 2i and 2i + 1 hold the same reals: sum them
+#pragma unroll
+    for (int i = 0; i < Sh::kOwn; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 1);
+  }
+}
+
+// flat double index of real j of site s in the [12][V] double2 layout
+__device__ __forceinline__ size_t real_index(int j, int s, int V) { return ((size_t)(j >> 1) * V + s) * 2 + (j & 1); }
+
+// All sites of out = D in (or b - D in) with L lanes per site over the whole grid (grid-stride on
+// the warp's first site, so all 32 lanes take the same trips and meet at the shuffles); returns this
+// thread's share of |out|^2.
+template <int L, bool DAG, int EPI>
+__device__ __forceinline__ double lanes_sites(const DslashArgs<P64, false>& a) {
+  typedef LaneShape<L> Sh;
+  const int V = a.g.V;
+  const int lane = threadIdx.x & (L - 1);
+  double n2 = 0.0;
+  const int step = (gridDim.x * blockDim.x) / L;
+  LaneSrc<false, true> src;
+  src.A = a.in.p;
+  src.B = nullptr;
+  src.c = 0.0;
+  for (int s0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / L; s0 < V; s0 += step) {
+    const int sl = s0 + (threadIdx.x & 31) / L;
+    const bool live = sl < V;
+    const int s = live ? sl : s0;
+    double v[24];
+    int base;
+    lanes_hopsum<L, DAG>(a.g, a.u, src, s, lane, v, base);
+    if (!live || (L == 16 && (lane & 1))) continue;
+    const double mk = a.kappa_dev ? -*a.kappa_dev : a.mkappa;
+    const double* in = reinterpret_cast<const double*>(a.in.p);
+    double* out = reinterpret_cast<double*>(a.out.p);
+#pragma unroll
+    for (int i = 0; i < Sh::kOwn; ++i) {
+      const size_t idx = real_index(base + i, s, V);
+      double o = fma(mk, v[i], __ldg(in + idx));
+      if (EPI == EPI_RESID) o = __ldg(reinterpret_cast<const double*>(a.b.p) + idx) - o;
+      out[idx] = o;
+      n2 = fma(o, o, n2);
+    }
+  }
+  return n2;
+}
+
+// One pass of the fused CG iteration with L lanes per site (persistent FP64 loop at small volumes):
+// w = A + c B formed at every neighbour and at the site itself (w = A without B), out = D w (or
+// D^dag w); the site's w is also stored to wout (if set) and x += ax * xs at the site (if x is set).
+// Returns this thread's shares of |out|^2 and |w|^2.
+struct FusedPass {
+  const double2* A;
+  const double2* B;
+  double c;
+  double2* wout;
+  double2* out;
+  double2* x;
+  const double2* xs;
+  double ax;
+};
+
+template <int L, bool DAG, bool HASB>
+__device__ __forceinline__ void lanes_fused_sites(const Geom& g, const GaugeRef<double, false>& gauge, double mk,
+                                                  const FusedPass& f, double& n_out, double& n_w) {
+  typedef LaneShape<L> Sh;
+  const int V = g.V;
+  const int lane = threadIdx.x & (L - 1);
+  const int step = (gridDim.x * blockDim.x) / L;
+  LaneSrc<HASB, false> src;
+  src.A = f.A;
+  src.B = f.B;
+  src.c = f.c;
+  const double* A = reinterpret_cast<const double*>(f.A);
+  const double* B = reinterpret_cast<const double*>(f.B);
+  double* wout = reinterpret_cast<double*>(f.wout);
+  double* out = reinterpret_cast<double*>(f.out);
+  double* x = reinterpret_cast<double*>(f.x);
+  const double* xs = reinterpret_cast<const double*>(f.xs);
+  for (int s0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / L; s0 < V; s0 += step) {
+    const int sl = s0 + (threadIdx.x & 31) / L;
+    const bool live = sl < V;
+    const int s = live ? sl : s0;
+    double v[24];
+    int base;
+    lanes_hopsum<L, DAG>(g, gauge, src, s, lane, v, base);
+    if (!live || (L == 16 && (lane & 1))) continue;
+#pragma unroll
+    for (int i = 0; i < Sh::kOwn; ++i) {
+      const size_t idx = real_index(base + i, s, V);
+      double w = A[idx];
+      if (HASB) w = fma(f.c, B[idx], w);
+      if (wout) wout[idx] = w;
+      const double o = fma(mk, v[i], w);
+      out[idx] = o;
+      if (x) x[idx] = fma(f.ax, xs[idx], x[idx]);
+      n_out = fma(o, o, n_out);
+      n_w = fma(w, w, n_w);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- even-odd (Schur) hopping
 //
 // With all extents even, sites split into parities p = (x + y + z + t) mod 2 and the hopping term

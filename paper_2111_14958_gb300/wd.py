@@ -58,12 +58,14 @@ WD_OPT_DSLASH_VARIANT = 11
 WD_OPT_LOOP_WAIT_LIMIT = 12
 WD_OPT_RESIDUAL_HISTORY = 13
 WD_OPT_APPLY_INNER = 14
+WD_OPT_MULTI_RHS_PER_THREAD = 15
 
 
 class WdMultiStats(ctypes.Structure):
     _fields_ = [("nrhs", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("group", ctypes.c_int), ("sites_per_block", ctypes.c_int),
-                ("status", ctypes.c_int), ("solve_ms", ctypes.c_double), ("dslash_ms", ctypes.c_double)]
+                ("status", ctypes.c_int), ("rhs_per_thread", ctypes.c_int), ("solve_ms", ctypes.c_double),
+                ("dslash_ms", ctypes.c_double)]
 
 
 class WdRequest(ctypes.Structure):
@@ -77,21 +79,22 @@ class WdRequest(ctypes.Structure):
 class WdResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
                 ("slot", ctypes.c_int), ("true_rel_residual", ctypes.c_double), ("queue_ms", ctypes.c_double),
-                ("solve_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("solve_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("batch", ctypes.c_int)]
 
 
 class WdServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
                 ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
                 ("warm_hits", ctypes.c_longlong), ("evictions", ctypes.c_longlong), ("pending", ctypes.c_int),
-                ("used_bytes", ctypes.c_double), ("peak_bytes", ctypes.c_double)]
+                ("used_bytes", ctypes.c_double), ("peak_bytes", ctypes.c_double),
+                ("batches", ctypes.c_longlong), ("batched_requests", ctypes.c_longlong)]
 
 
 class WdStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
                 ("dslash_calls_f64", ctypes.c_int), ("status", ctypes.c_int),
-                ("loop_mode", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("loop_mode", ctypes.c_int), ("loop_lanes", ctypes.c_int),
                 ("true_rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("loop_ms", ctypes.c_double)]
 
@@ -106,6 +109,8 @@ _sig = {
     "wd_load_gauge": (_I, [_P, _P, _I, _I, ctypes.POINTER(_D)]),
     "wd_apply": (_I, [_P, _P, _P, _I]),
     "cg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "cg_solve_batch": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_D), _I,
+                            ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "wd_set_option": (_I, [_P, _I, _D]),
     "wd_get_stats": (_I, [_P, ctypes.POINTER(WdStats)]),
     "wd_get_residual_history": (_I, [_P, ctypes.POINTER(_D), _I, ctypes.POINTER(_I)]),
@@ -124,6 +129,7 @@ _sig = {
     "wd_server_wait": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(WdResult)]),
     "wd_server_poll": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(WdResult), ctypes.POINTER(_I)]),
     "wd_server_get_stats": (_I, [_P, ctypes.POINTER(WdServerStats)]),
+    "wd_server_set_max_batch": (_I, [_P, _I]),
     "wd_server_destroy": (None, [_P]),
     "wd_last_error": (ctypes.c_char_p, []),
     "wd_version": (ctypes.c_char_p, []),
@@ -209,6 +215,26 @@ def cg_solve(ctx, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
                        ctypes.byref(res))
     _check(st, "cg_solve", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
     return st, it.value, res.value
+
+
+def cg_solve_batch(ctxs, srcs, xs, tols, maxit: int):
+    """n independent solves, each bitwise as cg_solve alone (one loop launch per pass where they share
+    a shape). Returns (status, iterations, true relative residuals, per-problem statuses); the x
+    tensors are updated in place."""
+    n = len(ctxs)
+    if not (len(srcs) == len(xs) == len(tols) == n):
+        raise ValueError("ctxs, srcs, xs and tols must have the same length")
+    for t in list(srcs) + list(xs):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("sources and solutions must be contiguous complex128 CUDA tensors")
+    c = (_P * n)(*[_P(v) for v in ctxs])
+    sp = (_P * n)(*[_P(_ptr(t)) for t in srcs])
+    xp = (_P * n)(*[_P(_ptr(t)) for t in xs])
+    tl = (_D * n)(*[float(t) for t in tols])
+    it, res, sts = (_I * n)(), (_D * n)(), (_I * n)()
+    st = _lib.cg_solve_batch(c, n, sp, xp, tl, int(maxit), it, res, sts)
+    _check(st, "cg_solve_batch", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
+    return st, list(it), list(res), list(sts)
 
 
 def wd_generate_gauge(ctx, eps: float, seed: int, compress12: bool = False, U_out: torch.Tensor = None) -> None:
@@ -419,11 +445,16 @@ def _struct_dict(obj):
 class Server:
     """Persistent solve server (wd_server_*): continuous admission of single-RHS requests."""
 
-    def __init__(self, budget_bytes: float, slots: int = 4):
+    def __init__(self, budget_bytes: float, slots: int = 4, max_batch: int = None):
         h = _P()
         _check(_lib.wd_server_create(float(budget_bytes), int(slots), ctypes.byref(h)), "wd_server_create")
         self.h = h.value
         self._keep = {}
+        if max_batch is not None:
+            self.set_max_batch(max_batch)
+
+    def set_max_batch(self, max_batch: int):
+        _check(_lib.wd_server_set_max_batch(_P(self.h), int(max_batch)), "wd_server_set_max_batch")
 
     def submit(self, dims, kappa, eps, gauge_seed, source_seed, tol, precision=WD_PREC_MIXED_F32, maxit=20000,
                boundary=None, src_host: torch.Tensor = None, x_host: torch.Tensor = None) -> int:

@@ -183,3 +183,74 @@ def test_solve_multi_mixed_with_fp64_updates():
         for r in range(3):
             assert ocg.true_residual(U, eta[r], x[r], 0.124) <= 1e-10
         op.close()
+
+
+# ---------------------------------------------------------------- several right-hand sides per thread
+
+@pytest.mark.parametrize("prec", ["f32", "f32c12", "f16_inner"])
+@pytest.mark.parametrize("kt", [2, 4])
+def test_rhs_per_thread_matches_one_per_thread_and_the_oracle(prec, kt):
+    """KT right-hand sides per thread share each link load; the arithmetic per right-hand side is
+    that of one per thread, so the outputs agree bit for bit, and with the oracle within the
+    working-precision bound."""
+    wd = require_gpu()
+    dims = (6, 5, 4, 8)
+    n = 12
+    U = synthetic.gauge_field(dims, 0.4, 1)
+    psi = _sources(dims, n)
+    p, c12 = {"f32": (wd.WD_PREC_F32, False), "f32c12": (wd.WD_PREC_F32, True),
+              "f16_inner": (wd.WD_PREC_MIXED_F16, True)}[prec]
+    op = wd.WilsonDirac(dims, 0.12, BC, p)
+    op.load_gauge(to_dev(U), compress12=c12)
+    if p == wd.WD_PREC_MIXED_F16:
+        op.set_option(wd.WD_OPT_APPLY_INNER, 1)
+    out = {}
+    for k in (1, kt):
+        op.set_option(wd.WD_OPT_MULTI_RHS_PER_THREAD, k)
+        op.set_option(wd.WD_OPT_MULTI_GROUP, 12)
+        op.set_option(wd.WD_OPT_MULTI_SITES, 8)
+        for dagger in (False, True):
+            out[(k, dagger)] = to_np(op.apply_multi(to_dev(psi), dagger=dagger))
+        assert op.multi_stats()["rhs_per_thread"] == k
+    op.close()
+    for dagger in (False, True):
+        assert np.array_equal(out[(1, dagger)], out[(kt, dagger)]), dagger
+        for r in range(n):
+            ref = wilson.apply_D(U, psi[r].astype(np.complex64).astype(np.complex128), 0.12, BC, dagger)
+            bound = 1e-6 if prec != "f16_inner" else 2.0 ** -9
+            assert rel(out[(kt, dagger)][r], ref) < bound, (r, dagger)
+
+
+@pytest.mark.parametrize("kt", [2, 4])
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_f16", "f32"])
+def test_multi_solve_with_rhs_per_thread(kt, prec):
+    wd = require_gpu()
+    dims = (6, 4, 4, 8)
+    n = 8
+    U = synthetic.gauge_field(dims, 0.4, 1)
+    eta = _sources(dims, n, seed0=40)
+    p, tol = {"mixed_f32": (wd.WD_PREC_MIXED_F32, 1e-10), "mixed_f16": (wd.WD_PREC_MIXED_F16, 1e-10),
+              "f32": (wd.WD_PREC_F32, 1e-6)}[prec]
+    op = wd.WilsonDirac(dims, 0.12, BC, p)
+    op.load_gauge(to_dev(U), compress12=True)
+    op.set_option(wd.WD_OPT_MULTI_RHS_PER_THREAD, kt)
+    x, iters, res, st = op.solve_multi(to_dev(eta), tol=tol, maxit=4000)
+    s = op.multi_stats()
+    op.close()
+    assert st == wd.WD_OK and s["rhs_per_thread"] == kt
+    xs = to_np(x)
+    for r in range(n):
+        true = ocg.true_residual(U, eta[r], xs[r], 0.12)
+        assert true <= tol * 1.05, (r, true)
+        assert abs(res[r] - true) <= max(1e-12, 0.05 * tol)
+
+
+def test_rhs_per_thread_option_checks():
+    wd = require_gpu()
+    dims = (4, 4, 4, 4)
+    op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_MIXED_F32)
+    for bad in (3, 5, -1, 8):
+        with pytest.raises(wd.WdError) as e:
+            op.set_option(wd.WD_OPT_MULTI_RHS_PER_THREAD, bad)
+        assert e.value.status == wd.WD_EINVAL
+    op.close()
