@@ -63,7 +63,7 @@ FP64_NOMINAL_TFLOPS = 1.259
 # reports, from one ncu capture each; the summary file holds the full command. None = not captured
 # for the kernel as it now stands.
 NCU_TRAFFIC = {
-    "cg_loop_f64_14x4": (57830144, "profiles/cg_loop_f64_14x4.md"),
+    "cg_loop_f64_14x4": (58503680, "profiles/cg_loop_f64_14x4.md"),
     "dslash_f64_14x4": (None, "profiles/dslash_f64_14x4.md"),
 }
 
@@ -734,10 +734,12 @@ def profile_case(argv):
     ap.add_argument("--multi", type=int, default=0, help="wd_apply_multi calls on this many Gaussian fields")
     ap.add_argument("--mgroup", type=int, default=0, help="multi-RHS group size K (0 = tuned)")
     ap.add_argument("--msites", type=int, default=0, help="multi-RHS sites per block (0 = tuned)")
+    ap.add_argument("--mkt", type=int, default=0, help="multi-RHS right-hand sides per thread (0 = tuned)")
     ap.add_argument("--msolve", type=int, default=0, help="one cg_solve_multi on this many Gaussian sources")
     ap.add_argument("--device-fields", action="store_true", help="generate links and sources on the device")
     ap.add_argument("--graph", type=int, default=-1,
                     help="WD_OPT_USE_GRAPH for the solves (0 = plain launches, which ncu lists one by one)")
+    ap.add_argument("--tma", type=int, default=0, help="WD_OPT_DSLASH_TMA (FP32 12-real: 1 or 2 = TMA-staged tiles)")
     ap.add_argument("--apply-inner", action="store_true",
                     help="mixed-precision contexts: wd_apply through the inner FP32 / FP16 operator")
     args = ap.parse_args(argv)
@@ -763,6 +765,8 @@ def profile_case(argv):
         op.set_option(wd.WD_OPT_BLOCK_DSLASH, args.block)
     if args.variant:
         op.set_option(wd.WD_OPT_DSLASH_VARIANT, args.variant)
+    if args.tma:
+        op.set_option(wd.WD_OPT_DSLASH_TMA, args.tma)
     if args.graph >= 0:
         op.set_option(wd.WD_OPT_USE_GRAPH, args.graph)
     if args.launches:
@@ -789,6 +793,8 @@ def profile_case(argv):
             op.set_option(wd.WD_OPT_MULTI_GROUP, args.mgroup)
         if args.msites:
             op.set_option(wd.WD_OPT_MULTI_SITES, args.msites)
+        if args.mkt:
+            op.set_option(wd.WD_OPT_MULTI_RHS_PER_THREAD, args.mkt)
         psi = torch.stack([source(10 + i) for i in range(args.multi)])
         out = op.apply_multi(psi)  # tunes the launch shape
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

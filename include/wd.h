@@ -122,10 +122,18 @@ enum {
                                 norm), D is applied with the FP32 links (12-real if loaded so)
                                 and the working-precision result is widened to complex128; 0
                                 (default) the FP64 operator                                      */
-  WD_OPT_MULTI_RHS_PER_THREAD = 15 /* multi-RHS, FP32 / FP16 working precision: right-hand sides
+  WD_OPT_MULTI_RHS_PER_THREAD = 15, /* multi-RHS, FP32 / FP16 working precision: right-hand sides
                                 held by one thread of the dslash, which loads and rebuilds each link
                                 once for all of them (1, 2 or 4; must divide the group K and not
                                 exceed the sites per block); 0 (default) = chosen by the autotuner */
+  WD_OPT_DSLASH_TMA = 16     /* FP32 working precision, lexicographic layout: 1 or 2 makes the
+                                stand-alone operator (wd_apply, wd_time_dslash) stage the neighbour
+                                spinors in shared memory by TMA bulk tensor copies, in tiles of
+                                Lx x 2 x 2 x 2 (1) or Lx x 4 x 2 x 2 (2) sites, when the FP32 links
+                                are 12-real (per-thread loads otherwise); needs Lx a multiple of 4
+                                up to 64 and the other extents divisible by the tile. A copy that
+                                does not land within its wait limit makes the call return
+                                WD_ECUDA. 0 (default): per-thread neighbour loads. Solves ignore it */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

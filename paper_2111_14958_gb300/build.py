@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwdcg.so")
-SOURCES = ["wd_dslash.cu", "wd_eo.cu", "wd_loop.cu", "wd_blas.cu", "wd_multi.cu", "wd_gen.cu", "wd_coo.cu", "wd_api.cu", "wd_serve.cu", "wd_noalloc.cu", "wd_probe.cu"]
+SOURCES = ["wd_dslash.cu", "wd_eo.cu", "wd_loop.cu", "wd_blas.cu", "wd_multi.cu", "wd_gen.cu", "wd_coo.cu", "wd_api.cu", "wd_serve.cu", "wd_noalloc.cu", "wd_probe.cu", "wd_tma.cu"]
 HEADERS = ["wd_device.cuh", "wd_stencil.cuh", "wd_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

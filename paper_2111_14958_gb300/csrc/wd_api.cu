@@ -129,6 +129,8 @@ struct wd_ctx {
   int loop_block, loop_var;   // launch shape of the persistent FP64 loop (timed on the loop itself)
   bool loop_tuned;
   FieldPtr p2, r2;            // second p and r buffers of the FP64 loop with 4, 8 or 16 lanes per site
+  int tma;                    // WD_OPT_DSLASH_TMA: stand-alone FP32 12-real operator staged by TMA (tile 1 or 2)
+  bool standalone;            // the current operator call is wd_apply / wd_time_dslash (not a solve)
   wd_multi_stats mstats;
 };
 
@@ -237,7 +239,23 @@ cudaError_t dslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fi
   d.block = dslash_block(c, in.prec);
   d.variant = dslash_variant(c, in.prec);
   d.kappa_dev = &c->sc->kappa;
+  d.tma = 0;
+  d.err = reinterpret_cast<int*>(c->loop_sync + 3);
+  if (c->tma && c->standalone && in.prec == SP32 && c->c12 && epi == EPI_PLAIN && !skip) d.tma = c->tma;
   return launch_dslash(d, st);
+}
+
+// After a stand-alone operator call: did a TMA staging wait give up?
+wd_status check_tma(wd_ctx* c) {
+  if (!c->tma) return WD_OK;
+  unsigned f = 0;
+  WD_CUDA(cudaMemcpy(&f, c->loop_sync + 3, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f) {
+    WD_CUDA(cudaMemset(c->loop_sync + 3, 0, sizeof(f)));
+    WD_CUDA(cudaMemset(&c->sc->ticket[TK_MISC], 0, sizeof(unsigned)));
+    return fail(WD_ECUDA, "TMA-staged dslash: a shared-memory staging wait gave up");
+  }
+  return WD_OK;
 }
 
 const GeomH* eo_geom(const wd_ctx* c) { return c->eo ? &c->geom : nullptr; }
@@ -1593,6 +1611,15 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float operator exists on mixed-precision contexts");
       c->apply_df = value != 0.0;
       return WD_OK;
+    case WD_OPT_DSLASH_TMA: {
+      const int v = (int)value;
+      if (value != (double)v || v < 0 || v > 2) return fail(WD_EINVAL, "TMA option must be 0, 1 or 2");
+      if (v && (c->wprec != SP32 || c->eo)) return fail(WD_EINVAL, "TMA staging serves the FP32 operator on the lexicographic layout");
+      if (v && !tma_dslash_supported(c->geom, v - 1))
+        return fail(WD_EINVAL, "TMA staging needs Lx a multiple of 4 up to 64 and Ly, Lz, Lt divisible by the tile");
+      c->tma = v;
+      return WD_OK;
+    }
     case WD_OPT_APPLY_INNER:
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "the inner operator exists on mixed-precision contexts");
       if (value != 0.0 && value != 1.0) return fail(WD_EINVAL, "apply-inner option must be 0 or 1");
@@ -1725,6 +1752,11 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
   if ((st = autotune_single(c)) != WD_OK) return st;
   const int bb = c->block_blas;
+  struct Standalone {
+    wd_ctx* c;
+    ~Standalone() { c->standalone = false; }
+  } standalone_{c};
+  c->standalone = true;
   if (c->precision == WD_PREC_F32) {
     WD_CUDA(launch_pack_c64((const float*)in, c->q, c->V, eo_geom(c), bb, c->stream));
     WD_CUDA(full_D(c, c->q, c->s, dagger ? 1 : 0, c->stream));
@@ -1749,7 +1781,7 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
     WD_CUDA(launch_unpack(b, (double*)out, c->V, eo_geom(c), bb, c->stream));
   }
   WD_CUDA(cudaStreamSynchronize(c->stream));
-  return WD_OK;
+  return check_tma(c);
 }
 
 }  // extern "C"
@@ -2117,6 +2149,11 @@ wd_status wd_time_dslash(wd_ctx* c, int dagger, int launches, double* avg_ms) {
   if ((st = autotune_single(c)) != WD_OK) return st;
   // the solver's dominant dslash: the working precision one, with its fused norm
   FieldPtr in = c->p, out = c->q;
+  struct Standalone {
+    wd_ctx* c;
+    ~Standalone() { c->standalone = false; }
+  } standalone_{c};
+  c->standalone = true;
   WD_CUDA(op(c, in, out, dagger, EPI_PLAIN, none_field(), &c->sc->scratch[0], TK_MISC, nullptr, c->stream));
   WD_CUDA(cudaEventRecord(c->ev0, c->stream));
   for (int i = 0; i < launches; ++i)
@@ -2126,7 +2163,7 @@ wd_status wd_time_dslash(wd_ctx* c, int dagger, int launches, double* avg_ms) {
   float ms = 0.f;
   WD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   *avg_ms = (double)ms / launches;
-  return WD_OK;
+  return check_tma(c);
 }
 
 wd_status wd_get_multi_stats(const wd_ctx* c, wd_multi_stats* out) {

@@ -115,6 +115,10 @@ static cudaError_t launch_p(const DslashCall& c, cudaStream_t st) {
 }
 
 cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
+  if (c.tma) {
+    if (!c.err) return cudaErrorInvalidValue;
+    return launch_dslash_tma(c, c.tma - 1, c.err, st);
+  }
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32) return cudaErrorInvalidValue;
   if (c.variant != 0 && (c.variant < 0 || c.variant > kMaxDslashVariant || c.in.prec != SP64))
     return cudaErrorInvalidValue;

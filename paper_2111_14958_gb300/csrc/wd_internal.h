@@ -111,7 +111,12 @@ struct DslashCall {
   int block;
   const double* kappa_dev;  // optional: kappa read from device memory (overrides `kappa`)
   int variant;              // FP64 only: lanes per site 1, 2, 4, 8, 16 for variant 0..4
+  int tma;                  // FP32 12-real, plain epilogue: 0 per-thread loads; 1 / 2 neighbour spinors staged
+                            // by TMA in tiles of Lx x 2 x 2 x 2 / Lx x 4 x 2 x 2 sites (wd_tma.cu)
+  int* err;                 // tma: set to 1 if a staging wait gave up
 };
+bool tma_dslash_supported(const GeomH& g, int tile);
+cudaError_t launch_dslash_tma(const DslashCall& c, int tile, int* err, cudaStream_t st);
 constexpr int kMaxDslashVariant = 4;
 inline int lanes_of_variant(int v) { return v <= 0 ? 1 : (1 << v); }
 

@@ -59,6 +59,7 @@ WD_OPT_LOOP_WAIT_LIMIT = 12
 WD_OPT_RESIDUAL_HISTORY = 13
 WD_OPT_APPLY_INNER = 14
 WD_OPT_MULTI_RHS_PER_THREAD = 15
+WD_OPT_DSLASH_TMA = 16
 
 
 class WdMultiStats(ctypes.Structure):
