@@ -19,23 +19,37 @@ struct LoopSync {
   long long limit;          // polls (64 ns sleep each) before a wait gives up
 };
 
+// Arrival with release and acquire semantics at GPU scope (the block's writes, ordered before it by
+// the __syncthreads that precedes, become visible to every block that later acquires the counter),
+// and the acquiring read of the pollers. No separate fence instruction is needed.
+__device__ __forceinline__ unsigned long long arrive_acq_rel(unsigned long long* p) {
+  unsigned long long old;
+  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], 1;" : "=l"(old) : "l"(p) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // All blocks arrive, then continue. Returns false (everywhere, eventually) if a wait gave up.
 // One monotonic 64-bit counter: barrier number k of the launch completes when the counter reaches
 // k * gridDim.x, so a waiter sees the last arrival's own atomic (no second release step), and the
-// last block to arrive does not wait at all.
+// last block to arrive does not wait at all. Thread 0 of each block arrives and polls; the
+// __syncthreads on either side carry the ordering to the rest of the block.
 __device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned long long G = gridDim.x;
-    __threadfence();  // this block's writes are visible before its arrival is
-    const unsigned long long arrived = atomicAdd(y.ctr, 1ull);
+    const unsigned long long arrived = arrive_acq_rel(y.ctr);
     const unsigned long long target = (arrived / G + 1) * G;
     int good = 1;
     if (arrived + 1 != target) {
-      volatile unsigned long long* ctr = y.ctr;
       long long spins = 0;
-      while (*ctr < target) {
+      while (load_acquire(y.ctr) < target) {
         if (++spins > y.limit || *(volatile int*)y.err) {
           atomicExch(y.err, 1);
           good = 0;
@@ -44,7 +58,6 @@ __device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
         __nanosleep(64);
       }
     }
-    __threadfence();
     ok = good && !*(volatile int*)y.err;
   }
   __syncthreads();
@@ -58,10 +71,7 @@ __device__ __forceinline__ bool loop_sum(double v, double* partials, const LoopS
   __shared__ double total;
   double w[1] = {v};
   block_reduce<OpSum, 1>(w, smem);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = w[0];
-    __threadfence();
-  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = w[0];  // released by the barrier's arrival
   if (!grid_barrier(y)) return false;
   if (threadIdx.x < 32) {
     double a = 0.0;
@@ -83,10 +93,9 @@ __device__ __forceinline__ bool loop_sum2(double v0, double v1, double* partials
   const int G = gridDim.x;
   double w[2] = {v0, v1};
   block_reduce<OpSum, 2>(w, smem);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {  // released by the barrier's arrival
     partials[blockIdx.x] = w[0];
     partials[G + blockIdx.x] = w[1];
-    __threadfence();
   }
   if (!grid_barrier(y)) return false;
   if (threadIdx.x < 32) {
