@@ -604,8 +604,9 @@ def _serve_requests(n_req, rate, seed):
     return reqs
 
 
-def _serve_run(wd, reqs, precision, slots, max_batch):
+def _serve_run(wd, reqs, precision, slots, max_batch, policy=0):
     srv = wd.Server(150e9, slots, max_batch=max_batch)
+    srv.set_policy(policy, 1000.0)
     # one untimed request per size and slot first: the resident contexts, tuned launch shapes, graphs
     warm = [srv.submit(dims=d, kappa=0.12, eps=0.4, gauge_seed=1, source_seed=2, tol=1e-8, precision=precision)
             for d in SERVE_SIZES for _ in range(slots)]
@@ -640,6 +641,7 @@ def _serve_run(wd, reqs, precision, slots, max_batch):
             "solves_per_s": len(res) / (t1 - t0), "wall_s": t1 - t0,
             "completed_ok": sum(1 for r in res if r["status"] == 0), "requests": len(res),
             "max_true_residual_over_tol": float(worst), "slots": slots, "max_batch": max_batch,
+            "policy": ["oldest first", "least work first, oldest first after 1 s"][policy],
             "batches": st["batches"] - base["batches"],
             "batched_requests": st["batched_requests"] - base["batched_requests"],
             "warm_hits": st["warm_hits"] - base["warm_hits"], "evictions": st["evictions"],
@@ -650,7 +652,8 @@ def _serving(wd, seed=7):
     """Poisson streams of single-RHS solves through the serving runtime (continuous admission, batches of
     same-operator requests where the persistent loop serves them: 8^4 and 12^4 in mixed precision).
     Above saturation (200 requests/s offered, 500 requests) and below it (15/s, 300 requests); mixed
-    precision on 4 slots with and without batching, on 1 slot, with even-odd preconditioning, and
+    precision on 4 slots with and without batching, with least-work-first admission (aging after
+    1 s), on 1 slot, with even-odd preconditioning, and
     plain FP64 one at a time (a 100-request sample: it serves about 4 solves/s). 150 GB budget."""
     hi = _serve_requests(500, 200.0, seed)
     lo = _serve_requests(300, 15.0, seed + 1)
@@ -658,6 +661,8 @@ def _serving(wd, seed=7):
                        "kappa U[0.115,0.124], tol {1e-8,1e-10}, eps U[0.3,0.5], 150 GB budget"}
     out["mixed_f32_4_slots_batched_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32, 4, 8)
     out["mixed_f32_4_slots_unbatched_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32, 4, 1)
+    out["mixed_f32_4_slots_batched_least_work_first_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32, 4, 8,
+                                                                            policy=1)
     out["mixed_f32_1_slot_batched_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32, 1, 8)
     out["mixed_f32_4_slots_batched_15_per_s"] = _serve_run(wd, lo, wd.WD_PREC_MIXED_F32, 4, 8)
     out["mixed_f32_even_odd_4_slots_200_per_s"] = _serve_run(wd, hi, wd.WD_PREC_MIXED_F32 | wd.WD_EVEN_ODD, 4, 8)

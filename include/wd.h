@@ -305,6 +305,9 @@ wd_status wd_generate_source(wd_ctx* ctx, unsigned long long seed, double* out);
  * wd_server_submit queues a request (returns its id at once); wd_server_wait blocks until it is
  * done; wd_server_poll returns immediately (*done = 0/1). A finished result is returned once and
  * then forgotten. wd_server_set_max_batch sets the batch limit (1..16; 1 = no batching; default 8).
+ * wd_server_set_policy chooses the request admitted next: 0 (default) the oldest; 1 the one with
+ * the least estimated work (sites times a per-precision factor) unless the oldest has waited more
+ * than max_wait_ms, which then goes first (no request waits unboundedly behind smaller ones).
  * wd_server_destroy finishes running solves, drops queued ones and frees all.
  * Errors: WD_EINVAL (bad request), WD_ENOMEM (a request larger than the whole budget), WD_ECUDA.
  */
@@ -352,6 +355,7 @@ wd_status wd_server_submit(wd_server* srv, const wd_request* req, long long* id)
 wd_status wd_server_wait(wd_server* srv, long long id, wd_result* out);
 wd_status wd_server_poll(wd_server* srv, long long id, wd_result* out, int* done);
 wd_status wd_server_set_max_batch(wd_server* srv, int max_batch);
+wd_status wd_server_set_policy(wd_server* srv, int policy, double max_wait_ms);
 wd_status wd_server_get_stats(wd_server* srv, wd_server_stats* out);
 void wd_server_destroy(wd_server* srv);
 

@@ -179,6 +179,7 @@ Red red_to(wd_ctx* c, int slot, double* result) {
   r.partials = c->partials;
   r.ticket = &c->sc->ticket[slot];
   r.result = result;
+  r.cap = (long long)c->partials_len;
   return r;
 }
 
@@ -187,6 +188,7 @@ Red no_red() {
   r.partials = nullptr;
   r.ticket = nullptr;
   r.result = nullptr;
+  r.cap = 0;
   return r;
 }
 
@@ -1482,8 +1484,9 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
     if (mixed && (st = alloc_field(c, &c->t64, SP64)) != WD_OK) return bail(st);
     if (wprec == SP64) c->t64 = c->t;
   }
-  // the largest grid of any reduction: 12 V words at 32 threads per block, or 4 V links
-  c->partials_len = (size_t)(12 * V / 32 + 64);
+  // the largest grid of any reduction: the FP64 dslash with 16 lanes per site at 32 threads per
+  // block (V / 2 blocks); the vector kernels need at most 12 V / 32, the gauge load 4 V / 128
+  c->partials_len = (size_t)(V / 2 + 64);
   if (cudaMalloc(&c->partials, sizeof(double) * c->partials_len) != cudaSuccess ||
       cudaMalloc(&c->sc, sizeof(CgScalars)) != cudaSuccess ||
       cudaMalloc(&c->loop_partials, sizeof(double) * 3 * kLoopMaxGrid) != cudaSuccess ||

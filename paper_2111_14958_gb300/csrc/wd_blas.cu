@@ -137,6 +137,7 @@ template <int SP>
 static cudaError_t pack_t(const double* canon, FieldPtr out, int V, const GeomH* eo, Red red, int block,
                           cudaStream_t st) {
   const int grid = grid_for(V, block);
+  if (!red_fits(red, grid)) return cudaErrorInvalidValue;
   const double2* c2 = reinterpret_cast<const double2*>(canon);
   const SiteMap m = site_map(eo);
   if (red.result)
@@ -262,6 +263,7 @@ __global__ void gauge_load_kernel(const double2* __restrict__ canon, void* out, 
 cudaError_t launch_gauge_load(const double* canon, GaugePtr out, int V, const GeomH* eo, Red red, int block,
                               cudaStream_t st) {
   const int grid = grid_for(4 * V, block);
+  if (!red_fits(red, grid)) return cudaErrorInvalidValue;
   const SiteMap m = site_map(eo);
   const double2* c2 = reinterpret_cast<const double2*>(canon);
   void* o = const_cast<void*>(out.p);

@@ -53,14 +53,17 @@ __global__ void __launch_bounds__(kDslashMaxThreads) dslash_lanes_kernel(const D
 }
 
 template <int L, bool DAG, int EPI>
-static void launch_lanes(const DslashArgs<P64, false>& a, const DslashCall& c, cudaStream_t st) {
+static cudaError_t launch_lanes(const DslashArgs<P64, false>& a, const DslashCall& c, cudaStream_t st) {
   if (c.red.result) {
     auto k = dslash_lanes_kernel<L, DAG, EPI, true>;
-    k<<<stride_grid(k, L * c.g.V, c.block), c.block, 0, st>>>(a);
+    const int grid = stride_grid(k, L * c.g.V, c.block);
+    if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
+    k<<<grid, c.block, 0, st>>>(a);
   } else {
     auto k = dslash_lanes_kernel<L, DAG, EPI, false>;
     k<<<stride_grid(k, L * c.g.V, c.block), c.block, 0, st>>>(a);
   }
+  return cudaSuccess;
 }
 
 template <int SP, bool C12, bool DAG, int EPI>
@@ -80,15 +83,19 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   a.result = c.red.result;
   if constexpr (SP == P64 && !C12) {
     if (c.variant >= 2) {  // 4, 8 or 16 lanes per site
-      if (c.variant == 2) launch_lanes<4, DAG, EPI>(a, c, st);
-      else if (c.variant == 3) launch_lanes<8, DAG, EPI>(a, c, st);
-      else launch_lanes<16, DAG, EPI>(a, c, st);
+      cudaError_t e;
+      if (c.variant == 2) e = launch_lanes<4, DAG, EPI>(a, c, st);
+      else if (c.variant == 3) e = launch_lanes<8, DAG, EPI>(a, c, st);
+      else e = launch_lanes<16, DAG, EPI>(a, c, st);
+      if (e != cudaSuccess) return e;
       return cudaGetLastError();
     }
     if (c.variant == 1) {  // two lanes per site
       if (c.red.result) {
         auto k = dslash_pair_kernel<C12, DAG, EPI, true>;
-        k<<<stride_grid(k, 2 * c.g.V, c.block), c.block, 0, st>>>(a);
+        const int grid = stride_grid(k, 2 * c.g.V, c.block);
+        if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
+        k<<<grid, c.block, 0, st>>>(a);
       } else {
         auto k = dslash_pair_kernel<C12, DAG, EPI, false>;
         k<<<stride_grid(k, 2 * c.g.V, c.block), c.block, 0, st>>>(a);
@@ -98,7 +105,9 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
   }
   if (c.red.result) {
     auto k = dslash_kernel<SP, C12, DAG, EPI, true>;
-    k<<<stride_grid(k, c.g.V, c.block), c.block, 0, st>>>(a);
+    const int grid = stride_grid(k, c.g.V, c.block);
+    if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
+    k<<<grid, c.block, 0, st>>>(a);
   } else {
     auto k = dslash_kernel<SP, C12, DAG, EPI, false>;
     k<<<stride_grid(k, c.g.V, c.block), c.block, 0, st>>>(a);

@@ -38,7 +38,9 @@ static cudaError_t eo_launch_t(const EoCall& c, cudaStream_t st) {
   a.b = make_ref<SP>(c.b, c.g.V);
   if (c.red.result) {
     auto k = dslash_eo_kernel<SP, C12, DAG, SELF, RESID, true>;
-    k<<<stride_grid(k, c.g.V / 2, c.block), c.block, 0, st>>>(a);
+    const int grid = stride_grid(k, c.g.V / 2, c.block);
+    if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
+    k<<<grid, c.block, 0, st>>>(a);
   } else {
     auto k = dslash_eo_kernel<SP, C12, DAG, SELF, RESID, false>;
     k<<<stride_grid(k, c.g.V / 2, c.block), c.block, 0, st>>>(a);

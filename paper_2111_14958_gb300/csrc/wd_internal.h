@@ -92,12 +92,15 @@ enum { TK_DSLASH_A = 0, TK_DSLASH_B = 1, TK_UPD_R = 2, TK_UPD_XP = 3, TK_PACK = 
 
 enum { EPI_PLAIN = 0, EPI_RESID = 1 };
 
-// A reduction target: result == nullptr means no reduction.
+// A reduction target: result == nullptr means no reduction. A launcher whose grid would need more
+// block partials than cap refuses the launch (cudaErrorInvalidValue) instead of writing past them.
 struct Red {
   double* partials;  // >= N * gridDim doubles
   unsigned* ticket;
   double* result;
+  long long cap;     // doubles available at partials
 };
+inline bool red_fits(const Red& r, long long grid, int n = 1) { return !r.result || grid * n <= r.cap; }
 
 struct DslashCall {
   GeomH g;

@@ -5,7 +5,8 @@
 // job) admits them into execution slots as slots and device memory free up; memory is charged
 // against the budget given at creation. Every slot has its own CUDA stream and worker thread, so
 // admitted work runs concurrently and its kernels overlap on the device. The oldest waiting
-// request is admitted first, together with up to max_batch - 1 later requests of the same operator
+// request is admitted first (or, under the shortest-first policy, the one with the least estimated
+// work unless the oldest has waited too long), together with up to max_batch - 1 other requests of the same operator
 // (lattice, precision, boundary, iteration limit) when that operator's CG loop is the persistent
 // kernel: the slot solves them with cg_solve_batch, one loop launch for all of them per pass, each
 // result bitwise the one of its solve alone. A slot keeps the contexts it created (links, Krylov
@@ -132,6 +133,8 @@ struct wd_server {
   long long next_id = 1;
   unsigned long long tick = 0;
   int max_batch = 8;
+  int policy = 0;             // 0: oldest first; 1: least estimated work first, with aging
+  double max_wait_ms = 1000;  // policy 1: a request waiting longer than this goes first
   bool stopping = false;
   int device = 0;
   wd_server_stats stats;
@@ -295,6 +298,39 @@ void slot_main(wd_server* srv, Slot* s) {
   s->cache.clear();
 }
 
+// Estimated work of a request (policy 1): sites times a per-precision factor (plain FP64 solves
+// take about 8x a mixed-precision solve on GB300, plain FP32 ones about 0.5x; even-odd about
+// 0.6x), times 1.2 for the tighter of the two tolerances. Only the order matters.
+double job_cost(const wd_request& r) {
+  double f = 1.0;
+  switch (r.precision & ~WD_EVEN_ODD) {
+    case WD_PREC_F64: f = 8.0; break;
+    case WD_PREC_F32: f = 0.5; break;
+    default: f = 1.0;
+  }
+  if (r.precision & WD_EVEN_ODD) f *= 0.6;
+  if (r.tol < 1e-9) f *= 1.2;
+  return f * (double)volume_of(r.dims);
+}
+
+// The request admitted next: the oldest, or (policy 1) the least work unless the oldest has waited
+// longer than max_wait_ms (then it goes first, so that large requests are not starved).
+Job* next_job(wd_server* srv) {
+  Job* oldest = srv->pending.front();
+  if (srv->policy == 0 || srv->pending.size() < 2) return oldest;
+  if (ms_between(oldest->t_submit, Clock::now()) > srv->max_wait_ms) return oldest;
+  Job* best = oldest;
+  double bc = job_cost(oldest->req);
+  for (Job* j : srv->pending) {
+    const double c = job_cost(j->req);
+    if (c < bc) {
+      best = j;
+      bc = c;
+    }
+  }
+  return best;
+}
+
 size_t slot_bytes(const Slot* s) {
   size_t b = 0;
   for (const auto& e : s->cache) b += e.bytes;
@@ -302,7 +338,8 @@ size_t slot_bytes(const Slot* s) {
 }
 
 // Assign pending jobs to idle slots (called with the mutex held).
-// The oldest pending job goes first, with up to max_batch - 1 later jobs of the same operator when
+// The job next_job picks goes first (the oldest, or under policy 1 the least work unless the oldest
+// has waited too long), with up to max_batch - 1 other queued jobs of the same operator when
 // its CG loop is the persistent kernel (a batch shares its loop launches); other jobs keep their
 // order. The slot: an idle one with resident contexts of the operator (the most of them), else the
 // idle slot holding the fewest resident bytes. Jobs without an idle resident get a placeholder
@@ -312,7 +349,7 @@ size_t slot_bytes(const Slot* s) {
 // charged.
 void schedule(wd_server* srv) {
   while (!srv->pending.empty()) {
-    Job* j = srv->pending.front();
+    Job* j = next_job(srv);
     Slot* pick = nullptr;
     int pick_warm = 0;
     for (auto& sp : srv->slots) {
@@ -335,8 +372,8 @@ void schedule(wd_server* srv) {
     // the batch: j and later jobs of its operator, up to max_batch
     std::vector<Job*> members{j};
     if (srv->max_batch > 1 && wdk::batch_capable(j->req.dims, j->req.precision)) {
-      for (size_t i = 1; i < srv->pending.size() && (int)members.size() < srv->max_batch; ++i)
-        if (same_batch_key(srv->pending[i]->req, j->req)) members.push_back(srv->pending[i]);
+      for (size_t i = 0; i < srv->pending.size() && (int)members.size() < srv->max_batch; ++i)
+        if (srv->pending[i] != j && same_batch_key(srv->pending[i]->req, j->req)) members.push_back(srv->pending[i]);
     }
     // residents: warm ones of the slot first, then placeholders charged against the budget
     std::vector<int> slots_idx;
@@ -534,6 +571,17 @@ wd_status wd_server_set_max_batch(wd_server* srv, int max_batch) {
   }
   std::lock_guard<std::mutex> lk(srv->mu);
   srv->max_batch = max_batch;
+  return WD_OK;
+}
+
+wd_status wd_server_set_policy(wd_server* srv, int policy, double max_wait_ms) {
+  if (!srv || (policy != 0 && policy != 1) || !(max_wait_ms >= 0.0)) {
+    wdk::set_last_error("null server, policy not 0 or 1, or negative max_wait_ms");
+    return WD_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->policy = policy;
+  srv->max_wait_ms = max_wait_ms;
   return WD_OK;
 }
 

@@ -320,6 +320,7 @@ cudaError_t launch_dslash_tma(const DslashCall& c, int tile, int* err, cudaStrea
     int grid = per_sm * sms;
     if (grid > a.ntiles) grid = a.ntiles;
     if (c.red.result && grid > kLoopMaxGrid) grid = kLoopMaxGrid;
+    if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
     k<<<grid, threads, smem, st>>>(tm_in, tm_fy, tm_fz, tm_ft, a);
     return cudaGetLastError();
   };

@@ -131,6 +131,7 @@ _sig = {
     "wd_server_poll": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(WdResult), ctypes.POINTER(_I)]),
     "wd_server_get_stats": (_I, [_P, ctypes.POINTER(WdServerStats)]),
     "wd_server_set_max_batch": (_I, [_P, _I]),
+    "wd_server_set_policy": (_I, [_P, _I, _D]),
     "wd_server_destroy": (None, [_P]),
     "wd_last_error": (ctypes.c_char_p, []),
     "wd_version": (ctypes.c_char_p, []),
@@ -456,6 +457,11 @@ class Server:
 
     def set_max_batch(self, max_batch: int):
         _check(_lib.wd_server_set_max_batch(_P(self.h), int(max_batch)), "wd_server_set_max_batch")
+
+    def set_policy(self, policy: int, max_wait_ms: float = 1000.0):
+        """0: oldest request first; 1: least estimated work first, the oldest first once it has
+        waited more than max_wait_ms."""
+        _check(_lib.wd_server_set_policy(_P(self.h), int(policy), float(max_wait_ms)), "wd_server_set_policy")
 
     def submit(self, dims, kappa, eps, gauge_seed, source_seed, tol, precision=WD_PREC_MIXED_F32, maxit=20000,
                boundary=None, src_host: torch.Tensor = None, x_host: torch.Tensor = None) -> int:

@@ -149,3 +149,27 @@ def test_server_without_batching_and_option_checks():
         with pytest.raises(wd.WdError):
             srv.set_max_batch(bad)
     srv.close()
+
+
+@pytest.mark.parametrize("policy,max_wait,small_first", [(1, 1e7, True), (1, 0.0, False), (0, 1e7, False)])
+def test_server_admission_policy(policy, max_wait, small_first):
+    """Shortest-first admission (policy 1) starts queued small requests before an older large one;
+    with no waiting allowed (max_wait 0) or the default policy the oldest goes first."""
+    import time
+    wd = require_gpu()
+    srv = wd.Server(budget_bytes=8e9, slots=1, max_batch=1)
+    srv.set_policy(policy, max_wait)
+    q = dict(kappa=0.12, eps=0.4, source_seed=3, tol=1e-10, precision=wd.WD_PREC_MIXED_F32)
+    t0 = time.perf_counter()
+    ids, ts = [], []
+    for i, dims in enumerate([(16, 16, 16, 16), (16, 16, 16, 32), (4, 4, 4, 4), (6, 6, 6, 6)]):
+        ts.append(time.perf_counter() - t0)
+        ids.append(srv.submit(dims=dims, gauge_seed=40 + i, **q))
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    assert all(r["status"] == wd.WD_OK for r in res)
+    start = [1e-3 * r["queue_ms"] + t for r, t in zip(res, ts)]
+    big, small = start[1], min(start[2], start[3])
+    assert (small < big) == small_first, (policy, max_wait, start)
+    with pytest.raises(wd.WdError):
+        wd.Server(budget_bytes=1e9, slots=1).set_policy(2, 0.0)

@@ -32,7 +32,7 @@ def test_lanes_dslash_matches_oracle(dims, lanes):
     op = wd.WilsonDirac(dims, 0.12, BC, wd.WD_PREC_F64)
     op.load_gauge(to_dev(U))
     op.set_option(wd.WD_OPT_DSLASH_VARIANT, VARIANTS[lanes])
-    for block in (64, 128, 256):
+    for block in (32, 64, 128, 256):
         op.set_option(wd.WD_OPT_BLOCK_DSLASH, block)
         for dagger in (False, True):
             out = to_np(op.apply(to_dev(psi), dagger=dagger))
@@ -144,3 +144,16 @@ def test_loop_tuner_choice_solves_and_repeats(dims):
         assert ocg.true_residual(U, eta, to_np(x), 0.12) <= 1e-10 * 1.01
         res.append((to_np(x), iters, r))
     assert np.array_equal(res[0][0], res[1][0]) and res[0][1:] == res[1][1:]
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16])
+def test_lanes_with_32_thread_blocks_solve(lanes):
+    """The widest grids (16 lanes per site, 32 threads per block: V / 2 blocks, each with a reduction
+    partial) in the prologue's fused-norm dslash and in the loop: the solve meets the oracle."""
+    wd = require_gpu()
+    dims = (8, 8, 8, 8)
+    U, eta = fields(dims)
+    for mode in (1, 2):
+        x, iters, res, st, stats = _solve(wd, dims, lanes, mode, U, eta, block=32)
+        assert st == wd.WD_OK and 60 < iters < 120, (mode, iters)
+        assert ocg.true_residual(U, eta, x, 0.12) <= 1e-10 * 1.01
