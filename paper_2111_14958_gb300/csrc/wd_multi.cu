@@ -539,29 +539,33 @@ static cudaError_t mlaunch_t(const MDslashCall& c, cudaStream_t st) {
   a.tickets = c.tickets;
   a.result = c.result;
   const int spb = c.sites_per_block;
-  dim3 grid(c.grid_x, c.nrhs / c.group);
+  const int groups = c.nrhs / c.group;
   const int kt = c.rhs_per_thread;
+  // One wave of resident blocks over all groups (grid-stride over sites): with more blocks than
+  // fit at once, the later ones would start only after the first wave had walked all its sites,
+  // and the neighbour spinors shared across the two would be read from DRAM twice.
+  auto launch = [&](auto k, int block, size_t smem) -> cudaError_t {
+    int gx = resident_blocks(reinterpret_cast<const void*>(k), block) / groups;
+    if (gx < 1) gx = 1;
+    if (gx > c.grid_x) gx = c.grid_x;
+    k<<<dim3(gx, groups), block, smem, st>>>(a);
+    return cudaGetLastError();
+  };
   if constexpr (SP == P32 || SP == P16) {
     if (kt == 2 || kt == 4) {
       const int block = c.group / kt * spb;
       const size_t smem = sizeof(double) * (c.group * spb + 32);
-      if (kt == 2) {
-        if (c.result) dslash_multi_kt_kernel<SP, C12, DAG, EPI, true, 2><<<grid, block, smem, st>>>(a);
-        else dslash_multi_kt_kernel<SP, C12, DAG, EPI, false, 2><<<grid, block, smem, st>>>(a);
-      } else {
-        if (c.result) dslash_multi_kt_kernel<SP, C12, DAG, EPI, true, 4><<<grid, block, smem, st>>>(a);
-        else dslash_multi_kt_kernel<SP, C12, DAG, EPI, false, 4><<<grid, block, smem, st>>>(a);
-      }
-      return cudaGetLastError();
+      if (kt == 2)
+        return c.result ? launch(dslash_multi_kt_kernel<SP, C12, DAG, EPI, true, 2>, block, smem)
+                        : launch(dslash_multi_kt_kernel<SP, C12, DAG, EPI, false, 2>, block, smem);
+      return c.result ? launch(dslash_multi_kt_kernel<SP, C12, DAG, EPI, true, 4>, block, smem)
+                      : launch(dslash_multi_kt_kernel<SP, C12, DAG, EPI, false, 4>, block, smem);
     }
   }
   const int block = c.group * spb;
   const size_t smem = sizeof(double) * (block + 32);
-  if (c.result)
-    dslash_multi_kernel<SP, C12, DAG, EPI, true><<<grid, block, smem, st>>>(a);
-  else
-    dslash_multi_kernel<SP, C12, DAG, EPI, false><<<grid, block, smem, st>>>(a);
-  return cudaGetLastError();
+  return c.result ? launch(dslash_multi_kernel<SP, C12, DAG, EPI, true>, block, smem)
+                  : launch(dslash_multi_kernel<SP, C12, DAG, EPI, false>, block, smem);
 }
 
 template <int SP, bool C12>
