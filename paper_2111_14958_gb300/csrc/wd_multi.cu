@@ -92,27 +92,31 @@ __device__ __forceinline__ void mload(const MSpinor<P16>& f, int s, int r, int V
   }
 }
 
-// Neighbour spinor of a hop, returning the hop's reconstruction factor (FP16: the per-site norm is
-// folded into the factor instead of the 24 values, as in the single right-hand-side kernel).
-template <typename Ref, typename R>
-__device__ __forceinline__ R mload_hop(const Ref& f, int s, int r, int V, int N, Cx<R> (&v)[12], R k) {
-  mload(f, s, r, V, N, v);
+// Neighbour spinor of a hop, projected (spin_project<MU, S>), returning the hop's reconstruction
+// factor (FP16: the per-site norm is folded into the factor instead of h, and the lower spins enter
+// the projection through mixed-precision FMAs, as in the single right-hand-side kernel).
+template <int MU, int S, typename Ref, typename R>
+__device__ __forceinline__ R mload_project_hop(const Ref& f, int s, int r, int V, int N, Cx<R> (&h)[6], R k) {
+  Cx<R> psi[12];
+  mload(f, s, r, V, N, psi);
+  spin_project<MU, S>(psi, h);
   return k;
 }
 
-__device__ __forceinline__ float mload_hop(const MSpinor<P16>& f, int s, int r, int V, int N, Cx<float> (&v)[12],
-                                           float k) {
+template <int MU, int S>
+__device__ __forceinline__ float mload_project_hop(const MSpinor<P16>& f, int s, int r, int V, int N,
+                                                   Cx<float> (&h)[6], float k) {
   const float nrm = __ldg(f.norm + (size_t)s * N + r);
+  uint32_t w[12];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const uint4 d = __ldg(f.p + ((size_t)j * V + s) * N + r);
-    const uint32_t w[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&w[q]));
-      v[4 * j + q] = cx(fl.x, fl.y);
-    }
+    w[4 * j] = d.x;
+    w[4 * j + 1] = d.y;
+    w[4 * j + 2] = d.z;
+    w[4 * j + 3] = d.w;
   }
+  spin_project_f16<MU, S>(w, h);
   return k * nrm;
 }
 
@@ -296,9 +300,8 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r
   {
     const bool wrap = c[MU] == a.g.L[MU] - 1;
     const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
-    Cx<R> psi[12], h[6], u[9], chi[6];
-    const R k = mload_hop(a.in, nb, r, V, N, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
-    spin_project<MU, SF>(psi, h);
+    Cx<R> h[6], u[9], chi[6];
+    const R k = mload_project_hop<MU, SF>(a.in, nb, r, V, N, h, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     load_link(a.u, MU, s, V, u);
     su3_mul(u, h, chi);
     spin_reconstruct<MU, SF>(acc, chi, k);
@@ -306,9 +309,8 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r
   {
     const bool wrap = c[MU] == 0;
     const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
-    Cx<R> psi[12], h[6], u[9], chi[6];
-    const R k = mload_hop(a.in, nb, r, V, N, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
-    spin_project<MU, -SF>(psi, h);
+    Cx<R> h[6], u[9], chi[6];
+    const R k = mload_project_hop<MU, -SF>(a.in, nb, r, V, N, h, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     load_link(a.u, MU, nb, V, u);
     su3_dag_mul(u, h, chi);
     spin_reconstruct<MU, -SF>(acc, chi, k);
@@ -357,9 +359,8 @@ __device__ __forceinline__ void mhop_kt(const MArgs<SP, C12>& a, R mk, int s, in
     load_link(a.u, MU, s, V, u);
 #pragma unroll
     for (int j = 0; j < KT; ++j) {
-      Cx<R> psi[12], h[6], chi[6];
-      const R k = mload_hop(a.in, nb, r0 + j, V, N, psi, k0);
-      spin_project<MU, SF>(psi, h);
+      Cx<R> h[6], chi[6];
+      const R k = mload_project_hop<MU, SF>(a.in, nb, r0 + j, V, N, h, k0);
       su3_mul(u, h, chi);
       spin_reconstruct<MU, SF>(acc[j], chi, k);
     }
@@ -372,9 +373,8 @@ __device__ __forceinline__ void mhop_kt(const MArgs<SP, C12>& a, R mk, int s, in
     load_link(a.u, MU, nb, V, u);
 #pragma unroll
     for (int j = 0; j < KT; ++j) {
-      Cx<R> psi[12], h[6], chi[6];
-      const R k = mload_hop(a.in, nb, r0 + j, V, N, psi, k0);
-      spin_project<MU, -SF>(psi, h);
+      Cx<R> h[6], chi[6];
+      const R k = mload_project_hop<MU, -SF>(a.in, nb, r0 + j, V, N, h, k0);
       su3_dag_mul(u, h, chi);
       spin_reconstruct<MU, -SF>(acc[j], chi, k);
     }

@@ -100,10 +100,8 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int
   {
     const bool wrap = c[MU] == a.g.L[MU] - 1;
     const int nb = wrap ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
-    Cx<R> psi[12];
-    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     Cx<R> h[6];
-    spin_project<MU, S_FWD>(psi, h);
+    const R k = load_project_hop<MU, S_FWD>(a.in, nb, V, h, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     Cx<R> u[9];
     load_link(a.u, MU, s, V, u);
     Cx<R> chi[6];
@@ -114,10 +112,8 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<SP, C12>& a, R mk, int
   {
     const bool wrap = c[MU] == 0;
     const int nb = wrap ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
-    Cx<R> psi[12];
-    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     Cx<R> h[6];
-    spin_project<MU, -S_FWD>(psi, h);
+    const R k = load_project_hop<MU, -S_FWD>(a.in, nb, V, h, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     Cx<R> u[9];
     load_link(a.u, MU, nb, V, u);
     Cx<R> chi[6];
@@ -722,9 +718,8 @@ __device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int 
     const bool wrap = n[MU] == a.e.g.L[MU] - 1;
     n[MU] = wrap ? 0 : n[MU] + 1;
     const int nb = eo_index(a.e.g, n);
-    Cx<R> psi[12], h[6], u[9], chi[6];
-    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
-    spin_project<MU, SF>(psi, h);
+    Cx<R> h[6], u[9], chi[6];
+    const R k = load_project_hop<MU, SF>(a.in, nb, V, h, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
     load_link(a.u, MU, s, V, u);
     su3_mul(u, h, chi);
     spin_reconstruct<MU, SF>(acc, chi, k);
@@ -734,9 +729,8 @@ __device__ __forceinline__ void eo_hop_pair(const EoArgs<SP, C12>& a, R k0, int 
     const bool wrap = n[MU] == 0;
     n[MU] = wrap ? a.e.g.L[MU] - 1 : n[MU] - 1;
     const int nb = eo_index(a.e.g, n);
-    Cx<R> psi[12], h[6], u[9], chi[6];
-    const R k = load_hop_spinor(a.in, nb, V, psi, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
-    spin_project<MU, -SF>(psi, h);
+    Cx<R> h[6], u[9], chi[6];
+    const R k = load_project_hop<MU, -SF>(a.in, nb, V, h, (wrap && a.e.g.bc[MU] < 0) ? -k0 : k0);
     load_link(a.u, MU, nb, V, u);
     su3_dag_mul(u, h, chi);
     spin_reconstruct<MU, -SF>(acc, chi, k);
