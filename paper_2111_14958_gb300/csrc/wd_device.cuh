@@ -636,6 +636,94 @@ __device__ __forceinline__ void su3_dag_mul(const Cx<R> (&u)[9], const Cx<R> (&h
   }
 }
 
+// ---------------------------------------------------------------- packed FP32 SU(3) products
+//
+// For FP32 the two spins of a half-spinor share every link entry, so each colour row's real parts
+// (spin 0, spin 1) and imaginary parts accumulate as packed pairs (fma.rn.f32x2, the link entry
+// broadcast to both halves): 36 packed instructions per product instead of 72 scalar ones, on the
+// same FP32 pipe. Each half performs the scalar form's operations in the scalar form's order, so
+// the results are the same bits.
+
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void unpk2(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 bc2(float x) { return pk2(x, x); }
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// The spin pairs (h[b], h[3 + b]) of a half-spinor: real parts and imaginary parts.
+__device__ __forceinline__ void spin_pairs(const Cx<float> (&h)[6], f32x2 (&hr)[3], f32x2 (&hi)[3]) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    hr[b] = pk2(h[b].re, h[3 + b].re);
+    hi[b] = pk2(h[b].im, h[3 + b].im);
+  }
+}
+
+template <>
+__device__ __forceinline__ void su3_mul<float>(const Cx<float> (&u)[9], const Cx<float> (&h)[6], Cx<float> (&chi)[6]) {
+  f32x2 hr[3], hi[3];
+  spin_pairs(h, hr, hi);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const Cx<float> u0 = u[3 * a], u1 = u[3 * a + 1], u2 = u[3 * a + 2];
+    f32x2 re = mul2(bc2(u0.re), hr[0]);
+    re = fma2(bc2(-u0.im), hi[0], re);
+    re = fma2(bc2(u1.re), hr[1], re);
+    re = fma2(bc2(-u1.im), hi[1], re);
+    re = fma2(bc2(u2.re), hr[2], re);
+    re = fma2(bc2(-u2.im), hi[2], re);
+    f32x2 im = mul2(bc2(u0.re), hi[0]);
+    im = fma2(bc2(u0.im), hr[0], im);
+    im = fma2(bc2(u1.re), hi[1], im);
+    im = fma2(bc2(u1.im), hr[1], im);
+    im = fma2(bc2(u2.re), hi[2], im);
+    im = fma2(bc2(u2.im), hr[2], im);
+    unpk2(re, chi[a].re, chi[3 + a].re);
+    unpk2(im, chi[a].im, chi[3 + a].im);
+  }
+}
+
+template <>
+__device__ __forceinline__ void su3_dag_mul<float>(const Cx<float> (&u)[9], const Cx<float> (&h)[6],
+                                                  Cx<float> (&chi)[6]) {
+  f32x2 hr[3], hi[3];
+  spin_pairs(h, hr, hi);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const Cx<float> u0 = u[a], u1 = u[3 + a], u2 = u[6 + a];
+    f32x2 re = mul2(bc2(u0.re), hr[0]);
+    re = fma2(bc2(u0.im), hi[0], re);
+    re = fma2(bc2(u1.re), hr[1], re);
+    re = fma2(bc2(u1.im), hi[1], re);
+    re = fma2(bc2(u2.re), hr[2], re);
+    re = fma2(bc2(u2.im), hi[2], re);
+    f32x2 im = mul2(bc2(u0.re), hi[0]);
+    im = fma2(bc2(-u0.im), hr[0], im);
+    im = fma2(bc2(u1.re), hi[1], im);
+    im = fma2(bc2(-u1.im), hr[1], im);
+    im = fma2(bc2(u2.re), hi[2], im);
+    im = fma2(bc2(-u2.im), hr[2], im);
+    unpk2(re, chi[a].re, chi[3 + a].re);
+    unpk2(im, chi[a].im, chi[3 + a].im);
+  }
+}
+
 // ---------------------------------------------------------------- deterministic grid reductions
 //
 // Every block reduces its threads' values with a fixed shuffle tree, stores one partial per block,
