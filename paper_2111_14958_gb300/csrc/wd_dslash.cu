@@ -15,7 +15,7 @@
 namespace wdk {
 
 template <int SP, bool C12, bool DAG, int EPI, bool NORM>
-__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashKernelMinBlocks<SP>::value)
     dslash_kernel(const DslashArgs<SP, C12> a) {
   if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
   const int V = a.g.V;

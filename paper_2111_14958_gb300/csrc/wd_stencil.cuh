@@ -197,6 +197,13 @@ template <int SP>
 struct DslashMinBlocks {
   static constexpr int value = SP == P64 ? 1 : (SP == PDF ? 1 : 3);
 };
+// The stand-alone FP16 dslash kernel: two blocks of 256 threads per SM (up to 128 registers) give
+// it more loads in flight per warp than three blocks give it warps (32^4: 76.5 vs 78.0 us; 24^4
+// with 128-thread blocks: 28.8 vs 31.3 us); FP32 stays at three (83.0 vs 86.4 us at 32^4).
+template <int SP>
+struct DslashKernelMinBlocks {
+  static constexpr int value = SP == P16 ? 2 : DslashMinBlocks<SP>::value;
+};
 
 
 // ---------------------------------------------------------------- FP64: two threads per site
