@@ -126,7 +126,7 @@ enum {
                                 held by one thread of the dslash, which loads and rebuilds each link
                                 once for all of them (1, 2 or 4; must divide the group K and not
                                 exceed the sites per block); 0 (default) = chosen by the autotuner */
-  WD_OPT_DSLASH_TMA = 16     /* FP32 working precision, lexicographic layout: 1 or 2 makes the
+  WD_OPT_DSLASH_TMA = 16,    /* FP32 working precision, lexicographic layout: 1 or 2 makes the
                                 stand-alone operator (wd_apply, wd_time_dslash) stage the neighbour
                                 spinors in shared memory by TMA bulk tensor copies, in tiles of
                                 Lx x 2 x 2 x 2 (1) or Lx x 4 x 2 x 2 (2) sites, when the FP32 links
@@ -134,6 +134,11 @@ enum {
                                 up to 64 and the other extents divisible by the tile. A copy that
                                 does not land within its wait limit makes the call return
                                 WD_ECUDA. 0 (default): per-thread neighbour loads. Solves ignore it */
+  WD_OPT_DSLASH_SITES_PER_THREAD = 17 /* FP32 / FP16 working precision, lexicographic layout, the
+                                stand-alone dslash launches (wd_apply, the graph and host-loop
+                                solvers): 1 one site per thread; 2 two sites per thread, each hop's
+                                loads for both issued before either's arithmetic (the same bits);
+                                0 (default) chosen with the block size on first use           */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

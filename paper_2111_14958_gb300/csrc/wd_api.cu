@@ -126,6 +126,7 @@ struct wd_ctx {
   int tuned_block[4];         // autotuned single-RHS dslash block size per storage precision
   int tuned_var[4];           // ... and kernel variant (FP64: 1 = two threads per site)
   int force_var;              // WD_OPT_DSLASH_VARIANT: 0 tuned, else 1 + variant (FP64)
+  int force_spt;              // WD_OPT_DSLASH_SITES_PER_THREAD: 0 tuned, else 1 or 2 (FP32 / FP16)
   int loop_block, loop_var;   // launch shape of the persistent FP64 loop (timed on the loop itself)
   bool loop_tuned;
   FieldPtr p2, r2;            // second p and r buffers of the FP64 loop with 4, 8 or 16 lanes per site
@@ -206,6 +207,15 @@ int dslash_variant(const wd_ctx* c, int prec) {
   return c->tuned_block[SP64] > 0 ? c->tuned_var[SP64] : 0;
 }
 
+// FP32 / FP16 single-RHS dslash on the lexicographic layout: sites per thread 1 or 2 (tuned variant
+// 0 or 1 of that precision)
+int dslash_spt(const wd_ctx* c, int prec) {
+  if ((prec != SP32 && prec != SP16) || c->eo) return 1;
+  if (c->force_spt) return c->force_spt;
+  if (c->block_dslash > 0) return 1;
+  return c->tuned_block[prec] > 0 ? 1 + c->tuned_var[prec] : 1;
+}
+
 GaugePtr gauge_for(const wd_ctx* c, int prec) {
   GaugePtr g;
   if (prec == SPDF) {
@@ -240,6 +250,7 @@ cudaError_t dslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fi
   d.red = norm_dst ? red_to(c, slot, norm_dst) : no_red();
   d.block = dslash_block(c, in.prec);
   d.variant = dslash_variant(c, in.prec);
+  d.sites_per_thread = dslash_spt(c, in.prec);
   d.kappa_dev = &c->sc->kappa;
   d.tma = 0;
   d.err = reinterpret_cast<int*>(c->loop_sync + 3);
@@ -817,9 +828,12 @@ wd_status autotune_single(wd_ctx* c) {
     // several warps of the one-thread kernel, which needs the fewest FP64 instructions per site)
     const int cands[15][2] = {{64, 0}, {128, 0}, {256, 0}, {64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2},
                               {256, 2}, {64, 3}, {128, 3}, {256, 3}, {64, 4}, {128, 4}, {256, 4}};
-    const int nc = prec == SP64 && !c->eo ? (c->V <= 65536 ? 15 : 6) : 3;
-    const int saved_force = c->force_var;
+    // FP32 / FP16 (lexicographic): variant 1 = two sites per thread
+    const bool spt = (prec == SP32 || prec == SP16) && !c->eo;
+    const int nc = prec == SP64 && !c->eo ? (c->V <= 65536 ? 15 : 6) : (spt ? 6 : 3);
+    const int saved_force = c->force_var, saved_spt = c->force_spt;
     c->force_var = 0;
+    c->force_spt = 0;
     float best = 1e30f, plain = 1e30f;  // plain: the default shape, 256 threads, one per site
     int best_b = 256, best_v = 0;
     const int reps = prec == SP64 ? 2 : 4;
@@ -848,6 +862,7 @@ wd_status autotune_single(wd_ctx* c) {
       best_v = 0;
     }
     c->force_var = saved_force;
+    c->force_spt = saved_spt;
     tune_store(key, &best_b, &best_v);
     c->tuned_block[prec] = best_b;
     c->tuned_var[prec] = best_v;
@@ -1614,6 +1629,15 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float operator exists on mixed-precision contexts");
       c->apply_df = value != 0.0;
       return WD_OK;
+    case WD_OPT_DSLASH_SITES_PER_THREAD: {
+      const int v = (int)value;
+      if (value != (double)v || v < 0 || v > 2) return fail(WD_EINVAL, "sites per thread must be 0, 1 or 2");
+      if (v == 2 && (c->wprec == SP64 || c->eo))
+        return fail(WD_EINVAL, "two sites per thread serves the FP32 / FP16 operator on the lexicographic layout");
+      c->force_spt = v;
+      destroy_graph(c);
+      return WD_OK;
+    }
     case WD_OPT_DSLASH_TMA: {
       const int v = (int)value;
       if (value != (double)v || v < 0 || v > 2) return fail(WD_EINVAL, "TMA option must be 0, 1 or 2");

@@ -32,6 +32,33 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashKernelMinBlocks<SP>::
   }
 }
 
+// FP32 / FP16 with NS sites per thread: thread t of the grid takes sites s0, s0 + stride, ...,
+// s0 + (NS - 1) stride of each grid-stride step (every load coalesced), hop by hop with all NS
+// sites' loads issued first (dslash_sites).
+template <int SP, bool C12, bool DAG, int EPI, bool NORM, int NS>
+__global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_sites_kernel(const DslashArgs<SP, C12> a) {
+  if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
+  const int V = a.g.V;
+  const int stride = gridDim.x * blockDim.x;
+  double n2 = 0.0;
+  for (int s0 = blockIdx.x * blockDim.x + threadIdx.x; s0 < V; s0 += NS * stride) {
+    int sv[NS];
+    bool live[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      const int si = s0 + i * stride;
+      live[i] = si < V;
+      sv[i] = live[i] ? si : s0;  // a site past the end repeats s0 and is not stored
+    }
+    const double v = dslash_sites<SP, C12, DAG, EPI, NS>(a, sv, live);
+    if (NORM) n2 += v;
+  }
+  if (NORM) {
+    double v[1] = {n2}, tot[1];
+    if (grid_reduce<OpSum, 1>(v, a.partials, a.ticket, tot) && threadIdx.x == 0) *a.result = tot[0];
+  }
+}
+
 template <bool C12, bool DAG, int EPI, bool NORM>
 __global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_pair_kernel(const DslashArgs<P64, C12> a) {
   if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
@@ -103,6 +130,21 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
       return cudaGetLastError();
     }
   }
+  if constexpr (SP == P32 || SP == P16) {
+    if (c.sites_per_thread == 2) {
+      const int units = (c.g.V + 1) / 2;
+      if (c.red.result) {
+        auto k = dslash_sites_kernel<SP, C12, DAG, EPI, true, 2>;
+        const int grid = stride_grid(k, units, c.block);
+        if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
+        k<<<grid, c.block, 0, st>>>(a);
+      } else {
+        auto k = dslash_sites_kernel<SP, C12, DAG, EPI, false, 2>;
+        k<<<stride_grid(k, units, c.block), c.block, 0, st>>>(a);
+      }
+      return cudaGetLastError();
+    }
+  }
   if (c.red.result) {
     auto k = dslash_kernel<SP, C12, DAG, EPI, true>;
     const int grid = stride_grid(k, c.g.V, c.block);
@@ -130,6 +172,9 @@ cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
   }
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32) return cudaErrorInvalidValue;
   if (c.variant != 0 && (c.variant < 0 || c.variant > kMaxDslashVariant || c.in.prec != SP64))
+    return cudaErrorInvalidValue;
+  if (c.sites_per_thread < 0 || c.sites_per_thread > 2 ||
+      (c.sites_per_thread == 2 && c.in.prec != SP32 && c.in.prec != SP16))
     return cudaErrorInvalidValue;
   if (c.in.prec == SPDF) {
     if (c.u.prec != SPDF) return cudaErrorInvalidValue;

@@ -148,6 +148,173 @@ __device__ __forceinline__ void hops_rt(const DslashArgs<SP, C12>& a, R mk, int 
   }
 }
 
+// ---------------------------------------------------------------- several sites per thread
+//
+// FP32 / FP16: the kernel is bound by the latency of its dependent neighbour loads, not by issue.
+// A thread that holds NS sites issues every site's loads of a hop before any site's arithmetic,
+// so each warp keeps NS hops' loads in flight. The per-site arithmetic and its order are those of
+// hop_pair, so the outputs are the same bits.
+
+template <int SP>
+struct HopRaw;
+template <>
+struct HopRaw<P32> {
+  float4 d[6];
+};
+template <>
+struct HopRaw<P16> {
+  uint4 d[3];
+  float nrm;
+};
+
+__device__ __forceinline__ void load_raw(const SpinorRef<P32>& f, int s, int V, HopRaw<P32>& r) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) r.d[j] = __ldg(f.p + (size_t)j * V + s);
+}
+__device__ __forceinline__ void load_raw(const SpinorRef<P16>& f, int s, int V, HopRaw<P16>& r) {
+  r.nrm = __ldg(f.norm + s);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) r.d[j] = __ldg(f.p + (size_t)j * V + s);
+}
+
+// spin_project<MU, S> of a loaded neighbour; returns the hop factor (FP16: times the site's norm)
+template <int MU, int S>
+__device__ __forceinline__ float project_raw(const HopRaw<P32>& r, Cx<float> (&h)[6], float k) {
+  Cx<float> psi[12];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    psi[2 * j] = cx(r.d[j].x, r.d[j].y);
+    psi[2 * j + 1] = cx(r.d[j].z, r.d[j].w);
+  }
+  spin_project<MU, S>(psi, h);
+  return k;
+}
+template <int MU, int S>
+__device__ __forceinline__ float project_raw(const HopRaw<P16>& r, Cx<float> (&h)[6], float k) {
+  uint32_t w[12];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    w[4 * j] = r.d[j].x;
+    w[4 * j + 1] = r.d[j].y;
+    w[4 * j + 2] = r.d[j].z;
+    w[4 * j + 3] = r.d[j].w;
+  }
+  spin_project_f16<MU, S>(w, h);
+  return k * r.nrm;
+}
+
+template <bool C12>
+struct LinkRaw;
+template <>
+struct LinkRaw<true> {
+  float4 d[3];
+};
+template <>
+struct LinkRaw<false> {
+  float2 d[9];
+};
+
+__device__ __forceinline__ void load_link_raw(const GaugeRef<float, true>& g, int mu, int s, int V,
+                                              LinkRaw<true>& l) {
+  const float4* base = g.p + (size_t)mu * 3 * V + s;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) l.d[j] = __ldg(base + (size_t)j * V);
+}
+__device__ __forceinline__ void load_link_raw(const GaugeRef<float, false>& g, int mu, int s, int V,
+                                              LinkRaw<false>& l) {
+  const float2* base = g.p + (size_t)mu * 9 * V + s;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) l.d[k] = __ldg(base + (size_t)k * V);
+}
+__device__ __forceinline__ void unpack_link(const LinkRaw<true>& l, Cx<float> (&u)[9]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    u[2 * j] = cx(l.d[j].x, l.d[j].y);
+    u[2 * j + 1] = cx(l.d[j].z, l.d[j].w);
+  }
+  reconstruct_row2(u);
+}
+__device__ __forceinline__ void unpack_link(const LinkRaw<false>& l, Cx<float> (&u)[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = cx(l.d[k].x, l.d[k].y);
+}
+
+// One hop (DIR 0: forward with U_mu(n); 1: backward with U_mu(n - mu)^dagger) of NS sites.
+template <int MU, int DIR, int S, int NS, int SP, bool C12>
+__device__ __forceinline__ void hop_sites(const DslashArgs<SP, C12>& a, float mk, const int (&s)[NS],
+                                          const int (&c)[NS][4], Cx<float> (&acc)[NS][12]) {
+  const int V = a.g.V;
+  HopRaw<SP> raw[NS];
+  LinkRaw<C12> lk[NS];
+  float k[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const bool wrap = DIR == 0 ? c[i][MU] == a.g.L[MU] - 1 : c[i][MU] == 0;
+    const int nb = DIR == 0 ? (wrap ? s[i] - (a.g.L[MU] - 1) * a.g.stride[MU] : s[i] + a.g.stride[MU])
+                            : (wrap ? s[i] + (a.g.L[MU] - 1) * a.g.stride[MU] : s[i] - a.g.stride[MU]);
+    k[i] = (wrap && a.g.bc[MU] < 0) ? -mk : mk;
+    load_raw(a.in, nb, V, raw[i]);
+    load_link_raw(a.u, MU, DIR == 0 ? s[i] : nb, V, lk[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    Cx<float> h[6], u[9], chi[6];
+    const float kk = project_raw<MU, S>(raw[i], h, k[i]);
+    unpack_link(lk[i], u);
+    if (DIR == 0)
+      su3_mul(u, h, chi);
+    else
+      su3_dag_mul(u, h, chi);
+    spin_reconstruct<MU, S>(acc[i], chi, kk);
+  }
+}
+
+// NS sites of out = D in (or b - D in); sites with live[i] false are computed but not stored.
+// Returns the sum of |out(s)|^2 over the live sites.
+template <int SP, bool C12, bool DAG, int EPI, int NS>
+__device__ __forceinline__ double dslash_sites(const DslashArgs<SP, C12>& a, const int (&s)[NS],
+                                               const bool (&live)[NS]) {
+  const int V = a.g.V;
+  int c[NS][4];
+  Cx<float> acc[NS][12];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    int r = s[i];
+    c[i][0] = r % a.g.L[0];
+    r /= a.g.L[0];
+    c[i][1] = r % a.g.L[1];
+    r /= a.g.L[1];
+    c[i][2] = r % a.g.L[2];
+    c[i][3] = r / a.g.L[2];
+    load_spinor(a.in, s[i], V, acc[i]);
+  }
+  const float mk = a.kappa_dev ? (float)(-*a.kappa_dev) : a.mkappa;
+  constexpr int SF = DAG ? +1 : -1;
+  hop_sites<0, 0, SF, NS>(a, mk, s, c, acc);
+  hop_sites<0, 1, -SF, NS>(a, mk, s, c, acc);
+  hop_sites<1, 0, SF, NS>(a, mk, s, c, acc);
+  hop_sites<1, 1, -SF, NS>(a, mk, s, c, acc);
+  hop_sites<2, 0, SF, NS>(a, mk, s, c, acc);
+  hop_sites<2, 1, -SF, NS>(a, mk, s, c, acc);
+  hop_sites<3, 0, SF, NS>(a, mk, s, c, acc);
+  hop_sites<3, 1, -SF, NS>(a, mk, s, c, acc);
+  double n2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    if (EPI == EPI_RESID) {
+      Cx<float> bv[12];
+      load_spinor(a.b, s[i], V, bv);
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[i][j] = cx<float>(bv[j].re - acc[i][j].re, bv[j].im - acc[i][j].im);
+    }
+    if (live[i]) {
+      store_spinor(a.out, s[i], V, acc[i]);
+      n2 += norm2_site(acc[i]);
+    }
+  }
+  return n2;
+}
+
 // One site of out = D in (or b - D in); returns |out(s)|^2.
 template <int SP, bool C12, bool DAG, int EPI>
 __device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int s) {

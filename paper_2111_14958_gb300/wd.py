@@ -60,6 +60,7 @@ WD_OPT_RESIDUAL_HISTORY = 13
 WD_OPT_APPLY_INNER = 14
 WD_OPT_MULTI_RHS_PER_THREAD = 15
 WD_OPT_DSLASH_TMA = 16
+WD_OPT_DSLASH_SITES_PER_THREAD = 17
 
 
 class WdMultiStats(ctypes.Structure):
@@ -206,11 +207,23 @@ def wd_load_gauge(ctx, U: torch.Tensor, compress12: bool = False, check: bool = 
 
 
 def wd_apply(ctx, inp: torch.Tensor, out: torch.Tensor, dagger: bool = False) -> None:
+    """inp and out: contiguous CUDA tensors of one complex dtype and size (complex64 for FP32
+    contexts, complex128 otherwise; the library checks the context side)."""
+    if (inp.dtype not in (torch.complex64, torch.complex128) or out.dtype != inp.dtype or
+            out.numel() != inp.numel() or not (inp.is_cuda and out.is_cuda) or
+            not (inp.is_contiguous() and out.is_contiguous())):
+        raise ValueError("wd_apply: in and out must be contiguous CUDA tensors of one complex dtype and size")
     _check(_lib.wd_apply(_P(ctx), _P(_ptr(inp)), _P(_ptr(out)), int(bool(dagger))), "wd_apply")
 
 
 def cg_solve(ctx, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
-    """Returns (status, iterations, true relative residual); x is updated in place."""
+    """Returns (status, iterations, true relative residual); x is updated in place. src and x are
+    contiguous complex128 CUDA tensors of one size, for every precision."""
+    for t in (src, x):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("cg_solve: src and x must be contiguous complex128 CUDA tensors")
+    if src.numel() != x.numel():
+        raise ValueError("cg_solve: src and x must have the same size")
     it = _I(0)
     res = _D(0.0)
     st = _lib.cg_solve(_P(ctx), _P(_ptr(src)), _P(_ptr(x)), float(tol), int(maxit), ctypes.byref(it),
@@ -389,13 +402,24 @@ class WilsonDirac:
     def load_gauge(self, U, compress12=False, check=True) -> float:
         return wd_load_gauge(self.ctx, U.contiguous(), compress12, check)
 
+    def _spinor_numel(self):
+        n = 12
+        for d in self.dims:
+            n *= d
+        return n
+
     def apply(self, psi, dagger=False, out=None):
+        want = torch.complex64 if (self.precision & ~WD_EVEN_ODD) == WD_PREC_F32 else torch.complex128
+        if psi.dtype != want or psi.numel() != self._spinor_numel():
+            raise ValueError(f"apply: psi must be a {want} spinor field of shape {self.spinor_shape}")
         if out is None:
             out = torch.empty_like(psi)
         wd_apply(self.ctx, psi.contiguous(), out, dagger)
         return out
 
     def solve(self, src, x0=None, tol=1e-10, maxit=2000):
+        if src.numel() != self._spinor_numel() or (x0 is not None and x0.numel() != src.numel()):
+            raise ValueError(f"solve: src (and x0) must be spinor fields of shape {self.spinor_shape}")
         x = torch.zeros_like(src) if x0 is None else x0.clone()
         status, iters, res = cg_solve(self.ctx, src.contiguous(), x, tol, maxit)
         return x, iters, res, status

@@ -90,3 +90,19 @@ def test_noalloc_rejects_bad_sizes_and_overlap_before_any_device_call(lib):
     assert "overlap" in wd.wd_last_error()
     assert call((4, 4, 4, 4), 0x100000, base + 16, base) == wd.WD_EINVAL
     assert call((4, 4, 4, 4), 0x100000, base, base) == wd.WD_EINVAL
+
+
+def test_binding_rejects_mistyped_fields_before_the_library(lib):
+    """The binding refuses fields the library would read or write past their end: cg_solve takes
+    complex128 for every precision, wd_apply one complex dtype and size on both sides (CPU tensors
+    are refused too, before any device call)."""
+    import torch
+    from paper_2111_14958_gb300 import wd
+    c128 = torch.zeros((2, 2, 2, 2, 4, 3), dtype=torch.complex128)
+    c64 = torch.zeros((2, 2, 2, 2, 4, 3), dtype=torch.complex64)
+    for src, x in ((c64, c64), (c128, c64), (c64, c128), (c128, c128)):   # the last: not on a device
+        with pytest.raises(ValueError):
+            wd.cg_solve(None, src, x, 1e-6, 10)
+    for inp, out in ((c64, c128), (c128, c128[:1]), (c128, c128.clone())):
+        with pytest.raises(ValueError):
+            wd.wd_apply(None, inp, out)
