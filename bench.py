@@ -746,7 +746,7 @@ def profile_case(argv):
                     help="WD_OPT_USE_GRAPH for the solves (0 = plain launches, which ncu lists one by one)")
     ap.add_argument("--tma", type=int, default=0, help="WD_OPT_DSLASH_TMA (FP32 12-real: 1 or 2 = TMA-staged tiles)")
     ap.add_argument("--spt", type=int, default=0,
-                    help="WD_OPT_DSLASH_SITES_PER_THREAD (FP32 / FP16: 1 or 2 sites per thread; 0 = tuned)")
+                    help="WD_OPT_DSLASH_SITES_PER_THREAD (FP32 / FP16: 1 or 2 sites per thread; 0 = 1)")
     ap.add_argument("--apply-inner", action="store_true",
                     help="mixed-precision contexts: wd_apply through the inner FP32 / FP16 operator")
     args = ap.parse_args(argv)

@@ -137,8 +137,9 @@ enum {
   WD_OPT_DSLASH_SITES_PER_THREAD = 17 /* FP32 / FP16 working precision, lexicographic layout, the
                                 stand-alone dslash launches (wd_apply, the graph and host-loop
                                 solvers): 1 one site per thread; 2 two sites per thread, each hop's
-                                loads for both issued before either's arithmetic (the same bits);
-                                0 (default) chosen with the block size on first use           */
+                                loads for both issued before either's arithmetic (the same bits;
+                                measured slower than one site per thread on GB300 at every
+                                volume and link format); 0 (default) = 1                      */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

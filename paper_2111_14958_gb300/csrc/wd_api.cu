@@ -126,7 +126,7 @@ struct wd_ctx {
   int tuned_block[4];         // autotuned single-RHS dslash block size per storage precision
   int tuned_var[4];           // ... and kernel variant (FP64: 1 = two threads per site)
   int force_var;              // WD_OPT_DSLASH_VARIANT: 0 tuned, else 1 + variant (FP64)
-  int force_spt;              // WD_OPT_DSLASH_SITES_PER_THREAD: 0 tuned, else 1 or 2 (FP32 / FP16)
+  int force_spt;              // WD_OPT_DSLASH_SITES_PER_THREAD: 0 or 1 one site per thread, 2 two (FP32 / FP16)
   int loop_block, loop_var;   // launch shape of the persistent FP64 loop (timed on the loop itself)
   bool loop_tuned;
   FieldPtr p2, r2;            // second p and r buffers of the FP64 loop with 4, 8 or 16 lanes per site
@@ -207,13 +207,11 @@ int dslash_variant(const wd_ctx* c, int prec) {
   return c->tuned_block[SP64] > 0 ? c->tuned_var[SP64] : 0;
 }
 
-// FP32 / FP16 single-RHS dslash on the lexicographic layout: sites per thread 1 or 2 (tuned variant
-// 0 or 1 of that precision)
+// FP32 / FP16 single-RHS dslash on the lexicographic layout: sites per thread, 1 unless the option
+// asks for 2 (measured slower at every volume and link format, so the tuner does not try it)
 int dslash_spt(const wd_ctx* c, int prec) {
   if ((prec != SP32 && prec != SP16) || c->eo) return 1;
-  if (c->force_spt) return c->force_spt;
-  if (c->block_dslash > 0) return 1;
-  return c->tuned_block[prec] > 0 ? 1 + c->tuned_var[prec] : 1;
+  return c->force_spt ? c->force_spt : 1;
 }
 
 GaugePtr gauge_for(const wd_ctx* c, int prec) {
@@ -828,9 +826,7 @@ wd_status autotune_single(wd_ctx* c) {
     // several warps of the one-thread kernel, which needs the fewest FP64 instructions per site)
     const int cands[15][2] = {{64, 0}, {128, 0}, {256, 0}, {64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2},
                               {256, 2}, {64, 3}, {128, 3}, {256, 3}, {64, 4}, {128, 4}, {256, 4}};
-    // FP32 / FP16 (lexicographic): variant 1 = two sites per thread
-    const bool spt = (prec == SP32 || prec == SP16) && !c->eo;
-    const int nc = prec == SP64 && !c->eo ? (c->V <= 65536 ? 15 : 6) : (spt ? 6 : 3);
+    const int nc = prec == SP64 && !c->eo ? (c->V <= 65536 ? 15 : 6) : 3;
     const int saved_force = c->force_var, saved_spt = c->force_spt;
     c->force_var = 0;
     c->force_spt = 0;

@@ -642,7 +642,10 @@ __device__ __forceinline__ void su3_dag_mul(const Cx<R> (&u)[9], const Cx<R> (&h
 // (spin 0, spin 1) and imaginary parts accumulate as packed pairs (fma.rn.f32x2, the link entry
 // broadcast to both halves): 36 packed instructions per product instead of 72 scalar ones, on the
 // same FP32 pipe. Each half performs the scalar form's operations in the scalar form's order, so
-// the results are the same bits.
+// the results are the same bits. Used where instruction issue limits the kernel (the multi-RHS
+// dslash, su3_mul_m / su3_dag_mul_m below); the single-RHS kernels are bound by load latency and
+// measured slower with it (pair registers lengthen their live ranges: FP32 18r at 32^4 103 -> 117
+// us), so they keep the scalar form.
 
 typedef unsigned long long f32x2;
 
@@ -675,8 +678,7 @@ __device__ __forceinline__ void spin_pairs(const Cx<float> (&h)[6], f32x2 (&hr)[
   }
 }
 
-template <>
-__device__ __forceinline__ void su3_mul<float>(const Cx<float> (&u)[9], const Cx<float> (&h)[6], Cx<float> (&chi)[6]) {
+__device__ __forceinline__ void su3_mul_x2(const Cx<float> (&u)[9], const Cx<float> (&h)[6], Cx<float> (&chi)[6]) {
   f32x2 hr[3], hi[3];
   spin_pairs(h, hr, hi);
 #pragma unroll
@@ -699,9 +701,8 @@ __device__ __forceinline__ void su3_mul<float>(const Cx<float> (&u)[9], const Cx
   }
 }
 
-template <>
-__device__ __forceinline__ void su3_dag_mul<float>(const Cx<float> (&u)[9], const Cx<float> (&h)[6],
-                                                  Cx<float> (&chi)[6]) {
+__device__ __forceinline__ void su3_dag_mul_x2(const Cx<float> (&u)[9], const Cx<float> (&h)[6],
+                                               Cx<float> (&chi)[6]) {
   f32x2 hr[3], hi[3];
   spin_pairs(h, hr, hi);
 #pragma unroll
@@ -722,6 +723,23 @@ __device__ __forceinline__ void su3_dag_mul<float>(const Cx<float> (&u)[9], cons
     unpk2(re, chi[a].re, chi[3 + a].re);
     unpk2(im, chi[a].im, chi[3 + a].im);
   }
+}
+
+// The issue-bound kernels' SU(3) products: packed pairs for FP32, the scalar form otherwise.
+template <typename R>
+__device__ __forceinline__ void su3_mul_m(const Cx<R> (&u)[9], const Cx<R> (&h)[6], Cx<R> (&chi)[6]) {
+  su3_mul(u, h, chi);
+}
+__device__ __forceinline__ void su3_mul_m(const Cx<float> (&u)[9], const Cx<float> (&h)[6], Cx<float> (&chi)[6]) {
+  su3_mul_x2(u, h, chi);
+}
+template <typename R>
+__device__ __forceinline__ void su3_dag_mul_m(const Cx<R> (&u)[9], const Cx<R> (&h)[6], Cx<R> (&chi)[6]) {
+  su3_dag_mul(u, h, chi);
+}
+__device__ __forceinline__ void su3_dag_mul_m(const Cx<float> (&u)[9], const Cx<float> (&h)[6],
+                                              Cx<float> (&chi)[6]) {
+  su3_dag_mul_x2(u, h, chi);
 }
 
 // ---------------------------------------------------------------- deterministic grid reductions

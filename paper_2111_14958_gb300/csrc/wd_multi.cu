@@ -303,7 +303,7 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r
     Cx<R> h[6], u[9], chi[6];
     const R k = mload_project_hop<MU, SF>(a.in, nb, r, V, N, h, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     load_link(a.u, MU, s, V, u);
-    su3_mul(u, h, chi);
+    su3_mul_m(u, h, chi);
     spin_reconstruct<MU, SF>(acc, chi, k);
   }
   {
@@ -312,7 +312,7 @@ __device__ __forceinline__ void mhop(const MArgs<SP, C12>& a, R mk, int s, int r
     Cx<R> h[6], u[9], chi[6];
     const R k = mload_project_hop<MU, -SF>(a.in, nb, r, V, N, h, (wrap && a.g.bc[MU] < 0) ? -mk : mk);
     load_link(a.u, MU, nb, V, u);
-    su3_dag_mul(u, h, chi);
+    su3_dag_mul_m(u, h, chi);
     spin_reconstruct<MU, -SF>(acc, chi, k);
   }
 }
@@ -336,9 +336,9 @@ __device__ __forceinline__ void mhops_rt(const MArgs<SP, C12>& a, R mk, int s, i
     spin_project_rt(mu, S, psi, h);
     load_link(a.u, mu, dir == 0 ? s : nb, V, u);
     if (dir == 0)
-      su3_mul(u, h, chi);
+      su3_mul_m(u, h, chi);
     else
-      su3_dag_mul(u, h, chi);
+      su3_dag_mul_m(u, h, chi);
     spin_reconstruct_rt(mu, S, acc, chi, k);
   }
 }
@@ -361,7 +361,7 @@ __device__ __forceinline__ void mhop_kt(const MArgs<SP, C12>& a, R mk, int s, in
     for (int j = 0; j < KT; ++j) {
       Cx<R> h[6], chi[6];
       const R k = mload_project_hop<MU, SF>(a.in, nb, r0 + j, V, N, h, k0);
-      su3_mul(u, h, chi);
+      su3_mul_m(u, h, chi);
       spin_reconstruct<MU, SF>(acc[j], chi, k);
     }
   }
@@ -375,7 +375,7 @@ __device__ __forceinline__ void mhop_kt(const MArgs<SP, C12>& a, R mk, int s, in
     for (int j = 0; j < KT; ++j) {
       Cx<R> h[6], chi[6];
       const R k = mload_project_hop<MU, -SF>(a.in, nb, r0 + j, V, N, h, k0);
-      su3_dag_mul(u, h, chi);
+      su3_dag_mul_m(u, h, chi);
       spin_reconstruct<MU, -SF>(acc[j], chi, k);
     }
   }
