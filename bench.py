@@ -745,8 +745,9 @@ def profile_case(argv):
     ap.add_argument("--graph", type=int, default=-1,
                     help="WD_OPT_USE_GRAPH for the solves (0 = plain launches, which ncu lists one by one)")
     ap.add_argument("--tma", type=int, default=0, help="WD_OPT_DSLASH_TMA (FP32 12-real: 1 or 2 = TMA-staged tiles)")
-    ap.add_argument("--spt", type=int, default=0,
-                    help="WD_OPT_DSLASH_SITES_PER_THREAD (FP32 / FP16: 1 or 2 sites per thread; 0 = 1)")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="WD_OPT_DSLASH_SCHEDULE (FP32 / FP16: 1 hop by hop, 2 two sites per thread, "
+                         "3 both hops of a direction loaded together; 0 = tuned)")
     ap.add_argument("--apply-inner", action="store_true",
                     help="mixed-precision contexts: wd_apply through the inner FP32 / FP16 operator")
     args = ap.parse_args(argv)
@@ -774,8 +775,8 @@ def profile_case(argv):
         op.set_option(wd.WD_OPT_DSLASH_VARIANT, args.variant)
     if args.tma:
         op.set_option(wd.WD_OPT_DSLASH_TMA, args.tma)
-    if args.spt:
-        op.set_option(wd.WD_OPT_DSLASH_SITES_PER_THREAD, args.spt)
+    if args.schedule:
+        op.set_option(wd.WD_OPT_DSLASH_SCHEDULE, args.schedule)
     if args.graph >= 0:
         op.set_option(wd.WD_OPT_USE_GRAPH, args.graph)
     if args.launches:

@@ -134,12 +134,14 @@ enum {
                                 up to 64 and the other extents divisible by the tile. A copy that
                                 does not land within its wait limit makes the call return
                                 WD_ECUDA. 0 (default): per-thread neighbour loads. Solves ignore it */
-  WD_OPT_DSLASH_SITES_PER_THREAD = 17 /* FP32 / FP16 working precision, lexicographic layout, the
-                                stand-alone dslash launches (wd_apply, the graph and host-loop
-                                solvers): 1 one site per thread; 2 two sites per thread, each hop's
-                                loads for both issued before either's arithmetic (the same bits;
-                                measured slower than one site per thread on GB300 at every
-                                volume and link format); 0 (default) = 1                      */
+  WD_OPT_DSLASH_SCHEDULE = 17 /* FP32 / FP16 working precision, lexicographic layout, the stand-alone
+                                dslash launches (wd_apply, the graph and host-loop solvers): the
+                                order of its loads. 1: hop by hop; 2: two sites per thread, each
+                                hop's loads for both issued before either's arithmetic; 3: both
+                                hops of each direction loaded before their arithmetic (1 and 3
+                                at three and two blocks per SM). The same bits in every schedule.
+                                0 (default): 1 or 3, timed with the block size on first use
+                                (2 is never chosen: slower wherever measured on GB300)          */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

@@ -126,7 +126,7 @@ struct wd_ctx {
   int tuned_block[4];         // autotuned single-RHS dslash block size per storage precision
   int tuned_var[4];           // ... and kernel variant (FP64: 1 = two threads per site)
   int force_var;              // WD_OPT_DSLASH_VARIANT: 0 tuned, else 1 + variant (FP64)
-  int force_spt;              // WD_OPT_DSLASH_SITES_PER_THREAD: 0 or 1 one site per thread, 2 two (FP32 / FP16)
+  int force_sched;            // WD_OPT_DSLASH_SCHEDULE: 0 tuned, else 1, 2 or 3 (FP32 / FP16 lexicographic)
   int loop_block, loop_var;   // launch shape of the persistent FP64 loop (timed on the loop itself)
   bool loop_tuned;
   FieldPtr p2, r2;            // second p and r buffers of the FP64 loop with 4, 8 or 16 lanes per site
@@ -207,11 +207,14 @@ int dslash_variant(const wd_ctx* c, int prec) {
   return c->tuned_block[SP64] > 0 ? c->tuned_var[SP64] : 0;
 }
 
-// FP32 / FP16 single-RHS dslash on the lexicographic layout: sites per thread, 1 unless the option
-// asks for 2 (measured slower at every volume and link format, so the tuner does not try it)
-int dslash_spt(const wd_ctx* c, int prec) {
+// FP32 / FP16 single-RHS dslash on the lexicographic layout: load schedule 1 (hop by hop), 2 (two
+// sites per thread, never tuned: slower wherever measured) or 3 (both hops of a direction loaded
+// together; tuned variant 1 of that precision)
+int dslash_sched(const wd_ctx* c, int prec) {
   if ((prec != SP32 && prec != SP16) || c->eo) return 1;
-  return c->force_spt ? c->force_spt : 1;
+  if (c->force_sched) return c->force_sched;
+  if (c->block_dslash > 0) return 1;
+  return c->tuned_block[prec] > 0 && c->tuned_var[prec] == 1 ? 3 : 1;
 }
 
 GaugePtr gauge_for(const wd_ctx* c, int prec) {
@@ -248,7 +251,7 @@ cudaError_t dslash(wd_ctx* c, FieldPtr in, FieldPtr out, int dagger, int epi, Fi
   d.red = norm_dst ? red_to(c, slot, norm_dst) : no_red();
   d.block = dslash_block(c, in.prec);
   d.variant = dslash_variant(c, in.prec);
-  d.sites_per_thread = dslash_spt(c, in.prec);
+  d.schedule = dslash_sched(c, in.prec);
   d.kappa_dev = &c->sc->kappa;
   d.tma = 0;
   d.err = reinterpret_cast<int*>(c->loop_sync + 3);
@@ -826,10 +829,12 @@ wd_status autotune_single(wd_ctx* c) {
     // several warps of the one-thread kernel, which needs the fewest FP64 instructions per site)
     const int cands[15][2] = {{64, 0}, {128, 0}, {256, 0}, {64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2},
                               {256, 2}, {64, 3}, {128, 3}, {256, 3}, {64, 4}, {128, 4}, {256, 4}};
-    const int nc = prec == SP64 && !c->eo ? (c->V <= 65536 ? 15 : 6) : 3;
-    const int saved_force = c->force_var, saved_spt = c->force_spt;
+    // FP32 / FP16 (lexicographic): variant 1 = both hops of each direction loaded together
+    const bool sched = (prec == SP32 || prec == SP16) && !c->eo;
+    const int nc = prec == SP64 && !c->eo ? (c->V <= 65536 ? 15 : 6) : (sched ? 6 : 3);
+    const int saved_force = c->force_var, saved_sched = c->force_sched;
     c->force_var = 0;
-    c->force_spt = 0;
+    c->force_sched = 0;
     float best = 1e30f, plain = 1e30f;  // plain: the default shape, 256 threads, one per site
     int best_b = 256, best_v = 0;
     const int reps = prec == SP64 ? 2 : 4;
@@ -858,7 +863,7 @@ wd_status autotune_single(wd_ctx* c) {
       best_v = 0;
     }
     c->force_var = saved_force;
-    c->force_spt = saved_spt;
+    c->force_sched = saved_sched;
     tune_store(key, &best_b, &best_v);
     c->tuned_block[prec] = best_b;
     c->tuned_var[prec] = best_v;
@@ -1625,12 +1630,12 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "double-float operator exists on mixed-precision contexts");
       c->apply_df = value != 0.0;
       return WD_OK;
-    case WD_OPT_DSLASH_SITES_PER_THREAD: {
+    case WD_OPT_DSLASH_SCHEDULE: {
       const int v = (int)value;
-      if (value != (double)v || v < 0 || v > 2) return fail(WD_EINVAL, "sites per thread must be 0, 1 or 2");
-      if (v == 2 && (c->wprec == SP64 || c->eo))
-        return fail(WD_EINVAL, "two sites per thread serves the FP32 / FP16 operator on the lexicographic layout");
-      c->force_spt = v;
+      if (value != (double)v || v < 0 || v > 3) return fail(WD_EINVAL, "dslash schedule must be 0, 1, 2 or 3");
+      if (v >= 2 && (c->wprec == SP64 || c->eo))
+        return fail(WD_EINVAL, "load schedules 2 and 3 serve the FP32 / FP16 operator on the lexicographic layout");
+      c->force_sched = v;
       destroy_graph(c);
       return WD_OK;
     }

@@ -32,31 +32,50 @@ __global__ void __launch_bounds__(kDslashMaxThreads, DslashKernelMinBlocks<SP>::
   }
 }
 
-// FP32 / FP16 with NS sites per thread: thread t of the grid takes sites s0, s0 + stride, ...,
-// s0 + (NS - 1) stride of each grid-stride step (every load coalesced), hop by hop with all NS
-// sites' loads issued first (dslash_sites).
-template <int SP, bool C12, bool DAG, int EPI, bool NORM, int NS>
-__global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_sites_kernel(const DslashArgs<SP, C12> a) {
+// FP32 / FP16 under another load schedule (two blocks per SM, up to 128 registers):
+//   MODE 2: thread t of the grid takes sites s0 and s0 + stride of each grid-stride step (every load
+//           coalesced), hop by hop with both sites' loads issued first (dslash_sites);
+//   MODE 3: one site per grid-stride step, both hops of each direction loaded before their
+//           arithmetic (dslash_site_loaded).
+template <int SP, bool C12, bool DAG, int EPI, bool NORM, int MODE>
+__global__ void __launch_bounds__(kDslashMaxThreads, 2) dslash_sched_kernel(const DslashArgs<SP, C12> a) {
   if (a.skip != nullptr && *a.skip != 0) return;  // uniform over the grid
   const int V = a.g.V;
   const int stride = gridDim.x * blockDim.x;
   double n2 = 0.0;
-  for (int s0 = blockIdx.x * blockDim.x + threadIdx.x; s0 < V; s0 += NS * stride) {
-    int sv[NS];
-    bool live[NS];
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-      const int si = s0 + i * stride;
-      live[i] = si < V;
-      sv[i] = live[i] ? si : s0;  // a site past the end repeats s0 and is not stored
+  if constexpr (MODE == 2) {
+    for (int s0 = blockIdx.x * blockDim.x + threadIdx.x; s0 < V; s0 += 2 * stride) {
+      const int s1 = s0 + stride;
+      const int sv[2] = {s0, s1 < V ? s1 : s0};  // a site past the end repeats s0 and is not stored
+      const bool live[2] = {true, s1 < V};
+      const double v = dslash_sites<SP, C12, DAG, EPI, 2>(a, sv, live);
+      if (NORM) n2 += v;
     }
-    const double v = dslash_sites<SP, C12, DAG, EPI, NS>(a, sv, live);
-    if (NORM) n2 += v;
+  } else {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
+      const double v = dslash_site_loaded<SP, C12, DAG, EPI>(a, s);
+      if (NORM) n2 += v;
+    }
   }
   if (NORM) {
     double v[1] = {n2}, tot[1];
     if (grid_reduce<OpSum, 1>(v, a.partials, a.ticket, tot) && threadIdx.x == 0) *a.result = tot[0];
   }
+}
+
+template <int SP, bool C12, bool DAG, int EPI, int MODE>
+static cudaError_t launch_sched(const DslashCall& c, const DslashArgs<SP, C12>& a, cudaStream_t st) {
+  const int units = MODE == 2 ? (c.g.V + 1) / 2 : c.g.V;
+  if (c.red.result) {
+    auto k = dslash_sched_kernel<SP, C12, DAG, EPI, true, MODE>;
+    const int grid = stride_grid(k, units, c.block);
+    if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
+    k<<<grid, c.block, 0, st>>>(a);
+  } else {
+    auto k = dslash_sched_kernel<SP, C12, DAG, EPI, false, MODE>;
+    k<<<stride_grid(k, units, c.block), c.block, 0, st>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 template <bool C12, bool DAG, int EPI, bool NORM>
@@ -131,19 +150,8 @@ static cudaError_t launch_t(const DslashCall& c, cudaStream_t st) {
     }
   }
   if constexpr (SP == P32 || SP == P16) {
-    if (c.sites_per_thread == 2) {
-      const int units = (c.g.V + 1) / 2;
-      if (c.red.result) {
-        auto k = dslash_sites_kernel<SP, C12, DAG, EPI, true, 2>;
-        const int grid = stride_grid(k, units, c.block);
-        if (!red_fits(c.red, grid)) return cudaErrorInvalidValue;
-        k<<<grid, c.block, 0, st>>>(a);
-      } else {
-        auto k = dslash_sites_kernel<SP, C12, DAG, EPI, false, 2>;
-        k<<<stride_grid(k, units, c.block), c.block, 0, st>>>(a);
-      }
-      return cudaGetLastError();
-    }
+    if (c.schedule == 2) return launch_sched<SP, C12, DAG, EPI, 2>(c, a, st);
+    if (c.schedule == 3) return launch_sched<SP, C12, DAG, EPI, 3>(c, a, st);
   }
   if (c.red.result) {
     auto k = dslash_kernel<SP, C12, DAG, EPI, true>;
@@ -173,8 +181,7 @@ cudaError_t launch_dslash(const DslashCall& c, cudaStream_t st) {
   if (c.block <= 0 || c.block > kDslashMaxThreads || c.block % 32) return cudaErrorInvalidValue;
   if (c.variant != 0 && (c.variant < 0 || c.variant > kMaxDslashVariant || c.in.prec != SP64))
     return cudaErrorInvalidValue;
-  if (c.sites_per_thread < 0 || c.sites_per_thread > 2 ||
-      (c.sites_per_thread == 2 && c.in.prec != SP32 && c.in.prec != SP16))
+  if (c.schedule < 0 || c.schedule > 3 || (c.schedule >= 2 && c.in.prec != SP32 && c.in.prec != SP16))
     return cudaErrorInvalidValue;
   if (c.in.prec == SPDF) {
     if (c.u.prec != SPDF) return cudaErrorInvalidValue;

@@ -117,7 +117,8 @@ struct DslashCall {
   int tma;                  // FP32 12-real, plain epilogue: 0 per-thread loads; 1 / 2 neighbour spinors staged
                             // by TMA in tiles of Lx x 2 x 2 x 2 / Lx x 4 x 2 x 2 sites (wd_tma.cu)
   int* err;                 // tma: set to 1 if a staging wait gave up
-  int sites_per_thread;     // FP32 / FP16: 2 = two sites per thread (dslash_sites_kernel); 0 or 1 = one
+  int schedule;             // FP32 / FP16 load schedule: 0 or 1 hop by hop; 2 two sites per thread;
+                            // 3 both hops of each direction loaded together (dslash_sched_kernel)
 };
 bool tma_dslash_supported(const GeomH& g, int tile);
 cudaError_t launch_dslash_tma(const DslashCall& c, int tile, int* err, cudaStream_t st);

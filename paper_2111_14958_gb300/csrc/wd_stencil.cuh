@@ -148,12 +148,13 @@ __device__ __forceinline__ void hops_rt(const DslashArgs<SP, C12>& a, R mk, int 
   }
 }
 
-// ---------------------------------------------------------------- several sites per thread
+// ---------------------------------------------------------------- load schedules (FP32 / FP16)
 //
 // FP32 / FP16: the kernel is bound by the latency of its dependent neighbour loads, not by issue.
-// A thread that holds NS sites issues every site's loads of a hop before any site's arithmetic,
-// so each warp keeps NS hops' loads in flight. The per-site arithmetic and its order are those of
-// hop_pair, so the outputs are the same bits.
+// Two other schedules keep more loads in flight per thread than hop_pair's one hop at a time: a
+// thread that holds NS sites issues every site's loads of a hop before any site's arithmetic
+// (dslash_sites), or one site's two hops of a direction are loaded together (hop_pair_loaded).
+// The per-site arithmetic and its order are those of hop_pair, so the outputs are the same bits.
 
 template <int SP>
 struct HopRaw;
@@ -313,6 +314,68 @@ __device__ __forceinline__ double dslash_sites(const DslashArgs<SP, C12>& a, con
     }
   }
   return n2;
+}
+
+// Both hops of direction mu for one site, their loads (neighbour spinors and links) issued before
+// either hop's arithmetic: two hops' loads in flight per thread (hop_pair issues them hop by hop).
+template <int MU, int SF, int SP, bool C12>
+__device__ __forceinline__ void hop_pair_loaded(const DslashArgs<SP, C12>& a, float mk, int s, const int (&c)[4],
+                                                Cx<float> (&acc)[12]) {
+  const int V = a.g.V;
+  HopRaw<SP> rf, rb;
+  LinkRaw<C12> lf, lb;
+  const bool wf = c[MU] == a.g.L[MU] - 1, wb = c[MU] == 0;
+  const int nbf = wf ? s - (a.g.L[MU] - 1) * a.g.stride[MU] : s + a.g.stride[MU];
+  const int nbb = wb ? s + (a.g.L[MU] - 1) * a.g.stride[MU] : s - a.g.stride[MU];
+  const float kf = (wf && a.g.bc[MU] < 0) ? -mk : mk, kb = (wb && a.g.bc[MU] < 0) ? -mk : mk;
+  load_raw(a.in, nbf, V, rf);
+  load_link_raw(a.u, MU, s, V, lf);
+  load_raw(a.in, nbb, V, rb);
+  load_link_raw(a.u, MU, nbb, V, lb);
+  {
+    Cx<float> h[6], u[9], chi[6];
+    const float kk = project_raw<MU, SF>(rf, h, kf);
+    unpack_link(lf, u);
+    su3_mul(u, h, chi);
+    spin_reconstruct<MU, SF>(acc, chi, kk);
+  }
+  {
+    Cx<float> h[6], u[9], chi[6];
+    const float kk = project_raw<MU, -SF>(rb, h, kb);
+    unpack_link(lb, u);
+    su3_dag_mul(u, h, chi);
+    spin_reconstruct<MU, -SF>(acc, chi, kk);
+  }
+}
+
+// One site of out = D in (or b - D in) with hop_pair_loaded; returns |out(s)|^2.
+template <int SP, bool C12, bool DAG, int EPI>
+__device__ __forceinline__ double dslash_site_loaded(const DslashArgs<SP, C12>& a, int s) {
+  const int V = a.g.V;
+  int c[4];
+  int r = s;
+  c[0] = r % a.g.L[0];
+  r /= a.g.L[0];
+  c[1] = r % a.g.L[1];
+  r /= a.g.L[1];
+  c[2] = r % a.g.L[2];
+  c[3] = r / a.g.L[2];
+  Cx<float> acc[12];
+  load_spinor(a.in, s, V, acc);
+  const float mk = a.kappa_dev ? (float)(-*a.kappa_dev) : a.mkappa;
+  constexpr int SF = DAG ? +1 : -1;
+  hop_pair_loaded<0, SF>(a, mk, s, c, acc);
+  hop_pair_loaded<1, SF>(a, mk, s, c, acc);
+  hop_pair_loaded<2, SF>(a, mk, s, c, acc);
+  hop_pair_loaded<3, SF>(a, mk, s, c, acc);
+  if (EPI == EPI_RESID) {
+    Cx<float> bv[12];
+    load_spinor(a.b, s, V, bv);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = cx<float>(bv[j].re - acc[j].re, bv[j].im - acc[j].im);
+  }
+  store_spinor(a.out, s, V, acc);
+  return norm2_site(acc);
 }
 
 // One site of out = D in (or b - D in); returns |out(s)|^2.

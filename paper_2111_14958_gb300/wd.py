@@ -60,7 +60,7 @@ WD_OPT_RESIDUAL_HISTORY = 13
 WD_OPT_APPLY_INNER = 14
 WD_OPT_MULTI_RHS_PER_THREAD = 15
 WD_OPT_DSLASH_TMA = 16
-WD_OPT_DSLASH_SITES_PER_THREAD = 17
+WD_OPT_DSLASH_SCHEDULE = 17
 
 
 class WdMultiStats(ctypes.Structure):
