@@ -134,7 +134,7 @@ enum {
                                 up to 64 and the other extents divisible by the tile. A copy that
                                 does not land within its wait limit makes the call return
                                 WD_ECUDA. 0 (default): per-thread neighbour loads. Solves ignore it */
-  WD_OPT_DSLASH_SCHEDULE = 17 /* FP32 / FP16 working precision, lexicographic layout, the stand-alone
+  WD_OPT_DSLASH_SCHEDULE = 17,/* FP32 / FP16 working precision, lexicographic layout, the stand-alone
                                 dslash launches (wd_apply, the graph and host-loop solvers): the
                                 order of its loads. 1: hop by hop; 2: two sites per thread, each
                                 hop's loads for both issued before either's arithmetic; 3: both
@@ -142,6 +142,17 @@ enum {
                                 at three and two blocks per SM). The same bits in every schedule.
                                 0 (default): 1 or 3, timed with the block size on first use
                                 (2 is never chosen: slower wherever measured on GB300)          */
+  WD_OPT_LOOP_TIME_BASIS = 18 /* plain FP64 contexts, lexicographic layout, the persistent CG loop
+                                with one thread per site: 1 (default) runs the loop in the spin
+                                basis psi' = T psi, T = [[1, 1], [-1, 1]] on (upper, lower) spins,
+                                where gamma_t of the chiral basis is diagonal and the spatial
+                                gammas are unchanged (the operator is T D T^-1 of Eq. (1)), so a
+                                time hop needs no spin projection: 813 instead of 849 FP64
+                                operations per site and dslash. x, r, p, s enter the basis in the
+                                loop kernel and leave it when the loop ends; cg_solve's inputs,
+                                outputs, true residual and stopping rule are unchanged, and the
+                                iterates equal the chiral ones up to rounding. 0: the chiral
+                                basis throughout                                                 */
 };
 
 /* Per-solve statistics, filled by wd_get_stats after cg_solve. */

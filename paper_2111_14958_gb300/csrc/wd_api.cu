@@ -96,6 +96,7 @@ struct wd_ctx {
   int block_blas;
   int max_restarts;
   int cg_form;  // 0: CGLS on D^dag D; 1: the paper's CG on D D^dag, carried in x
+  int time_basis;  // WD_OPT_LOOP_TIME_BASIS: persistent FP64 loop in the basis where gamma_t is diagonal
 
   // graph
   cudaGraph_t graph;
@@ -674,6 +675,7 @@ wd_status run_persistent(wd_ctx* c, double* loop_ms) {
   L.max_grid = kLoopMaxGrid;
   L.wait_limit = c->loop_wait_limit;
   L.variant = variant;
+  L.time_basis = variant == 0 && c->wprec == SP64 && !c->eo ? c->time_basis : 0;
   L.t = c->t;
   L.p2 = c->p2;
   L.r2 = c->r2;
@@ -883,7 +885,7 @@ wd_status autotune_loop(wd_ctx* c, bool* ran) {
   NvtxRange nvtx_("wd:autotune_loop");
   *ran = false;
   if (c->loop_tuned || c->block_dslash > 0 || c->force_var) return WD_OK;
-  const TuneKey key = tune_key(c, 2, SP64, 0, 0);
+  const TuneKey key = tune_key(c, 2, SP64, 0, c->time_basis);  // the loop's kernels differ by basis
   int b = 0, v = 0;
   if (tune_lookup(key, &b, &v)) {
     c->loop_block = b;
@@ -1459,6 +1461,7 @@ wd_status wd_create(const int dims[4], double kappa, const int boundary[4], int 
   c->delta = 0.1;  // a reliable update each time |r| has dropped 10x
   c->use_graph = 3;
   c->loop_wait_limit = kLoopWaitLimit;
+  c->time_basis = 1;
   c->block_blas = 256;
   c->max_restarts = 5;
   wd_status st = WD_OK;
@@ -1648,6 +1651,11 @@ wd_status wd_set_option(wd_ctx* c, int key, double value) {
       c->tma = v;
       return WD_OK;
     }
+    case WD_OPT_LOOP_TIME_BASIS:
+      if (value != 0.0 && value != 1.0) return fail(WD_EINVAL, "time-basis option must be 0 or 1");
+      c->time_basis = (int)value;
+      c->loop_tuned = false;  // the loop's launch shape is timed on the kernel it runs
+      return WD_OK;
     case WD_OPT_APPLY_INNER:
       if (!is_mixed(c->precision)) return fail(WD_EINVAL, "the inner operator exists on mixed-precision contexts");
       if (value != 0.0 && value != 1.0) return fail(WD_EINVAL, "apply-inner option must be 0 or 1");
@@ -1981,6 +1989,7 @@ CgLoopCall loop_call(wd_ctx* c, int start_b) {
   L.max_grid = kLoopMaxGrid;
   L.wait_limit = c->loop_wait_limit;
   L.variant = is_mixed(c->precision) ? 0 : loop_variant_of(c);
+  L.time_basis = !is_mixed(c->precision) && L.variant == 0 && c->wprec == SP64 && !c->eo ? c->time_basis : 0;
   L.t = c->t;
   L.p2 = c->p2;
   L.r2 = c->r2;

@@ -131,11 +131,17 @@ struct LoopArgs {
   LoopSync y;
 };
 
-// The dslash phases of the loop: one thread per site, or (FP64) two lanes per site.
-template <int SP, bool C12, bool DAG, int LANES>
+// The dslash phases of the loop: one thread per site, (FP64) two lanes per site, or (FP64, one
+// thread per site, DT) the operator in the basis where gamma_t is diagonal (hop_t_dirac).
+template <int SP, bool C12, bool DAG, int LANES, bool DT = false>
 __device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int n, int t0, int tstep) {
   if constexpr (SP == P64 && LANES == 2) {
     return pair_sites<C12, DAG, EPI_PLAIN>(d);
+  } else if constexpr (DT) {
+    static_assert(SP == P64 && !C12 && LANES == 1, "the time-diagonal basis serves the FP64 one-thread loop");
+    double v = 0.0;
+    for (int i = t0; i < n; i += tstep) v += dslash_site_dirac_t<DAG>(d, i);
+    return v;
   } else {
     double v = 0.0;
     for (int i = t0; i < n; i += tstep) v += dslash_site<SP, C12, DAG, EPI_PLAIN>(d, i);
@@ -159,21 +165,39 @@ struct BatchMinBlocks {
   static constexpr int value = SP == P64 ? 1 : 2;
 };
 
-template <int SP, bool C12, int LANES>
+// DT (FP64, one thread per site): the loop runs in the spin basis psi' = T psi of hop_t_dirac.
+// x, r, p and s enter it in place before the first iteration (a grid barrier follows, since the
+// first dslash reads p at neighbours) and leave it, with q, when the loop ends; each thread
+// transforms only the sites it updates itself, whose last writes are its own. T = sqrt(2) x a
+// unitary, so every norm in the basis is twice the chiral one: gamma and |r|^2 enter doubled and
+// leave halved (exact scalings), alpha and beta are unchanged, and the iterates are T times the
+// chiral ones up to rounding.
+template <int SP, bool C12, int LANES, bool DT = false>
 __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
   typedef typename RealOf<SP>::type R;
   CgScalars* sc = a.sc;
   if (sc->status != ST_RUNNING) return;  // uniform over the grid
   const int n = a.n, V = a.dq.g.V, G = gridDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
-  double gamma = sc->gamma, rr = sc->rr;
-  const double tol2e = sc->tol2 * sc->eta2;
+  const double nscale = DT ? 2.0 : 1.0;  // |T v|^2 / |v|^2
+  double gamma = sc->gamma * nscale, rr = sc->rr * nscale;
+  const double tol2e = sc->tol2 * sc->eta2 * nscale;
   int iter = sc->iter, status = ST_RUNNING;
   const int maxit = sc->maxit;
   double alpha = 0.0, beta = 0.0;
-  for (;;) {
+  bool run = true;
+  if constexpr (DT) {
+    for (int i = t0; i < n; i += tstep) {
+      dirac_t_basis<false>(a.x, i, V);
+      dirac_t_basis<false>(a.r, i, V);
+      dirac_t_basis<false>(a.p, i, V);
+      dirac_t_basis<false>(a.s, i, V);
+    }
+    run = grid_barrier(a.y);  // p in the basis everywhere before D p reads its neighbours
+  }
+  while (run) {
     // q = D p, |q|^2
-    double v = loop_dslash<SP, C12, false, LANES>(a.dq, n, t0, tstep);
+    double v = loop_dslash<SP, C12, false, LANES, DT>(a.dq, n, t0, tstep);
     double qq;
     if (!loop_sum(v, a.partials, a.y, &qq)) break;
     if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
@@ -197,7 +221,7 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
       v += norm2_site(rv);
     }
     if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr / nscale);
     if (!isfinite(rr)) {
       status = ST_BREAKDOWN;
       break;
@@ -206,7 +230,7 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
     // s = D^dag r, |s|^2 (not needed once converged)
     double gnew = 0.0;
     if (!conv) {
-      v = loop_dslash<SP, C12, true, LANES>(a.ds, n, t0, tstep);
+      v = loop_dslash<SP, C12, true, LANES, DT>(a.ds, n, t0, tstep);
       if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
     }
     const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
@@ -250,26 +274,36 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
     }
     if (!grid_barrier(a.y)) break;  // p complete before the next dslash reads its neighbours
   }
+  if constexpr (DT) {
+    // every neighbour read of this launch is behind the last barrier all blocks passed
+    for (int i = t0; i < n; i += tstep) {
+      dirac_t_basis<true>(a.x, i, V);
+      dirac_t_basis<true>(a.r, i, V);
+      dirac_t_basis<true>(a.p, i, V);
+      dirac_t_basis<true>(a.s, i, V);
+      dirac_t_basis<true>(a.q, i, V);
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const bool failed = *(volatile int*)a.y.err != 0;
     sc->status = failed ? ST_BREAKDOWN : status;
     sc->iter = iter;
-    sc->gamma = gamma;
-    sc->rr = rr;
+    sc->gamma = gamma / nscale;
+    sc->rr = rr / nscale;
     sc->alpha = alpha;
     sc->beta = beta;
   }
 }
 
-template <int SP, bool C12, int LANES>
+template <int SP, bool C12, int LANES, bool DT>
 __global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value) cg_loop_kernel(const LoopArgs<SP, C12> a) {
-  cg_loop_body<SP, C12, LANES>(a);
+  cg_loop_body<SP, C12, LANES, DT>(a);
 }
 
-template <int SP, bool C12, int LANES>
+template <int SP, bool C12, int LANES, bool DT>
 __global__ void __launch_bounds__(kDslashMaxThreads, BatchMinBlocks<SP>::value)
     cg_loop_batch_kernel(const __grid_constant__ LoopBatch<LoopArgs<SP, C12>> b) {
-  cg_loop_body<SP, C12, LANES>(b.a[blockIdx.y]);
+  cg_loop_body<SP, C12, LANES, DT>(b.a[blockIdx.y]);
 }
 
 // The inner loop of the mixed-precision solver (FP32 or FP16 vectors, x_lo in FP32) in one
@@ -486,7 +520,7 @@ static bool same_shape(const CgLoopCall* cs, int n) {
     const CgLoopCall &a = cs[0], &b = cs[i];
     if (memcmp(&a.g, &b.g, sizeof(GeomH)) != 0 || a.block != b.block || a.variant != b.variant ||
         a.max_grid != b.max_grid || a.u.prec != b.u.prec || a.u.c12 != b.u.c12 || a.r.prec != b.r.prec ||
-        a.x.prec != b.x.prec)
+        a.x.prec != b.x.prec || a.time_basis != b.time_basis)
       return false;
   }
   return true;
@@ -550,10 +584,10 @@ static LoopArgs<SP, C12> plain_loop_args(const CgLoopCall& c) {
   return a;
 }
 
-template <int SP, bool C12, int LANES>
+template <int SP, bool C12, int LANES, bool DT = false>
 static cudaError_t loop_launch_t(const CgLoopCall* cs, int n, cudaStream_t st) {
-  return loop_launch(cg_loop_kernel<SP, C12, LANES>, cg_loop_batch_kernel<SP, C12, LANES>, plain_loop_args<SP, C12>, cs,
-                     n, LANES * cs[0].g.V, st);
+  return loop_launch(cg_loop_kernel<SP, C12, LANES, DT>, cg_loop_batch_kernel<SP, C12, LANES, DT>,
+                     plain_loop_args<SP, C12>, cs, n, LANES * cs[0].g.V, st);
 }
 
 // ---------------------------------------------------------------- persistent CG loop, FP64 lanes
@@ -701,7 +735,7 @@ cudaError_t launch_cg_loop_n(const CgLoopCall* cs, int n, cudaStream_t st) {
   if (c.r.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;
     switch (c.variant) {
-      case 0: return loop_launch_t<P64, false, 1>(cs, n, st);
+      case 0: return c.time_basis ? loop_launch_t<P64, false, 1, true>(cs, n, st) : loop_launch_t<P64, false, 1>(cs, n, st);
       case 1: return loop_launch_t<P64, false, 2>(cs, n, st);
       case 2: return lanes_loop_launch_t<4>(cs, n, st);
       case 3: return lanes_loop_launch_t<8>(cs, n, st);

@@ -61,6 +61,7 @@ WD_OPT_APPLY_INNER = 14
 WD_OPT_MULTI_RHS_PER_THREAD = 15
 WD_OPT_DSLASH_TMA = 16
 WD_OPT_DSLASH_SCHEDULE = 17
+WD_OPT_LOOP_TIME_BASIS = 18
 
 
 class WdMultiStats(ctypes.Structure):
