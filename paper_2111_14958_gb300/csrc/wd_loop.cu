@@ -1,4 +1,6 @@
 // Persistent cooperative CG loops: plain (lexicographic), mixed-precision inner loop and even-odd.
+#include <type_traits>
+
 #include "wd_stencil.cuh"
 
 namespace wdk {
@@ -64,8 +66,38 @@ __device__ __forceinline__ bool grid_barrier(const LoopSync& y) {
   return ok;
 }
 
+// The sum of G block partials by the first warp, in one fixed order: lane l adds partials l, l + 32,
+// l + 64, ... in turn, then a shuffle tree. AHEAD: up to 256 partials, the lane's loads are issued
+// together ahead of the additions, whose order is kept (same bits). Measured per loop kernel: the
+// one-thread-per-site FP64 loop gains with it (14^4 11.57 -> 11.45 ms, 16^4 22.60 -> 22.41 ms), the
+// FP64 loop with 4 to 16 lanes per site loses (8^4 at 64-thread blocks 3.00 -> 3.10 ms, 4^4 with
+// 8 lanes 1.70 -> 1.78 ms), so the others keep the plain strided sum.
+template <bool AHEAD>
+__device__ __forceinline__ double lane_sum(const double* partials, int G) {
+  double a = 0.0;
+  if constexpr (AHEAD) {
+    constexpr int kAhead = 8;
+    double x[kAhead];
+#pragma unroll
+    for (int k = 0; k < kAhead; ++k) {
+      const int b = threadIdx.x + 32 * k;
+      x[k] = b < G ? __ldcg(partials + b) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < kAhead; ++k)
+      if (threadIdx.x + 32 * k < G) a += x[k];
+    for (int b = threadIdx.x + 32 * kAhead; b < G; b += 32) a += __ldcg(partials + b);
+  } else {
+    for (int b = threadIdx.x; b < G; b += 32) a += __ldcg(partials + b);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+  return a;
+}
+
 // Sum over the grid of one value per thread: block partial, barrier, then every block sums the
 // partials in the same order (lanes stride over them, then a fixed shuffle tree).
+template <bool AHEAD = false>
 __device__ __forceinline__ bool loop_sum(double v, double* partials, const LoopSync& y, double* out) {
   __shared__ double smem[32];
   __shared__ double total;
@@ -74,10 +106,7 @@ __device__ __forceinline__ bool loop_sum(double v, double* partials, const LoopS
   if (threadIdx.x == 0) partials[blockIdx.x] = w[0];  // released by the barrier's arrival
   if (!grid_barrier(y)) return false;
   if (threadIdx.x < 32) {
-    double a = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) a += __ldcg(partials + b);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    const double a = lane_sum<AHEAD>(partials, gridDim.x);
     if (threadIdx.x == 0) total = a;
   }
   __syncthreads();
@@ -140,13 +169,26 @@ __device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int 
   } else if constexpr (DT) {
     static_assert(SP == P64 && !C12 && LANES == 1, "the time-diagonal basis serves the FP64 one-thread loop");
     double v = 0.0;
-    for (int i = t0; i < n; i += tstep) v += dslash_site_dirac_t<DAG>(d, i);
+    for (int i = t0; i < n; i += tstep) {
+      Cx<double> acc[12];
+      v += dslash_site_dirac_t<DAG>(d, i, acc);
+    }
     return v;
   } else {
     double v = 0.0;
     for (int i = t0; i < n; i += tstep) v += dslash_site<SP, C12, DAG, EPI_PLAIN>(d, i);
     return v;
   }
+}
+
+// One site of a dslash phase whose output stays in registers (the loop with one site per thread).
+template <int SP, bool C12, bool DAG, bool DT>
+__device__ __forceinline__ double loop_dslash_site(const DslashArgs<SP, C12>& d, int i,
+                                                   Cx<typename RealOf<SP>::type> (&out)[12]) {
+  if constexpr (DT)
+    return dslash_site_dirac_t<DAG>(d, i, out);
+  else
+    return dslash_site_out<SP, C12, DAG, EPI_PLAIN>(d, i, out);
 }
 
 // A batch of independent loops in one cooperative launch: blockIdx.y selects the problem, whose
@@ -179,6 +221,7 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
   if (sc->status != ST_RUNNING) return;  // uniform over the grid
   const int n = a.n, V = a.dq.g.V, G = gridDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  constexpr bool AH = SP == P64 && LANES == 1;  // see lane_sum
   const double nscale = DT ? 2.0 : 1.0;  // |T v|^2 / |v|^2
   double gamma = sc->gamma * nscale, rr = sc->rr * nscale;
   const double tol2e = sc->tol2 * sc->eta2 * nscale;
@@ -195,84 +238,113 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
     }
     run = grid_barrier(a.y);  // p in the basis everywhere before D p reads its neighbours
   }
-  while (run) {
-    // q = D p, |q|^2
-    double v = loop_dslash<SP, C12, false, LANES, DT>(a.dq, n, t0, tstep);
-    double qq;
-    if (!loop_sum(v, a.partials, a.y, &qq)) break;
-    if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
-      status = ST_BREAKDOWN;
-      break;
-    }
-    alpha = gamma / qq;
-    const R ar = (R)alpha;
-    // r -= alpha q, |r|^2
-    v = 0.0;
-    for (int i = t0; i < n; i += tstep) {
-      Cx<R> rv[12], qv[12];
-      load_spinor(a.r, i, V, rv);
-      load_spinor(a.q, i, V, qv);
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        rv[c].re = fma(-ar, qv[c].re, rv[c].re);
-        rv[c].im = fma(-ar, qv[c].im, rv[c].im);
+  // One site per thread (FP64, the grid covers the lattice): the dslash outputs q and s stay in
+  // registers for the vector phase after the next barrier instead of being read back from the L2
+  // (they are still stored: the fields are the loop's state). The arithmetic and its order are those
+  // of the general path, and FP64 fields store the register values unrounded, so both give the same
+  // bits. Loading r, x and p before the barrier as well measured slower (spills at 255 registers).
+  // The two paths are separate instantiations, so neither keeps the other's values live.
+  auto iterate = [&](auto one_tag) {
+    constexpr bool ONE = decltype(one_tag)::value;
+    const bool mine = t0 < n;
+    while (run) {
+      // q = D p, |q|^2
+      Cx<R> qv[12];
+      double v = 0.0;
+      if constexpr (ONE) {
+        if (mine) v = loop_dslash_site<SP, C12, false, DT>(a.dq, t0, qv);
+      } else {
+        v = loop_dslash<SP, C12, false, LANES, DT>(a.dq, n, t0, tstep);
       }
-      store_spinor(a.r, i, V, rv);
-      v += norm2_site(rv);
-    }
-    if (!loop_sum(v, a.partials + G, a.y, &rr)) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr / nscale);
-    if (!isfinite(rr)) {
-      status = ST_BREAKDOWN;
-      break;
-    }
-    const bool conv = rr <= tol2e;
-    // s = D^dag r, |s|^2 (not needed once converged)
-    double gnew = 0.0;
-    if (!conv) {
-      v = loop_dslash<SP, C12, true, LANES, DT>(a.ds, n, t0, tstep);
-      if (!loop_sum(v, a.partials + 2 * G, a.y, &gnew)) break;
-    }
-    const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
-    beta = do_p ? gnew / gamma : 0.0;
-    const R br = (R)beta;
-    // x += alpha p; p = s + beta p
-    for (int i = t0; i < n; i += tstep) {
-      Cx<R> xv[12], pv[12];
-      load_spinor(a.x, i, V, xv);
-      load_spinor(a.p, i, V, pv);
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        xv[c].re = fma(ar, pv[c].re, xv[c].re);
-        xv[c].im = fma(ar, pv[c].im, xv[c].im);
+      double qq;
+      if (!loop_sum<AH>(v, a.partials, a.y, &qq)) break;
+      if (!(qq > 0.0 && isfinite(qq) && isfinite(gamma))) {
+        status = ST_BREAKDOWN;
+        break;
       }
-      store_spinor(a.x, i, V, xv);
-      if (do_p) {
-        Cx<R> sv[12];
-        load_spinor(a.s, i, V, sv);
+      alpha = gamma / qq;
+      const R ar = (R)alpha;
+      // r -= alpha q, |r|^2
+      v = 0.0;
+      for (int i = t0; i < n; i += tstep) {
+        Cx<R> rv[12];
+        load_spinor(a.r, i, V, rv);
+        if constexpr (!ONE) load_spinor(a.q, i, V, qv);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-          pv[c].re = fma(br, pv[c].re, sv[c].re);
-          pv[c].im = fma(br, pv[c].im, sv[c].im);
+          rv[c].re = fma(-ar, qv[c].re, rv[c].re);
+          rv[c].im = fma(-ar, qv[c].im, rv[c].im);
         }
-        store_spinor(a.p, i, V, pv);
+        store_spinor(a.r, i, V, rv);
+        v += norm2_site(rv);
       }
+      if (!loop_sum<AH>(v, a.partials + G, a.y, &rr)) break;
+      if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rr / nscale);
+      if (!isfinite(rr)) {
+        status = ST_BREAKDOWN;
+        break;
+      }
+      const bool conv = rr <= tol2e;
+      // s = D^dag r, |s|^2 (not needed once converged)
+      double gnew = 0.0;
+      Cx<R> sv[12];
+      if (!conv) {
+        if constexpr (ONE) {
+          v = 0.0;
+          if (mine) v = loop_dslash_site<SP, C12, true, DT>(a.ds, t0, sv);
+        } else {
+          v = loop_dslash<SP, C12, true, LANES, DT>(a.ds, n, t0, tstep);
+        }
+        if (!loop_sum<AH>(v, a.partials + 2 * G, a.y, &gnew)) break;
+      }
+      const bool do_p = !conv && isfinite(gnew) && gamma > 0.0;
+      beta = do_p ? gnew / gamma : 0.0;
+      const R br = (R)beta;
+      // x += alpha p; p = s + beta p
+      for (int i = t0; i < n; i += tstep) {
+        Cx<R> xv[12], pv[12];
+        load_spinor(a.x, i, V, xv);
+        load_spinor(a.p, i, V, pv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          xv[c].re = fma(ar, pv[c].re, xv[c].re);
+          xv[c].im = fma(ar, pv[c].im, xv[c].im);
+        }
+        store_spinor(a.x, i, V, xv);
+        if (do_p) {
+          if constexpr (!ONE) load_spinor(a.s, i, V, sv);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            pv[c].re = fma(br, pv[c].re, sv[c].re);
+            pv[c].im = fma(br, pv[c].im, sv[c].im);
+          }
+          store_spinor(a.p, i, V, pv);
+        }
+      }
+      iter += 1;
+      if (conv) {
+        status = ST_CONVERGED;
+        break;
+      }
+      if (!do_p) {
+        status = ST_BREAKDOWN;
+        break;
+      }
+      gamma = gnew;
+      if (iter >= maxit) {
+        status = ST_MAXIT;
+        break;
+      }
+      if (!grid_barrier(a.y)) break;  // p complete before the next dslash reads its neighbours
     }
-    iter += 1;
-    if (conv) {
-      status = ST_CONVERGED;
-      break;
-    }
-    if (!do_p) {
-      status = ST_BREAKDOWN;
-      break;
-    }
-    gamma = gnew;
-    if (iter >= maxit) {
-      status = ST_MAXIT;
-      break;
-    }
-    if (!grid_barrier(a.y)) break;  // p complete before the next dslash reads its neighbours
+  };
+  if constexpr (SP == P64 && LANES == 1) {
+    if (n <= tstep)
+      iterate(std::true_type{});
+    else
+      iterate(std::false_type{});
+  } else {
+    iterate(std::false_type{});
   }
   if constexpr (DT) {
     // every neighbour read of this launch is behind the last barrier all blocks passed

@@ -378,9 +378,10 @@ __device__ __forceinline__ double dslash_site_loaded(const DslashArgs<SP, C12>& 
   return norm2_site(acc);
 }
 
-// One site of out = D in (or b - D in); returns |out(s)|^2.
+// One site of out = D in (or b - D in); returns |out(s)|^2 and leaves the stored value in acc.
 template <int SP, bool C12, bool DAG, int EPI>
-__device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int s) {
+__device__ __forceinline__ double dslash_site_out(const DslashArgs<SP, C12>& a, int s,
+                                                  Cx<typename RealOf<SP>::type> (&acc)[12]) {
   typedef typename RealOf<SP>::type R;
   const int V = a.g.V;
   int c[4];
@@ -394,7 +395,6 @@ __device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int 
     c[3] = r / a.g.L[2];
   }
   const R mk = a.kappa_dev ? (R)(-*a.kappa_dev) : a.mkappa;
-  Cx<R> acc[12];
   load_spinor(a.in, s, V, acc);
   // D: forward (1 - gamma), backward (1 + gamma); D^dagger: the reverse
   constexpr int SF = DAG ? +1 : -1;
@@ -414,6 +414,13 @@ __device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int 
   }
   store_spinor(a.out, s, V, acc);
   return norm2_site(acc);
+}
+
+// One site of out = D in (or b - D in); returns |out(s)|^2.
+template <int SP, bool C12, bool DAG, int EPI>
+__device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int s) {
+  Cx<typename RealOf<SP>::type> acc[12];
+  return dslash_site_out<SP, C12, DAG, EPI>(a, s, acc);
 }
 
 // ---------------------------------------------------------------- FP64: time hops in the Dirac basis
@@ -472,9 +479,10 @@ __device__ __forceinline__ void hop_t_dirac(const DslashArgs<P64, false>& a, dou
   }
 }
 
-// One site of out' = D' in' (the FP64 operator in the basis above, 18-real links); returns |out'|^2.
+// One site of out' = D' in' (the FP64 operator in the basis above, 18-real links); returns |out'|^2
+// and leaves the stored value in acc.
 template <bool DAG>
-__device__ __forceinline__ double dslash_site_dirac_t(const DslashArgs<P64, false>& a, int s) {
+__device__ __forceinline__ double dslash_site_dirac_t(const DslashArgs<P64, false>& a, int s, Cx<double> (&acc)[12]) {
   const int V = a.g.V;
   int c[4];
   {
@@ -487,7 +495,6 @@ __device__ __forceinline__ double dslash_site_dirac_t(const DslashArgs<P64, fals
     c[3] = r / a.g.L[2];
   }
   const double mk = a.kappa_dev ? -*a.kappa_dev : a.mkappa;
-  Cx<double> acc[12];
   load_spinor(a.in, s, V, acc);
   constexpr int SF = DAG ? +1 : -1;
   hop_pair<0, SF>(a, mk, s, c, acc);

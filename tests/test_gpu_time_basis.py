@@ -12,6 +12,7 @@ the same loop in the chiral basis (same iterations within one).
 """
 import numpy as np
 import pytest
+import torch
 
 from oracle import cg as ocg
 from tests.gpu_util import fields, rel, require_gpu, to_dev, to_np
@@ -94,3 +95,35 @@ def test_basis_solves_repeat_bitwise_and_the_option_is_checked():
         with pytest.raises(wd.WdError):
             op.set_option(wd.WD_OPT_LOOP_TIME_BASIS, bad)
     op.close()
+
+
+def test_batched_loops_in_the_basis_equal_solves_alone_bitwise():
+    """cg_solve_batch runs each problem's loop on its own blocks of one launch: with the basis on,
+    every result equals its solve alone bit for bit, and meets the tolerance by the oracle."""
+    wd = require_gpu()
+    dims = (6, 4, 4, 8)
+    bc = (1, 1, 1, -1)
+    probs = [fields(dims, gseed=10 + i, sseed=20 + i) for i in range(3)]
+
+    def make(U):
+        op = wd.WilsonDirac(dims, 0.12, bc, wd.WD_PREC_F64)
+        op.load_gauge(to_dev(U))
+        op.set_option(wd.WD_OPT_DSLASH_VARIANT, 1)
+        op.set_option(wd.WD_OPT_LOOP_TIME_BASIS, 1)
+        return op
+
+    ops = [make(U) for U, _ in probs]
+    srcs = [to_dev(eta) for _, eta in probs]
+    xs = [torch.zeros_like(s) for s in srcs]
+    st, iters, res, sts = wd.cg_solve_batch([o.ctx for o in ops], srcs, xs, [1e-10] * 3, 4000)
+    modes = [(o.stats()["loop_mode"], o.stats()["loop_lanes"]) for o in ops]
+    for o in ops:
+        o.close()
+    assert st == wd.WD_OK and all(s == wd.WD_OK for s in sts) and all(m == (2, 1) for m in modes)
+    for i, (U, eta) in enumerate(probs):
+        op = make(U)
+        xa, ia, ra, sa = op.solve(to_dev(eta), tol=1e-10)
+        op.close()
+        assert sa == wd.WD_OK and ia == iters[i] and ra == res[i]
+        assert np.array_equal(to_np(xs[i]), to_np(xa)), i
+        assert ocg.true_residual(U, eta, to_np(xa), 0.12, bc) <= 1e-10
