@@ -147,9 +147,11 @@ enum {
                                 basis psi' = T psi, T = [[1, 1], [-1, 1]] on (upper, lower) spins,
                                 where gamma_t of the chiral basis is diagonal and the spatial
                                 gammas are unchanged (the operator is T D T^-1 of Eq. (1)), so a
-                                time hop needs no spin projection: 813 instead of 849 FP64
-                                operations per site and dslash. x, r, p, s enter the basis in the
-                                loop kernel and leave it when the loop ends; cg_solve's inputs,
+                                time hop needs no spin projection, and with the time links
+                                pre-scaled by the loop (2 x -kappa x the boundary phase, in a
+                                buffer of the context) no separate scaling either: 789 instead of
+                                849 FP64 operations per site and dslash. x, r, p, s enter the
+                                basis in the loop kernel and leave it when the loop ends; cg_solve's inputs,
                                 outputs, true residual and stopping rule are unchanged, and the
                                 iterates equal the chiral ones up to rounding. 0: the chiral
                                 basis throughout                                                 */

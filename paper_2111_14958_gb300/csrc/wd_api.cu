@@ -131,6 +131,7 @@ struct wd_ctx {
   int loop_block, loop_var;   // launch shape of the persistent FP64 loop (timed on the loop itself)
   bool loop_tuned;
   FieldPtr p2, r2;            // second p and r buffers of the FP64 loop with 4, 8 or 16 lanes per site
+  FieldPtr tl;                // FP64 loop in the time-diagonal basis: pre-scaled time links (in an FP64 field)
   int tma;                    // WD_OPT_DSLASH_TMA: stand-alone FP32 12-real operator staged by TMA (tile 1 or 2)
   bool standalone;            // the current operator call is wd_apply / wd_time_dslash (not a solve)
   wd_multi_stats mstats;
@@ -651,10 +652,22 @@ wd_status ensure_lane_buffers(wd_ctx* c) {
   return WD_OK;
 }
 
+// Whether the plain FP64 loop of this launch shape runs in the time-diagonal basis.
+bool loop_time_basis(const wd_ctx* c, int variant) {
+  return !is_mixed(c->precision) && variant == 0 && c->wprec == SP64 && !c->eo && c->time_basis;
+}
+
+// The loop in the time-diagonal basis keeps its pre-scaled time links (9 of an FP64 field's 12
+// complex components per site) in a buffer of the context, rewritten by every launch.
+wd_status ensure_time_links(wd_ctx* c) {
+  return c->tl.p ? WD_OK : alloc_field(c, &c->tl, SP64);
+}
+
 wd_status run_persistent(wd_ctx* c, double* loop_ms) {
   const int variant = loop_variant_of(c);
   wd_status st;
   if (variant >= 2 && (st = ensure_lane_buffers(c)) != WD_OK) return st;
+  if (loop_time_basis(c, variant) && (st = ensure_time_links(c)) != WD_OK) return st;
   WD_CUDA(plain_prologue(c, c->stream, 0, 0));
   CgLoopCall L;
   memset(&L, 0, sizeof(L));
@@ -675,10 +688,11 @@ wd_status run_persistent(wd_ctx* c, double* loop_ms) {
   L.max_grid = kLoopMaxGrid;
   L.wait_limit = c->loop_wait_limit;
   L.variant = variant;
-  L.time_basis = variant == 0 && c->wprec == SP64 && !c->eo ? c->time_basis : 0;
+  L.time_basis = loop_time_basis(c, variant) ? 1 : 0;
   L.t = c->t;
   L.p2 = c->p2;
   L.r2 = c->r2;
+  L.tl = c->tl;
   WD_CUDA(cudaEventRecord(c->ev0, c->stream));
   WD_CUDA(c->eo ? launch_cg_eo_loop(L, c->stream) : launch_cg_loop(L, c->stream));
   WD_CUDA(cudaEventRecord(c->ev1, c->stream));
@@ -1550,6 +1564,7 @@ void wd_destroy(wd_ctx* c) {
   free_field(&c->etadf);
   free_field(&c->tdf);
   free_field(&c->p2);
+  free_field(&c->tl);
   free_field(&c->r2);
   if (c->gauge_df) cudaFree(c->gauge_df);
   if (c->gauge64) cudaFree(c->gauge64);
@@ -1989,10 +2004,11 @@ CgLoopCall loop_call(wd_ctx* c, int start_b) {
   L.max_grid = kLoopMaxGrid;
   L.wait_limit = c->loop_wait_limit;
   L.variant = is_mixed(c->precision) ? 0 : loop_variant_of(c);
-  L.time_basis = !is_mixed(c->precision) && L.variant == 0 && c->wprec == SP64 && !c->eo ? c->time_basis : 0;
+  L.time_basis = loop_time_basis(c, L.variant) ? 1 : 0;
   L.t = c->t;
   L.p2 = c->p2;
   L.r2 = c->r2;
+  L.tl = c->tl;
   L.start_b = start_b;
   return L;
 }
@@ -2039,6 +2055,7 @@ wd_status batch_pass(wd_ctx* const* cs, int n, cudaStream_t st, double* loop_ms)
   for (int i = 0; i < n; ++i) {
     wd_ctx* c = cs[i];
     if (!mixed && loop_variant_of(c) >= 2 && (r = ensure_lane_buffers(c)) != WD_OK) return r;
+    if (loop_time_basis(c, loop_variant_of(c)) && (r = ensure_time_links(c)) != WD_OK) return r;
     WD_CUDA(mixed ? mixed_prologue(c, st, 0, 0) : plain_prologue(c, st, 0, 0));
     calls[i] = loop_call(c, 0);
   }

@@ -583,7 +583,35 @@ __device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6]
   }
 }
 
-// p = t + U^dag h (the product accumulated onto t: fused multiply-adds only)
+// p = t + U h (the product accumulated onto t: fused multiply-adds only). p may be t itself: each
+// output entry reads only its own entry of t.
+template <typename R>
+__device__ __forceinline__ void su3_mul_add(const Cx<R> (&u)[9], const Cx<R> (&h)[6], const Cx<R> (&t)[6],
+                                            Cx<R> (&p)[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const Cx<R> u0 = u[3 * a], u1 = u[3 * a + 1], u2 = u[3 * a + 2];
+      const Cx<R> h0 = h[3 * sp], h1 = h[3 * sp + 1], h2 = h[3 * sp + 2];
+      R re = madd(u0.re, h0.re, t[3 * sp + a].re);
+      re = madd(-u0.im, h0.im, re);
+      re = madd(u1.re, h1.re, re);
+      re = madd(-u1.im, h1.im, re);
+      re = madd(u2.re, h2.re, re);
+      re = madd(-u2.im, h2.im, re);
+      R im = madd(u0.re, h0.im, t[3 * sp + a].im);
+      im = madd(u0.im, h0.re, im);
+      im = madd(u1.re, h1.im, im);
+      im = madd(u1.im, h1.re, im);
+      im = madd(u2.re, h2.im, im);
+      im = madd(u2.im, h2.re, im);
+      p[3 * sp + a] = cx<R>(re, im);
+    }
+  }
+}
+
+// p = t + U^dag h (the product accumulated onto t: fused multiply-adds only; p may be t itself)
 template <typename R>
 __device__ __forceinline__ void su3_dag_mul_add(const Cx<R> (&u)[9], const Cx<R> (&h)[6], const Cx<R> (&t)[6],
                                                 Cx<R> (&p)[6]) {

@@ -147,6 +147,7 @@ struct CgLoopCall {
   int start_b;  // mixed loop: resume at the D^dag half of an iteration (after a reliable update)
   FieldPtr t;   // even-odd loop: the odd-site temporary
   FieldPtr p2, r2;  // FP64 loop with 4, 8 or 16 lanes per site: second buffers of p and r
+  FieldPtr tl;      // FP64 loop in the time-diagonal basis: pre-scaled time links (double2 [9][V])
   long long wait_limit;  // grid-barrier polls (64 ns sleep each) before a wait gives up
 };
 constexpr long long kLoopWaitLimit = 1LL << 26;  // about 4 s

@@ -154,6 +154,7 @@ struct LoopArgs {
   DslashArgs<SP, C12> dq;  // q = D p
   DslashArgs<SP, C12> ds;  // s = D^dag r
   SpinorRef<SP> x, r, p, q, s;
+  double2* tl;             // FP64 loop in the time-diagonal basis: pre-scaled time links [9][V]
   int n;                   // sites
   CgScalars* sc;
   double* partials;        // 3 x gridDim.x
@@ -163,7 +164,8 @@ struct LoopArgs {
 // The dslash phases of the loop: one thread per site, (FP64) two lanes per site, or (FP64, one
 // thread per site, DT) the operator in the basis where gamma_t is diagonal (hop_t_dirac).
 template <int SP, bool C12, bool DAG, int LANES, bool DT = false>
-__device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int n, int t0, int tstep) {
+__device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, const double2* tl, int n, int t0,
+                                              int tstep) {
   if constexpr (SP == P64 && LANES == 2) {
     return pair_sites<C12, DAG, EPI_PLAIN>(d);
   } else if constexpr (DT) {
@@ -171,7 +173,7 @@ __device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int 
     double v = 0.0;
     for (int i = t0; i < n; i += tstep) {
       Cx<double> acc[12];
-      v += dslash_site_dirac_t<DAG>(d, i, acc);
+      v += dslash_site_dirac_t<DAG>(d, tl, i, acc);
     }
     return v;
   } else {
@@ -183,10 +185,10 @@ __device__ __forceinline__ double loop_dslash(const DslashArgs<SP, C12>& d, int 
 
 // One site of a dslash phase whose output stays in registers (the loop with one site per thread).
 template <int SP, bool C12, bool DAG, bool DT>
-__device__ __forceinline__ double loop_dslash_site(const DslashArgs<SP, C12>& d, int i,
+__device__ __forceinline__ double loop_dslash_site(const DslashArgs<SP, C12>& d, const double2* tl, int i,
                                                    Cx<typename RealOf<SP>::type> (&out)[12]) {
   if constexpr (DT)
-    return dslash_site_dirac_t<DAG>(d, i, out);
+    return dslash_site_dirac_t<DAG>(d, tl, i, out);
   else
     return dslash_site_out<SP, C12, DAG, EPI_PLAIN>(d, i, out);
 }
@@ -235,8 +237,9 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
       dirac_t_basis<false>(a.r, i, V);
       dirac_t_basis<false>(a.p, i, V);
       dirac_t_basis<false>(a.s, i, V);
+      scale_time_link(a.dq, a.tl, i);
     }
-    run = grid_barrier(a.y);  // p in the basis everywhere before D p reads its neighbours
+    run = grid_barrier(a.y);  // p and the time links everywhere before D p reads its neighbours
   }
   // One site per thread (FP64, the grid covers the lattice): the dslash outputs q and s stay in
   // registers for the vector phase after the next barrier instead of being read back from the L2
@@ -252,9 +255,9 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
       Cx<R> qv[12];
       double v = 0.0;
       if constexpr (ONE) {
-        if (mine) v = loop_dslash_site<SP, C12, false, DT>(a.dq, t0, qv);
+        if (mine) v = loop_dslash_site<SP, C12, false, DT>(a.dq, a.tl, t0, qv);
       } else {
-        v = loop_dslash<SP, C12, false, LANES, DT>(a.dq, n, t0, tstep);
+        v = loop_dslash<SP, C12, false, LANES, DT>(a.dq, a.tl, n, t0, tstep);
       }
       double qq;
       if (!loop_sum<AH>(v, a.partials, a.y, &qq)) break;
@@ -291,9 +294,9 @@ __device__ __forceinline__ void cg_loop_body(const LoopArgs<SP, C12>& a) {
       if (!conv) {
         if constexpr (ONE) {
           v = 0.0;
-          if (mine) v = loop_dslash_site<SP, C12, true, DT>(a.ds, t0, sv);
+          if (mine) v = loop_dslash_site<SP, C12, true, DT>(a.ds, a.tl, t0, sv);
         } else {
-          v = loop_dslash<SP, C12, true, LANES, DT>(a.ds, n, t0, tstep);
+          v = loop_dslash<SP, C12, true, LANES, DT>(a.ds, a.tl, n, t0, tstep);
         }
         if (!loop_sum<AH>(v, a.partials + 2 * G, a.y, &gnew)) break;
       }
@@ -647,6 +650,7 @@ static LoopArgs<SP, C12> plain_loop_args(const CgLoopCall& c) {
   a.p = make_ref<SP>(c.p, c.g.V);
   a.q = make_ref<SP>(c.q, c.g.V);
   a.s = make_ref<SP>(c.s, c.g.V);
+  a.tl = reinterpret_cast<double2*>(c.tl.p);
   a.n = c.g.V;
   a.sc = c.sc;
   a.partials = c.partials;
@@ -803,6 +807,7 @@ cudaError_t launch_cg_loop_n(const CgLoopCall* cs, int n, cudaStream_t st) {
     if (d.r.prec == SP64 && d.variant >= 2 &&
         (!d.p2.p || !d.r2.p || d.p2.prec != SP64 || d.r2.prec != SP64))
       return cudaErrorInvalidValue;
+    if (d.r.prec == SP64 && d.variant == 0 && d.time_basis && !d.tl.p) return cudaErrorInvalidValue;
   }
   if (c.r.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;

@@ -54,8 +54,8 @@ size_t request_bytes(const int d[4], int precision) {
   precision &= ~WD_EVEN_ODD;
   const size_t f64 = V * 192, f32 = V * 96, f16 = V * 52;
   switch (precision) {
-    // FP64: + two more p, r buffers of the small-volume loop
-    case WD_PREC_F64: return extra + V * 576 + 11 * f64 + 2 * f64 + (V / 32 + 64) * 8 * 12;
+    // FP64: + two more p, r buffers of the small-volume loop and the loop's pre-scaled time links
+    case WD_PREC_F64: return extra + V * 576 + 11 * f64 + 3 * f64 + (V / 32 + 64) * 8 * 12;
     case WD_PREC_F32: return extra + V * 288 + 6 * f32 + 2 * f64 + V * 12;
     // mixed: + double-float solution, residual, source (3 x 192 B) and links (576 B) per site
     case WD_PREC_MIXED_F32: return extra + V * 576 + V * 192 + 5 * f32 + 3 * f64 + 2 * f64 + V * 12 + V * 1152;

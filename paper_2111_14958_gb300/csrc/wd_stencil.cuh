@@ -431,58 +431,69 @@ __device__ __forceinline__ double dslash_site(const DslashArgs<SP, C12>& a, int 
 // and gamma_t becomes diag(1, 1, -1, -1), so (1 -/+ gamma_t) keeps two spins, doubled: a time hop
 // needs no spin projection and its link product feeds only two output spins. The links act on
 // colour and commute with T, so D' = T D T^-1 is Eq. (1) with these gammas and the same links and
-// boundary phases. A time direction costs 2 x (72 + 12) = 168 FP64 operations instead of the 204
-// of hop_pair_combined (24 projection adds, 144 link products, 36 reconstruction operations).
+// boundary phases. The time links enter pre-scaled (scale_time_link below), so a time direction
+// costs 2 x 72 = 144 FP64 operations (the link products, accumulated onto the two output spins they
+// feed) instead of the 204 of hop_pair_combined (24 projection adds, 144 link products, 36
+// reconstruction operations).
 // SF: -1 for D (forward hop (1 - gamma_t): lower spins), +1 for D^dagger (upper spins).
+
+// The loop's time links, pre-scaled: tl(s) = 2 mk b(s) U_t(s), mk = -kappa, b(s) the time boundary
+// phase when s is on the last time slice (the two hops that use U_t(s) across the lattice edge, the
+// forward hop from s and the backward hop into s's neighbour, both start or end there), else 1;
+// the 2 is the doubling of the spins (1 -/+ gamma_t) keeps in this basis. One rounding per real
+// (the factor 2 is exact). Written by the loop's prologue, one site per call (tl: double2 [9][V]).
+__device__ __forceinline__ void scale_time_link(const DslashArgs<P64, false>& a, double2* tl, int s) {
+  const int V = a.g.V;
+  const double mk = a.kappa_dev ? -*a.kappa_dev : a.mkappa;
+  const bool last = s / a.g.stride[3] == a.g.L[3] - 1;
+  const double k = 2.0 * ((last && a.g.bc[3] < 0) ? -mk : mk);
+  Cx<double> u[9];
+  load_link(a.u, 3, s, V, u);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) tl[(size_t)j * V + s] = make_double2(k * u[j].re, k * u[j].im);
+}
+
+// Both time hops of site s in the basis above with the pre-scaled links: acc += tl(s) h_f on the
+// spins the forward hop keeps and acc += tl(s - t)^dag h_b on the others. tl is written by the same
+// launch, so it is read through the L2 (ld.global.cg), not the read-only path.
 template <int SF>
-__device__ __forceinline__ void hop_t_dirac(const DslashArgs<P64, false>& a, double mk, int s, const int (&c)[4],
-                                            Cx<double> (&acc)[12]) {
+__device__ __forceinline__ void hop_t_dirac(const DslashArgs<P64, false>& a, const double2* tl, int s,
+                                            const int (&c)[4], Cx<double> (&acc)[12]) {
   constexpr int FO = SF < 0 ? 6 : 0;  // first component of the spins the forward hop keeps
   constexpr int BO = 6 - FO;          // ... and of those the backward hop keeps
   const int V = a.g.V, L = a.g.L[3], st = a.g.stride[3];
-  const bool aper = a.g.bc[3] < 0;
-  {
-    const bool wrap = c[3] == L - 1;
-    const int nb = wrap ? s - (L - 1) * st : s + st;
-    Cx<double> h[6], u[9], chi[6];
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    const int O = dir == 0 ? FO : BO;
+    const int nb = dir == 0 ? (c[3] == L - 1 ? s - (L - 1) * st : s + st) : (c[3] == 0 ? s + (L - 1) * st : s - st);
+    const int ls = dir == 0 ? s : nb;  // the link's site
+    Cx<double> h[6], u[9], t[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      const double2 d = __ldg(a.in.p + (size_t)(FO + i) * V + nb);
+      const double2 d = __ldg(a.in.p + (size_t)(O + i) * V + nb);
       h[i] = cx(d.x, d.y);
     }
-    load_link(a.u, 3, s, V, u);
-    su3_mul(u, h, chi);
-    const double k = 2.0 * ((wrap && aper) ? -mk : mk);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      acc[FO + i].re = fma(k, chi[i].re, acc[FO + i].re);
-      acc[FO + i].im = fma(k, chi[i].im, acc[FO + i].im);
+    for (int k = 0; k < 9; ++k) {
+      const double2 d = __ldcg(tl + (size_t)k * V + ls);
+      u[k] = cx(d.x, d.y);
     }
-  }
-  {
-    const bool wrap = c[3] == 0;
-    const int nb = wrap ? s + (L - 1) * st : s - st;
-    Cx<double> h[6], u[9], chi[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      const double2 d = __ldg(a.in.p + (size_t)(BO + i) * V + nb);
-      h[i] = cx(d.x, d.y);
-    }
-    load_link(a.u, 3, nb, V, u);
-    su3_dag_mul(u, h, chi);
-    const double k = 2.0 * ((wrap && aper) ? -mk : mk);
+    for (int i = 0; i < 6; ++i) t[i] = acc[O + i];
+    if (dir == 0)
+      su3_mul_add(u, h, t, t);
+    else
+      su3_dag_mul_add(u, h, t, t);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      acc[BO + i].re = fma(k, chi[i].re, acc[BO + i].re);
-      acc[BO + i].im = fma(k, chi[i].im, acc[BO + i].im);
-    }
+    for (int i = 0; i < 6; ++i) acc[O + i] = t[i];
   }
 }
 
-// One site of out' = D' in' (the FP64 operator in the basis above, 18-real links); returns |out'|^2
-// and leaves the stored value in acc.
+// One site of out' = D' in' (the FP64 operator in the basis above, 18-real links, the time links
+// pre-scaled in tl); returns |out'|^2 and leaves the stored value in acc.
 template <bool DAG>
-__device__ __forceinline__ double dslash_site_dirac_t(const DslashArgs<P64, false>& a, int s, Cx<double> (&acc)[12]) {
+__device__ __forceinline__ double dslash_site_dirac_t(const DslashArgs<P64, false>& a, const double2* tl, int s,
+                                                      Cx<double> (&acc)[12]) {
   const int V = a.g.V;
   int c[4];
   {
@@ -500,7 +511,7 @@ __device__ __forceinline__ double dslash_site_dirac_t(const DslashArgs<P64, fals
   hop_pair<0, SF>(a, mk, s, c, acc);
   hop_pair<1, SF>(a, mk, s, c, acc);
   hop_pair<2, SF>(a, mk, s, c, acc);
-  hop_t_dirac<SF>(a, mk, s, c, acc);
+  hop_t_dirac<SF>(a, tl, s, c, acc);
   store_spinor(a.out, s, V, acc);
   return norm2_site(acc);
 }
