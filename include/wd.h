@@ -33,6 +33,8 @@
 #ifndef WD_H
 #define WD_H
 
+#include <stddef.h> /* size_t */
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -268,6 +270,42 @@ wd_status cg_solve(wd_ctx* ctx, const void* src, void* x, double tol, int maxit,
  */
 wd_status cg_solve_batch(wd_ctx* const* ctxs, int n, const void* const* srcs, void* const* xs, const double* tols,
                          int maxit, int* iters, double* true_rel_res, int* statuses);
+
+/*
+ * Checkpoint and resume of a CG solve. The paper's CG (Sec. 2, the iteration carries x, r, p and
+ * gamma from one step to the next) has no checkpoint; this lets a caller stop a long solve after
+ * maxit iterations, keep its state in host memory (to give the GPU to other work, or to free the
+ * context), and continue it later from exactly that iteration. Plain FP64 and FP32 contexts
+ * (lexicographic or even-odd, either CG form); mixed-precision contexts return WD_EINVAL.
+ *
+ * wd_cg_state_size -- *bytes = size of a saved state for this context (a header, then x, r and p
+ *   in the context's device layout: 3 x 192 B per site in FP64, 3 x 96 B in FP32).
+ *
+ * wd_cg_save_state -- copies the state into `host` (caller-owned host memory of >= that size;
+ *   pageable or pinned). Valid only right after a cg_solve or cg_resume on this context that
+ *   returned WD_NOT_CONVERGED because its CG loop reached maxit, and before any call that changes
+ *   the context's fields or operator (wd_apply, wd_apply_multi, cg_solve_multi, wd_time_dslash,
+ *   wd_load_gauge, wd_generate_gauge, wd_set_kappa, a new solve); otherwise WD_EINVAL. The state
+ *   is opaque and tied to this library build.
+ *
+ * cg_resume -- continues the saved state on `ctx` (the same context or a new one with the same
+ *   lattice, boundary, precision and kappa, with the same gauge field loaded; WD_EINVAL if the
+ *   header does not match): no new starting residual is formed; the iteration goes on from the
+ *   saved x, r, p, gamma and iteration count until the recursive residual meets tol, then the true
+ *   residual is checked and restarts follow as in cg_solve.
+ *   state, bytes : the saved state (host) and its size (>= wd_cg_state_size).
+ *   src          : device, complex128 canonical: the source of the saved solve.
+ *   x            : device, complex128 canonical; output only (the saved iterate is the start).
+ *   tol, maxit   : as in cg_solve; maxit counts the iterations done before the save as well.
+ *   iters, true_rel_res : optional host outs (iters: total, including those before the save).
+ * On the same context and launch shape, a resumed solve computes bitwise what the uninterrupted
+ * solve computes, except in the FP64 persistent loop's time-diagonal basis (WD_OPT_LOOP_TIME_BASIS),
+ * whose state leaves and re-enters that basis at the stop (equal to rounding). Returns as cg_solve.
+ */
+wd_status wd_cg_state_size(const wd_ctx* ctx, size_t* bytes);
+wd_status wd_cg_save_state(wd_ctx* ctx, void* host, size_t bytes);
+wd_status cg_resume(wd_ctx* ctx, const void* state, size_t bytes, const void* src, void* x, double tol, int maxit,
+                    int* iters, double* true_rel_res);
 
 /*
  * Multiple right-hand sides sharing the operator (a propagator's 12 spin-colour sources, say).

@@ -133,6 +133,7 @@ struct wd_ctx {
   FieldPtr p2, r2;            // second p and r buffers of the FP64 loop with 4, 8 or 16 lanes per site
   FieldPtr tl;                // FP64 loop in the time-diagonal basis: pre-scaled time links (in an FP64 field)
   int tma;                    // WD_OPT_DSLASH_TMA: stand-alone FP32 12-real operator staged by TMA (tile 1 or 2)
+  bool resumable;             // x, r, p and the scalars hold a CG state stopped at maxit (wd_cg_save_state)
   bool standalone;            // the current operator call is wd_apply / wd_time_dslash (not a solve)
   wd_multi_stats mstats;
 };
@@ -663,12 +664,14 @@ wd_status ensure_time_links(wd_ctx* c) {
   return c->tl.p ? WD_OK : alloc_field(c, &c->tl, SP64);
 }
 
-wd_status run_persistent(wd_ctx* c, double* loop_ms) {
+// resume: the context holds a restored CG state (x, r, p, gamma, |r|^2, iteration), so the pass
+// starts without the prologue and only decides from the scalars whether the loop has work to do.
+wd_status run_persistent(wd_ctx* c, double* loop_ms, bool resume = false) {
   const int variant = loop_variant_of(c);
   wd_status st;
   if (variant >= 2 && (st = ensure_lane_buffers(c)) != WD_OK) return st;
   if (loop_time_basis(c, variant) && (st = ensure_time_links(c)) != WD_OK) return st;
-  WD_CUDA(plain_prologue(c, c->stream, 0, 0));
+  WD_CUDA(resume ? launch_cg_check(c->sc, 0, 0, c->stream, 0) : plain_prologue(c, c->stream, 0, 0));
   CgLoopCall L;
   memset(&L, 0, sizeof(L));
   L.g = c->geom;
@@ -758,10 +761,13 @@ wd_status run_mixed_persistent(wd_ctx* c, double* loop_ms) {
   return WD_OK;
 }
 
-wd_status run_host_loop(wd_ctx* c) {
+wd_status run_host_loop(wd_ctx* c, bool resume = false) {
   const bool mixed = is_mixed(c->precision);
   CgScalars* sc = c->sc;
-  WD_CUDA(mixed ? mixed_prologue(c, c->stream, 0, 0) : plain_prologue(c, c->stream, 0, 0));
+  if (resume)  // plain precision only (see run_persistent)
+    WD_CUDA(launch_cg_check(sc, 0, 0, c->stream, 0));
+  else
+    WD_CUDA(mixed ? mixed_prologue(c, c->stream, 0, 0) : plain_prologue(c, c->stream, 0, 0));
   for (;;) {
     WD_CUDA(cudaMemcpyAsync(c->sc_host, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
     WD_CUDA(cudaStreamSynchronize(c->stream));
@@ -1740,6 +1746,7 @@ wd_status wd_load_gauge(wd_ctx* c, const double* U, int on_device, int compress1
   NvtxRange nvtx_("wd:load_gauge");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
+  c->resumable = false;  // the Krylov fields or the operator change
   if (!U) return fail(WD_EINVAL, "U is null");
   const size_t bytes = (size_t)c->V * 4 * 9 * 16;
   const double* src = U;
@@ -1798,6 +1805,7 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
   NvtxRange nvtx_("wd:apply");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
+  c->resumable = false;  // the Krylov fields or the operator change
   if (!in || !out) return fail(WD_EINVAL, "null field pointer");
   if (in == out) return fail(WD_EINVAL, "in and out must differ");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
@@ -1837,12 +1845,38 @@ wd_status wd_apply(wd_ctx* c, const void* in, void* out, int dagger) {
 
 }  // extern "C"
 
+// Saved CG state (wd_cg_save_state / cg_resume): this header, then x, r and p in the context's
+// device layout (each spinor_bytes(working precision, V) bytes), copied byte for byte.
+struct CgStateHeader {
+  char magic[8];  // "WDCGST1"
+  int dims[4];
+  int bc[4];
+  int precision;
+  int iter;       // iterations done
+  double kappa;
+  double gamma;   // |D^dag r|^2 of the current direction p
+  double rr;      // recursive |r|^2
+  unsigned long long field_bytes;
+};
+constexpr char kStateMagic[8] = {'W', 'D', 'C', 'G', 'S', 'T', '1', 0};
+
+__global__ void set_state_kernel(CgScalars* sc, int iter, double gamma, double rr) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc->iter = iter;
+    sc->gamma = gamma;
+    sc->rr = rr;
+    sc->status = ST_RUNNING;
+  }
+}
+
 namespace {
 
 // One solve's progress, shared by cg_solve and cg_solve_batch.
 struct Solve {
   const void* src;
   void* x;
+  const unsigned char* state;  // cg_resume: the saved state (header, then x, r, p); null for cg_solve
+  bool resume_pass;            // the next pass continues the restored state (no prologue)
   double tol;
   int maxit;
   bool persistent;
@@ -1863,8 +1897,10 @@ wd_status solve_begin(wd_ctx* c, Solve& v) {
   if (!(v.tol > 0.0) || !std::isfinite(v.tol)) return fail(WD_EINVAL, "tol must be a positive finite number");
   if (v.maxit < 0 || v.maxit > 10000000) return fail(WD_EINVAL, "maxit must be in [0, 10^7]");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
+  c->resumable = false;
   v.t0 = std::chrono::steady_clock::now();
   v.done = false;
+  v.resume_pass = false;
   v.status = ST_RUNNING;
   v.restarts = 0;
   v.rel = 0.0;
@@ -1877,7 +1913,12 @@ wd_status solve_begin(wd_ctx* c, Solve& v) {
   set_params_kernel<<<1, 32, 0, c->stream>>>(sc, v.tol * v.tol, c->delta * c->delta, v.maxit, c->hist_dev, c->hist_cap);
   WD_CUDA(cudaGetLastError());
   WD_CUDA(launch_pack((const double*)v.src, eta, c->V, eo_geom(c), red_to(c, TK_PACK, &sc->eta2), bb, c->stream));
-  WD_CUDA(launch_pack((const double*)v.x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
+  const size_t fb = spinor_bytes(c->wprec, c->V);
+  const unsigned char* saved = v.state ? v.state + sizeof(CgStateHeader) : nullptr;  // x, r, p
+  if (saved)
+    WD_CUDA(cudaMemcpyAsync(xs.p, saved, fb, cudaMemcpyHostToDevice, c->stream));
+  else
+    WD_CUDA(launch_pack((const double*)v.x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
   if (c->eo) {
     // Schur source on the even sites, in place: b_e = eta_e + kappa H_eo eta_o (eta_o is kept for
     // the reconstruction x_o = eta_o + kappa H_oe x_e)
@@ -1896,11 +1937,23 @@ wd_status solve_begin(wd_ctx* c, Solve& v) {
       set_params_kernel<<<1, 32, 0, c->stream>>>(sc, v.tol * v.tol, c->delta * c->delta, v.maxit, c->hist_dev,
                                                  c->hist_cap);
       WD_CUDA(cudaGetLastError());
-      WD_CUDA(launch_pack((const double*)v.x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
+      if (saved)
+        WD_CUDA(cudaMemcpyAsync(xs.p, saved, fb, cudaMemcpyHostToDevice, c->stream));
+      else
+        WD_CUDA(launch_pack((const double*)v.x, xs, c->V, eo_geom(c), no_red(), bb, c->stream));
     }
   }
   if (c->use_graph && !v.persistent) {
     if ((st = build_graph(c)) != WD_OK) return st;
+  }
+  if (saved) {  // the rest of the saved state, after any tuning that iterated on the context's fields
+    const CgStateHeader* h = reinterpret_cast<const CgStateHeader*>(v.state);
+    WD_CUDA(cudaMemcpyAsync(c->r.p, saved + fb, fb, cudaMemcpyHostToDevice, c->stream));
+    WD_CUDA(cudaMemcpyAsync(c->p.p, saved + 2 * fb, fb, cudaMemcpyHostToDevice, c->stream));
+    set_state_kernel<<<1, 32, 0, c->stream>>>(sc, h->iter, h->gamma, h->rr);
+    WD_CUDA(cudaGetLastError());
+    WD_CUDA(cudaStreamSynchronize(c->stream));  // the caller's host buffer may be reused on return
+    v.resume_pass = true;
   }
   return WD_OK;
 }
@@ -1928,14 +1981,17 @@ void solve_judge(wd_ctx* c, Solve& v) {
 
 wd_status solve_pass(wd_ctx* c, Solve& v) {
   wd_status st;
+  const bool resume = v.resume_pass;  // plain precision only; the graph holds the prologue, so a
+  v.resume_pass = false;              // resumed first pass runs its kernels from the host
   if (v.persistent) {
-    if ((st = is_mixed(c->precision) ? run_mixed_persistent(c, &v.loop_ms) : run_persistent(c, &v.loop_ms)) != WD_OK)
+    if ((st = is_mixed(c->precision) ? run_mixed_persistent(c, &v.loop_ms) : run_persistent(c, &v.loop_ms, resume)) !=
+        WD_OK)
       return st;
-  } else if (c->use_graph) {
+  } else if (c->use_graph && !resume) {
     WD_CUDA(cudaGraphLaunch(c->exec, c->stream));
     WD_CUDA(cudaStreamSynchronize(c->stream));
   } else {
-    if ((st = run_host_loop(c)) != WD_OK) return st;
+    if ((st = run_host_loop(c, resume)) != WD_OK) return st;
   }
   solve_judge(c, v);
   return WD_OK;
@@ -1949,6 +2005,8 @@ wd_status solve_end(wd_ctx* c, Solve& v, int* iters, double* true_rel_res) {
   WD_CUDA(cudaStreamSynchronize(c->stream));
   const CgScalars& h = *c->sc_host;
   const auto t1 = std::chrono::steady_clock::now();
+  // a plain CG loop that stopped at maxit leaves x, r, p and the scalars ready for the next iteration
+  c->resumable = !mixed && v.status == ST_MAXIT && h.status == ST_MAXIT;
   c->stats.iterations = h.iter;
   c->stats.restarts = v.restarts;
   c->stats.loop_mode = v.persistent ? 2 : (c->use_graph ? 1 : 0);
@@ -2117,9 +2175,77 @@ wd_status cg_solve(wd_ctx* c, const void* src, void* x, double tol, int maxit, i
   Solve v;
   v.src = src;
   v.x = x;
+  v.state = nullptr;
   v.tol = tol;
   v.maxit = maxit;
   wd_status st;
+  if ((st = solve_begin(c, v)) != WD_OK) return st;
+  while (!v.done)
+    if ((st = solve_pass(c, v)) != WD_OK) return st;
+  return solve_end(c, v, iters, true_rel_res);
+}
+
+wd_status wd_cg_state_size(const wd_ctx* c, size_t* bytes) {
+  wd_status st;
+  if ((st = check_ctx(c)) != WD_OK) return st;
+  if (!bytes) return fail(WD_EINVAL, "bytes is null");
+  if (is_mixed(c->precision)) return fail(WD_EINVAL, "CG states are saved for plain FP64 or FP32 contexts only");
+  *bytes = sizeof(CgStateHeader) + 3 * spinor_bytes(c->wprec, c->V);
+  return WD_OK;
+}
+
+wd_status wd_cg_save_state(wd_ctx* c, void* host, size_t bytes) {
+  NvtxRange nvtx_("wd:cg_save_state");
+  wd_status st;
+  size_t need = 0;
+  if ((st = wd_cg_state_size(c, &need)) != WD_OK) return st;
+  if (!host) return fail(WD_EINVAL, "host buffer is null");
+  if (bytes < need) return fail(WD_EINVAL, "host buffer smaller than wd_cg_state_size");
+  if (!c->resumable)
+    return fail(WD_EINVAL, "no resumable CG state: the last solve on this context did not stop at maxit, or a "
+                           "later call changed its fields or operator");
+  CgStateHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kStateMagic, sizeof(h.magic));
+  memcpy(h.dims, c->dims, sizeof(h.dims));
+  memcpy(h.bc, c->bc, sizeof(h.bc));
+  h.precision = c->precision;
+  h.iter = c->sc_host->iter;
+  h.kappa = c->kappa;
+  h.gamma = c->sc_host->gamma;
+  h.rr = c->sc_host->rr;
+  h.field_bytes = spinor_bytes(c->wprec, c->V);
+  unsigned char* out = static_cast<unsigned char*>(host);
+  memcpy(out, &h, sizeof(h));
+  const FieldPtr* fs[3] = {&c->x, &c->r, &c->p};
+  for (int i = 0; i < 3; ++i)
+    WD_CUDA(cudaMemcpyAsync(out + sizeof(h) + i * h.field_bytes, fs[i]->p, h.field_bytes, cudaMemcpyDeviceToHost,
+                            c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return WD_OK;
+}
+
+wd_status cg_resume(wd_ctx* c, const void* state, size_t bytes, const void* src, void* x, double tol, int maxit,
+                    int* iters, double* true_rel_res) {
+  NvtxRange nvtx_("wd:cg_resume");
+  wd_status st;
+  size_t need = 0;
+  if ((st = wd_cg_state_size(c, &need)) != WD_OK) return st;
+  if (!state || bytes < need) return fail(WD_EINVAL, "state is null or smaller than wd_cg_state_size");
+  CgStateHeader h;
+  memcpy(&h, state, sizeof(h));
+  if (memcmp(h.magic, kStateMagic, sizeof(h.magic)) != 0) return fail(WD_EINVAL, "not a saved CG state");
+  if (memcmp(h.dims, c->dims, sizeof(h.dims)) != 0 || memcmp(h.bc, c->bc, sizeof(h.bc)) != 0 ||
+      h.precision != c->precision || h.field_bytes != spinor_bytes(c->wprec, c->V))
+    return fail(WD_EINVAL, "the saved state belongs to another lattice, boundary or precision");
+  if (h.kappa != c->kappa) return fail(WD_EINVAL, "the saved state was taken with another kappa");
+  if (h.iter < 0) return fail(WD_EINVAL, "corrupt saved state");
+  Solve v;
+  v.src = src;
+  v.x = x;
+  v.state = static_cast<const unsigned char*>(state);
+  v.tol = tol;
+  v.maxit = maxit;
   if ((st = solve_begin(c, v)) != WD_OK) return st;
   while (!v.done)
     if ((st = solve_pass(c, v)) != WD_OK) return st;
@@ -2140,6 +2266,7 @@ wd_status cg_solve_batch(wd_ctx* const* ctxs, int n, const void* const* srcs, vo
   for (int i = 0; i < n; ++i) {
     vs[i].src = srcs[i];
     vs[i].x = xs[i];
+    vs[i].state = nullptr;
     vs[i].tol = tols[i];
     vs[i].maxit = maxit;
     if ((st = solve_begin(ctxs[i], vs[i])) != WD_OK) return st;
@@ -2198,6 +2325,7 @@ wd_status wd_get_residual_history(const wd_ctx* c, double* out, int max_entries,
 wd_status wd_time_dslash(wd_ctx* c, int dagger, int launches, double* avg_ms) {
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
+  c->resumable = false;  // the Krylov fields or the operator change
   if (!avg_ms || launches <= 0) return fail(WD_EINVAL, "bad arguments");
   if (!c->gauge_loaded) return fail(WD_ENOGAUGE, "wd_load_gauge has not been called");
   if ((st = autotune_single(c)) != WD_OK) return st;
@@ -2230,6 +2358,7 @@ wd_status wd_apply_multi(wd_ctx* c, const double* in, double* out, int nrhs, int
   NvtxRange nvtx_("wd:apply_multi");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
+  c->resumable = false;
   if (!in || !out || in == out) return fail(WD_EINVAL, "null or aliased field pointer");
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(WD_EINVAL, "nrhs must be in [1, 16]");
   if (c->eo) return fail(WD_EINVAL, "multi-RHS calls need a context without WD_EVEN_ODD");
@@ -2254,6 +2383,7 @@ wd_status cg_solve_multi(wd_ctx* c, const double* src, double* x, int nrhs, doub
   NvtxRange nvtx_("wd:cg_solve_multi");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
+  c->resumable = false;
   if (!src || !x) return fail(WD_EINVAL, "null field pointer");
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(WD_EINVAL, "nrhs must be in [1, 16]");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(WD_EINVAL, "tol must be a positive finite number");
@@ -2343,6 +2473,7 @@ wd_status wd_generate_gauge(wd_ctx* c, double eps, unsigned long long seed, int 
   NvtxRange nvtx_("wd:generate_gauge");
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
+  c->resumable = false;
   if (!std::isfinite(eps)) return fail(WD_EINVAL, "eps must be finite");
   bool need64 = false, need32 = false;
   int c12 = 0;
@@ -2366,6 +2497,7 @@ wd_status wd_generate_source(wd_ctx* c, unsigned long long seed, double* out) {
 wd_status wd_set_kappa(wd_ctx* c, double kappa) {
   wd_status st;
   if ((st = check_ctx(c)) != WD_OK) return st;
+  c->resumable = false;  // the Krylov fields or the operator change
   if (!std::isfinite(kappa) || std::fabs(kappa) >= 1.0) return fail(WD_EINVAL, "kappa must be finite with |kappa| < 1");
   WD_CUDA(cudaStreamSynchronize(c->stream));
   c->kappa = kappa;

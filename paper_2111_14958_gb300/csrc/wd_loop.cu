@@ -750,6 +750,22 @@ __device__ __forceinline__ void cg_loop_lanes_body(const LanesLoopArgs& a) {
       break;
     }
   }
+  if (status == ST_MAXIT) {
+    // Stopped between iterations: leave the state every loop starts from, p_k = s + beta p_{k-1} in
+    // p0 and r_k in r0 (the same fma the next pass would form), so that a later launch can continue
+    // it (cg_resume). Each thread rewrites only the reals it reads; the last barrier ended every
+    // neighbour read.
+    const double* pold = reinterpret_cast<const double*>(pi ? a.p1 : a.p0);
+    const double* rcur = reinterpret_cast<const double*>(a.r1);
+    const double* sv = reinterpret_cast<const double*>(a.s);
+    double* p0 = reinterpret_cast<double*>(a.p0);
+    double* r0 = reinterpret_cast<double*>(a.r0);
+    const int ne = 24 * a.g.V;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+      p0[e] = fma(beta, pold[e], sv[e]);
+      if (ri) r0[e] = rcur[e];
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const bool failed = *(volatile int*)a.y.err != 0;
     sc->status = failed ? ST_BREAKDOWN : status;

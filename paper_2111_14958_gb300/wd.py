@@ -114,6 +114,9 @@ _sig = {
     "cg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "cg_solve_batch": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_D), _I,
                             ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "wd_cg_state_size": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "wd_cg_save_state": (_I, [_P, _P, ctypes.c_size_t]),
+    "cg_resume": (_I, [_P, _P, ctypes.c_size_t, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "wd_set_option": (_I, [_P, _I, _D]),
     "wd_get_stats": (_I, [_P, ctypes.POINTER(WdStats)]),
     "wd_get_residual_history": (_I, [_P, ctypes.POINTER(_D), _I, ctypes.POINTER(_I)]),
@@ -251,6 +254,35 @@ def cg_solve_batch(ctxs, srcs, xs, tols, maxit: int):
     st = _lib.cg_solve_batch(c, n, sp, xp, tl, int(maxit), it, res, sts)
     _check(st, "cg_solve_batch", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
     return st, list(it), list(res), list(sts)
+
+
+def wd_cg_state_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.wd_cg_state_size(_P(ctx), ctypes.byref(n)), "wd_cg_state_size")
+    return n.value
+
+
+def wd_cg_save_state(ctx) -> bytearray:
+    """The CG state of a solve that stopped at maxit, as a host byte buffer."""
+    buf = bytearray(wd_cg_state_size(ctx))
+    cbuf = (ctypes.c_char * len(buf)).from_buffer(buf)
+    _check(_lib.wd_cg_save_state(_P(ctx), ctypes.cast(cbuf, _P), len(buf)), "wd_cg_save_state")
+    return buf
+
+
+def cg_resume(ctx, state, src: torch.Tensor, x: torch.Tensor, tol: float, maxit: int):
+    """Continue a saved CG state; x (output) receives the solution. Returns (status, iters, residual)."""
+    for t in (src, x):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("src and x must be contiguous complex128 CUDA tensors")
+    if src.numel() != x.numel():
+        raise ValueError("cg_resume: src and x must have the same size")
+    buf = bytes(state)
+    it, res = ctypes.c_int(), ctypes.c_double()
+    st = _lib.cg_resume(_P(ctx), ctypes.c_char_p(buf), len(buf), _P(_ptr(src)), _P(_ptr(x)), float(tol), int(maxit),
+                        ctypes.byref(it), ctypes.byref(res))
+    _check(st, "cg_resume", allow=(WD_OK, WD_NOT_CONVERGED, WD_BREAKDOWN))
+    return st, it.value, res.value
 
 
 def wd_generate_gauge(ctx, eps: float, seed: int, compress12: bool = False, U_out: torch.Tensor = None) -> None:
@@ -423,6 +455,18 @@ class WilsonDirac:
             raise ValueError(f"solve: src (and x0) must be spinor fields of shape {self.spinor_shape}")
         x = torch.zeros_like(src) if x0 is None else x0.clone()
         status, iters, res = cg_solve(self.ctx, src.contiguous(), x, tol, maxit)
+        return x, iters, res, status
+
+    def save_state(self) -> bytearray:
+        """The state of the last solve, which must have stopped at maxit (WD_NOT_CONVERGED)."""
+        return wd_cg_save_state(self.ctx)
+
+    def resume(self, state, src, tol=1e-10, maxit=2000):
+        """Continue a saved solve; maxit counts the iterations before the save too."""
+        if src.numel() != self._spinor_numel():
+            raise ValueError(f"resume: src must be a spinor field of shape {self.spinor_shape}")
+        x = torch.empty_like(src)
+        status, iters, res = cg_resume(self.ctx, state, src.contiguous(), x, tol, maxit)
         return x, iters, res, status
 
     def set_option(self, key, value):
