@@ -75,7 +75,7 @@ def _fp64_unit_peak(dev) -> tuple:
 # for the kernel as it now stands.
 NCU_TRAFFIC = {
     "cg_loop_f64_14x4": (70633984, "profiles/cg_loop_f64_14x4.md"),
-    "dslash_f64_14x4": (None, "profiles/dslash_f64_14x4.md"),
+    "dslash_f64_14x4": (29587712, "profiles/dslash_f64_14x4.md"),
 }
 
 
