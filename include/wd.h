@@ -297,7 +297,8 @@ wd_status cg_solve_batch(wd_ctx* const* ctxs, int n, const void* const* srcs, vo
  *   src          : device, complex128 canonical: the source of the saved solve.
  *   x            : device, complex128 canonical; output only (the saved iterate is the start).
  *   tol, maxit   : as in cg_solve; maxit counts the iterations done before the save as well.
- *   iters, true_rel_res : optional host outs (iters: total, including those before the save).
+ *   iters, true_rel_res : optional host outs (iters: total, including those before the save;
+ *                         so are the iteration and dslash counts of wd_get_stats afterwards).
  * On the same context and launch shape, a resumed solve computes bitwise what the uninterrupted
  * solve computes, except in the FP64 persistent loop's time-diagonal basis (WD_OPT_LOOP_TIME_BASIS),
  * whose state leaves and re-enters that basis at the stop (equal to rounding). Returns as cg_solve.
