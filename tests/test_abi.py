@@ -106,3 +106,20 @@ def test_binding_rejects_mistyped_fields_before_the_library(lib):
     for inp, out in ((c64, c128), (c128, c128[:1]), (c128, c128.clone())):
         with pytest.raises(ValueError):
             wd.wd_apply(None, inp, out)
+
+
+def test_checkpoint_calls_validate_before_any_device_call(lib):
+    """wd_cg_state_size / wd_cg_save_state / cg_resume refuse a null context (and the binding a
+    mistyped field) without touching a device."""
+    import ctypes
+    import torch
+    from paper_2111_14958_gb300 import wd
+    n = ctypes.c_size_t()
+    assert lib.wd_cg_state_size(None, ctypes.byref(n)) == wd.WD_EINVAL
+    buf = ctypes.create_string_buffer(64)
+    assert lib.wd_cg_save_state(None, buf, 64) == wd.WD_EINVAL
+    assert lib.cg_resume(None, buf, 64, None, None, ctypes.c_double(1e-10), 10, None, None) == wd.WD_EINVAL
+    assert "null context" in wd.wd_last_error()
+    c128 = torch.zeros((2, 2, 2, 2, 4, 3), dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        wd.cg_resume(None, bytes(64), c128, c128.to(torch.complex64), 1e-10, 10)
