@@ -2,7 +2,8 @@
 
 This shows the pins are not vacuous: a dropped boundary phase, swapped projectors, transposed
 links, a flipped kappa sign or an undaggered backward link all change some checked fact, and so
-do mistakes in the two CG solvers (norms without their squares, D in place of D^dagger) and in the
+do mistakes in the two CG solvers (norms without their squares, D in place of D^dagger, a search
+direction restarted, or a beta lagging by one iteration, which still converges) and in the
 two checking helpers every GPU test reads (a residual without its square root or with D^dagger,
 a relative difference normalised by the wrong argument or left squared).
 """
@@ -108,10 +109,36 @@ def check_rel_diff_against_numpy():
         assert abs(wilson.rel_diff(u, v) - ref) <= 1e-14 * ref
 
 
+def _krylov_basis(A, b, k):
+    V = np.zeros((b.size, k), dtype=np.complex128)
+    v = b / np.linalg.norm(b)
+    for j in range(k):
+        for _ in range(2):
+            v = v - V[:, :j] @ (V[:, :j].conj().T @ v)
+        V[:, j] = v / np.linalg.norm(v)
+        v = A @ V[:, j]
+    return V
+
+
+def check_cg_iterates_are_krylov_minimisers():
+    # after 3 iterations from zero: CGLS minimises ||eta - D x||, the paper's CG the error of
+    # x = D^dag psi, both over K_3(D^dag D, D^dag eta)
+    dims = (2, 2, 2, 2)
+    U, eta, xd = _dense_solution(dims, 0.12)
+    d = wilson.dense_D(U, 0.12, BC)
+    b = eta.reshape(-1)
+    V = _krylov_basis(d.conj().T @ d, d.conj().T @ b, 3)
+    y, *_ = np.linalg.lstsq(d @ V, b, rcond=None)
+    x, _, _, _ = ocg.cgls(U, eta, 0.12, 0.0, 3, boundary=BC)
+    assert wilson.rel_diff(x.reshape(-1), V @ y) < 1e-9
+    x, _, _, _ = ocg.cg_paper(U, eta, 0.12, 0.0, 3, boundary=BC)
+    assert wilson.rel_diff(x.reshape(-1), V @ (V.conj().T @ xd)) < 1e-9
+
+
 CHECKS = [check_fft_solve, check_gauge_covariance, check_gamma5_hermiticity_dense,
           check_stencil_vs_coo, check_plane_wave, check_cgls_against_dense_solve,
           check_cg_paper_against_dense_solve, check_true_residual_against_dense,
-          check_rel_diff_against_numpy]
+          check_rel_diff_against_numpy, check_cg_iterates_are_krylov_minimisers]
 
 
 def _wrap_both(monkeypatch, transform_args):
@@ -210,7 +237,59 @@ def _mut_rel_diff_squared(mp):
         wilson.norm2(np.asarray(a) - np.asarray(b)) / wilson.norm2(b)))
 
 
+def _mut_cgls_periodic_restart(mp):
+    # CGLS that drops the search direction's history every other iteration (p = s): the third
+    # iterate already leaves the Krylov minimiser
+    def cgls(U, eta, kappa, tol, maxit, x0=None, boundary=BC):
+        D = lambda v: wilson.apply_D(U, v, kappa, boundary)                  # noqa: E731
+        Dd = lambda v: wilson.apply_D(U, v, kappa, boundary, dagger=True)    # noqa: E731
+        x = np.zeros_like(eta) if x0 is None else np.array(x0, dtype=np.complex128)
+        en = np.sqrt(wilson.norm2(eta))
+        r = eta - D(x)
+        s = Dd(r)
+        p, gamma, hist, k = s.copy(), wilson.norm2(s), [np.sqrt(wilson.norm2(r)) / en], 0
+        while hist[-1] > tol and k < maxit:
+            q = D(p)
+            alpha = gamma / wilson.norm2(q)
+            x, r = x + alpha * p, r - alpha * q
+            s = Dd(r)
+            gnew = wilson.norm2(s)
+            p = s if (k + 1) % 2 == 0 else s + (gnew / gamma) * p
+            gamma, k = gnew, k + 1
+            hist.append(np.sqrt(wilson.norm2(r)) / en)
+        return x, k, float(np.sqrt(wilson.norm2(eta - D(x))) / en), np.array(hist)
+
+    mp.setattr(ocg, "cgls", cgls)
+
+
+def _mut_paper_cg_lagged_beta(mp):
+    # the paper's CG with beta taken from the previous iteration's ratio: it still reaches
+    # D^-1 eta within the dense-solve check's budget, so only the iterate check sees it
+    def cg_paper(U, eta, kappa, tol, maxit, psi0=None, boundary=BC):
+        D = lambda v: wilson.apply_D(U, v, kappa, boundary)                  # noqa: E731
+        Dd = lambda v: wilson.apply_D(U, v, kappa, boundary, dagger=True)    # noqa: E731
+        psi = np.zeros_like(eta) if psi0 is None else np.array(psi0, dtype=np.complex128)
+        en = np.sqrt(wilson.norm2(eta))
+        r = eta - D(Dd(psi))
+        p, k, beta_prev, hist = r.copy(), 0, 0.0, [np.sqrt(wilson.norm2(r)) / en]
+        while np.sqrt(wilson.norm2(r)) >= tol * en and k < maxit:
+            r_old = wilson.norm2(r)
+            ddp = Dd(p)
+            alpha = r_old / wilson.norm2(ddp)
+            psi, r = psi + alpha * p, r - alpha * D(ddp)
+            beta = wilson.norm2(r) / r_old
+            p = r + (beta_prev if k > 0 else beta) * p
+            beta_prev, k = beta, k + 1
+            hist.append(np.sqrt(wilson.norm2(r)) / en)
+        x = Dd(psi)
+        return x, k, float(np.sqrt(wilson.norm2(eta - D(x))) / en), np.array(hist)
+
+    mp.setattr(ocg, "cg_paper", cg_paper)
+
+
 MUTATIONS = {
+    "cgls_periodic_restart": _mut_cgls_periodic_restart,
+    "paper_cg_lagged_beta": _mut_paper_cg_lagged_beta,
     "drop_boundary_phase": _mut_drop_phase,
     "transpose_links": _mut_transpose_links,
     "flip_kappa_sign": _mut_kappa_sign,

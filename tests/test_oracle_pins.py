@@ -278,3 +278,47 @@ def test_cgls_free_field_matches_fft_solve():
     x, _, res, _ = cg.cgls(U, eta, 0.12, 1e-11, 2000)
     assert res <= 1e-11
     assert wilson.rel_diff(x, freefield.solve(eta, 0.12, BC)) < 1e-9
+
+
+def _krylov_basis(A, b, k):
+    """Orthonormal basis of K_k(A, b) = span{b, A b, ..., A^(k-1) b} (Gram-Schmidt, twice)."""
+    V = np.zeros((b.size, k), dtype=np.complex128)
+    v = b / np.linalg.norm(b)
+    for j in range(k):
+        for _ in range(2):
+            v = v - V[:, :j] @ (V[:, :j].conj().T @ v)
+        V[:, j] = v / np.linalg.norm(v)
+        v = A @ V[:, j]
+    return V
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
+def test_cgls_iterate_is_the_krylov_least_squares_minimiser(k):
+    """From x0 = 0, the k-th CGLS iterate minimises ||eta - D x|| over K_k(D^dag D, D^dag eta):
+    checked against a least-squares solve on an explicit Krylov basis of the dense D, so a wrong
+    alpha, beta or update order fails here even where the iteration would still converge."""
+    dims = (2, 2, 2, 4)
+    U, eta = _fields(dims, eps=0.5, gseed=7, sseed=8)
+    D = wilson.dense_D(U, 0.124, BC)
+    b = eta.reshape(-1)
+    V = _krylov_basis(D.conj().T @ D, D.conj().T @ b, k)
+    y, *_ = np.linalg.lstsq(D @ V, b, rcond=None)
+    x, iters, _, _ = cg.cgls(U, eta, 0.124, 0.0, k)
+    assert iters == k
+    assert wilson.rel_diff(x.reshape(-1), V @ y) < 1e-9
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 6])
+def test_paper_cg_iterate_minimises_the_error_norm(k):
+    """CG on D D^dag psi = eta from psi0 = 0 minimises the D D^dag-energy norm of the error of psi,
+    which is the 2-norm of the error of x = D^dag psi; x_k therefore is the orthogonal projection of
+    the exact solution D^-1 eta onto K_k(D^dag D, D^dag eta) (dense solve, explicit basis)."""
+    dims = (2, 2, 2, 4)
+    U, eta = _fields(dims, eps=0.5, gseed=9, sseed=10)
+    D = wilson.dense_D(U, 0.124, BC)
+    b = eta.reshape(-1)
+    xstar = np.linalg.solve(D, b)
+    V = _krylov_basis(D.conj().T @ D, D.conj().T @ b, k)
+    x, iters, _, _ = cg.cg_paper(U, eta, 0.124, 0.0, k)
+    assert iters == k
+    assert wilson.rel_diff(x.reshape(-1), V @ (V.conj().T @ xstar)) < 1e-9
