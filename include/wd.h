@@ -75,9 +75,11 @@ enum {
                                 about 0.003                                                      */
   WD_OPT_USE_GRAPH = 2,      /* how cg_solve runs the CG loop: 0 plain stream launches with a
                                 host poll; 1 a CUDA graph with a device-side while node; 2 a
-                                persistent cooperative kernel for the loop (CGLS; mixed
-                                precision returns to the host for each reliable update; mixed
-                                even-odd contexts and the paper's CG form use the graph); 3
+                                persistent cooperative kernel for the loop (CGLS, or the paper's
+                                CG form on the lexicographic layout with one thread per site;
+                                mixed precision returns to the host for each reliable update;
+                                mixed even-odd contexts and the even-odd paper form use the
+                                graph); 3
                                 (default) automatic: the persistent kernel for plain FP32 on
                                 the lexicographic layout at every volume, for plain FP64 on it up
                                 to 65,536 sites (its launch shape, 1 to 16 threads per site,
@@ -102,7 +104,9 @@ enum {
                                 form (Sec. 2): CG on D D^dag y = eta with x = D^dag y, carried in
                                 x directly (x += alpha D^dag p), so x on input is the initial
                                 guess in both forms. Same two operator applications, stopping
-                                rule and true residual; mixed-precision contexts reject 1.       */
+                                rule and true residual; mixed-precision contexts reject 1. The
+                                paper's form needs three grid barriers per iteration in the
+                                persistent loop, CGLS four.                                      */
   WD_OPT_DSLASH_VARIANT = 11,/* FP64 single-RHS dslash (FP64 contexts, and the reliable updates
                                 of mixed ones), also inside the persistent CG loop: 0 (default)
                                 chosen with the block size on first use (the wider splits are

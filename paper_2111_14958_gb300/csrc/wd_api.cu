@@ -606,7 +606,8 @@ constexpr int kPersistentMaxSites = 48000;
 constexpr int kPersistentMaxSitesF64 = 65536;
 
 bool persistent_loop(const wd_ctx* c) {
-  if (c->cg_form || (c->eo && is_mixed(c->precision))) return false;
+  // the paper's CG form has a persistent loop on the lexicographic layout (one thread per site)
+  if ((c->cg_form && c->eo) || (c->eo && is_mixed(c->precision))) return false;
   if (c->use_graph == 2) return true;
   // even-odd (FP64 14^4: 4 %; FP64 24^4: the graph by 25 %) keeps to the volume limit in FP32 too
   const bool plain32 = !is_mixed(c->precision) && c->wprec == SP32 && !c->eo;
@@ -637,10 +638,12 @@ namespace {
 // Shape of the persistent FP64 loop: options first, then the loop's own timing, else the dslash's.
 int loop_block_of(const wd_ctx* c) {
   if (c->block_dslash > 0) return c->block_dslash;
+  if (c->cg_form)  // one thread per site; where the dslash tuner split sites over lanes, spread them
+    return c->wprec == SP64 && dslash_variant(c, SP64) != 0 ? 64 : dslash_block(c, c->wprec);
   return c->loop_tuned ? c->loop_block : dslash_block(c, c->wprec);
 }
 int loop_variant_of(const wd_ctx* c) {
-  if (c->wprec != SP64 || c->eo) return 0;
+  if (c->wprec != SP64 || c->eo || c->cg_form) return 0;  // the paper's loop: one thread per site
   if (c->force_var) return c->force_var - 1;
   return c->loop_tuned ? c->loop_var : dslash_variant(c, c->wprec);
 }
@@ -692,6 +695,7 @@ wd_status run_persistent(wd_ctx* c, double* loop_ms, bool resume = false) {
   L.wait_limit = c->loop_wait_limit;
   L.variant = variant;
   L.time_basis = loop_time_basis(c, variant) ? 1 : 0;
+  L.cg_form = c->cg_form;
   L.t = c->t;
   L.p2 = c->p2;
   L.r2 = c->r2;
@@ -2063,6 +2067,7 @@ CgLoopCall loop_call(wd_ctx* c, int start_b) {
   L.wait_limit = c->loop_wait_limit;
   L.variant = is_mixed(c->precision) ? 0 : loop_variant_of(c);
   L.time_basis = loop_time_basis(c, L.variant) ? 1 : 0;
+  L.cg_form = c->cg_form;
   L.t = c->t;
   L.p2 = c->p2;
   L.r2 = c->r2;

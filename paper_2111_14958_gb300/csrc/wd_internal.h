@@ -144,6 +144,7 @@ struct CgLoopCall {
   int max_grid;
   int variant;  // FP64: 1 = the dslash phases use two lanes per site
   int time_basis;  // FP64, one thread per site: 1 = the loop runs in the basis where gamma_t is diagonal
+  int cg_form;     // 1: the paper's CG on D D^dag (one thread per site; variant must be 0)
   int start_b;  // mixed loop: resume at the D^dag half of an iteration (after a reliable update)
   FieldPtr t;   // even-odd loop: the odd-site temporary
   FieldPtr p2, r2;  // FP64 loop with 4, 8 or 16 lanes per site: second buffers of p and r

@@ -381,6 +381,157 @@ __global__ void __launch_bounds__(kDslashMaxThreads, BatchMinBlocks<SP>::value)
   cg_loop_body<SP, C12, LANES, DT>(b.a[blockIdx.y]);
 }
 
+// The paper's CG (Sec. 2: CG on D D^dag psi = eta, carried in x = D^dag psi) as one persistent
+// launch. Its iteration needs three grid barriers where CGLS needs four: alpha comes from the first
+// operator's output, so the second operator and both vector updates share one phase.
+//   A: s = D^dag p, |s|^2;                                  barrier; alpha = |r|^2 / |s|^2
+//   B: q = D s and, at the same site, x += alpha s, r -= alpha q, |r|^2
+//                                                          barrier; beta = |r'|^2 / |r|^2, convergence
+//   C: p = r + beta p;                                      barrier (p complete before A reads it)
+// gamma holds |r|^2 here. The vector arithmetic is that of the graph's kernels (fma(alpha, s, x),
+// fma(-alpha, q, r), fma(beta, p, r)). DT: the spin basis of cg_loop_body, entered and left the
+// same way. ds reads p and writes s; dq reads s and writes q (paper_loop_args).
+template <int SP, bool C12, bool DT>
+__device__ __forceinline__ void cg_paper_loop_body(const LoopArgs<SP, C12>& a) {
+  typedef typename RealOf<SP>::type R;
+  CgScalars* sc = a.sc;
+  if (sc->status != ST_RUNNING) return;  // uniform over the grid
+  const int n = a.n, V = a.dq.g.V, G = gridDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, tstep = G * blockDim.x;
+  constexpr bool AH = SP == P64;  // see lane_sum
+  const double nscale = DT ? 2.0 : 1.0;
+  double gamma = sc->gamma * nscale, rr = sc->rr * nscale;
+  const double tol2e = sc->tol2 * sc->eta2 * nscale;
+  int iter = sc->iter, status = ST_RUNNING;
+  const int maxit = sc->maxit;
+  double alpha = 0.0, beta = 0.0;
+  bool run = true;
+  if constexpr (DT) {
+    for (int i = t0; i < n; i += tstep) {
+      dirac_t_basis<false>(a.x, i, V);
+      dirac_t_basis<false>(a.r, i, V);
+      dirac_t_basis<false>(a.p, i, V);
+      scale_time_link(a.dq, a.tl, i);
+    }
+    run = grid_barrier(a.y);  // p and the time links everywhere before D^dag p reads them
+  }
+  // FP64, one site per thread: r stays in registers from B to C (the FP32 kernel's register budget
+  // of three blocks per SM has no room for it)
+  constexpr bool KEEP = SP == P64;
+  const bool one = KEEP && n <= tstep;
+  while (run) {
+    // A: s = D^dag p, |s|^2
+    double v = loop_dslash<SP, C12, true, 1, DT>(a.ds, a.tl, n, t0, tstep);
+    double ss;
+    if (!loop_sum<AH>(v, a.partials, a.y, &ss)) break;
+    if (!(ss > 0.0 && isfinite(ss) && isfinite(gamma))) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    alpha = gamma / ss;
+    const R ar = (R)alpha;
+    // B: q = D s; x += alpha s; r -= alpha q; |r|^2
+    v = 0.0;
+    Cx<R> rkeep[12];
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> qv[12], sv[12], xv[12], rv[12];
+      loop_dslash_site<SP, C12, false, DT>(a.dq, a.tl, i, qv);
+      load_spinor(a.s, i, V, sv);
+      load_spinor(a.x, i, V, xv);
+      load_spinor(a.r, i, V, rv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        xv[c].re = fma(ar, sv[c].re, xv[c].re);
+        xv[c].im = fma(ar, sv[c].im, xv[c].im);
+        rv[c].re = fma(-ar, qv[c].re, rv[c].re);
+        rv[c].im = fma(-ar, qv[c].im, rv[c].im);
+      }
+      store_spinor(a.x, i, V, xv);
+      store_spinor(a.r, i, V, rv);
+      v += norm2_site(rv);
+      if constexpr (KEEP) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) rkeep[c] = rv[c];
+      }
+    }
+    double rnew;
+    if (!loop_sum<AH>(v, a.partials + G, a.y, &rnew)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_residual(sc, iter, rnew / nscale);
+    if (!isfinite(rnew)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    iter += 1;
+    if (rnew <= tol2e) {
+      rr = rnew;
+      gamma = rnew;
+      status = ST_CONVERGED;
+      break;
+    }
+    if (!(gamma > 0.0)) {
+      status = ST_BREAKDOWN;
+      break;
+    }
+    beta = rnew / gamma;
+    gamma = rnew;
+    rr = rnew;
+    const R br = (R)beta;
+    // C: p = r + beta p
+    for (int i = t0; i < n; i += tstep) {
+      Cx<R> pv[12], rv[12];
+      load_spinor(a.p, i, V, pv);
+      if (KEEP && one) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) rv[c] = rkeep[c];
+      } else {
+        load_spinor(a.r, i, V, rv);
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        pv[c].re = fma(br, pv[c].re, rv[c].re);
+        pv[c].im = fma(br, pv[c].im, rv[c].im);
+      }
+      store_spinor(a.p, i, V, pv);
+    }
+    if (iter >= maxit) {
+      status = ST_MAXIT;
+      break;
+    }
+    if (!grid_barrier(a.y)) break;  // p complete before A reads its neighbours
+  }
+  if constexpr (DT) {
+    // every neighbour read of this launch is behind the last barrier all blocks passed
+    for (int i = t0; i < n; i += tstep) {
+      dirac_t_basis<true>(a.x, i, V);
+      dirac_t_basis<true>(a.r, i, V);
+      dirac_t_basis<true>(a.p, i, V);
+      dirac_t_basis<true>(a.s, i, V);
+      dirac_t_basis<true>(a.q, i, V);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool failed = *(volatile int*)a.y.err != 0;
+    sc->status = failed ? ST_BREAKDOWN : status;
+    sc->iter = iter;
+    sc->gamma = gamma / nscale;
+    sc->rr = rr / nscale;
+    sc->alpha = alpha;
+    sc->beta = beta;
+  }
+}
+
+template <int SP, bool C12, bool DT>
+__global__ void __launch_bounds__(kDslashMaxThreads, DslashMinBlocks<SP>::value)
+    cg_paper_loop_kernel(const LoopArgs<SP, C12> a) {
+  cg_paper_loop_body<SP, C12, DT>(a);
+}
+
+template <int SP, bool C12, bool DT>
+__global__ void __launch_bounds__(kDslashMaxThreads, BatchMinBlocks<SP>::value)
+    cg_paper_loop_batch_kernel(const __grid_constant__ LoopBatch<LoopArgs<SP, C12>> b) {
+  cg_paper_loop_body<SP, C12, DT>(b.a[blockIdx.y]);
+}
+
 // The inner loop of the mixed-precision solver (FP32 or FP16 vectors, x_lo in FP32) in one
 // cooperative launch. Phase A: q = D p, |q|^2; r_lo -= alpha q, x_lo += alpha p, |r_lo|^2, and
 // the reliable-update test. Phase B: s = D^dag r_lo, |s|^2; p = s + beta p. The kernel starts at A
@@ -595,7 +746,7 @@ static bool same_shape(const CgLoopCall* cs, int n) {
     const CgLoopCall &a = cs[0], &b = cs[i];
     if (memcmp(&a.g, &b.g, sizeof(GeomH)) != 0 || a.block != b.block || a.variant != b.variant ||
         a.max_grid != b.max_grid || a.u.prec != b.u.prec || a.u.c12 != b.u.c12 || a.r.prec != b.r.prec ||
-        a.x.prec != b.x.prec || a.time_basis != b.time_basis)
+        a.x.prec != b.x.prec || a.time_basis != b.time_basis || a.cg_form != b.cg_form)
       return false;
   }
   return true;
@@ -658,6 +809,23 @@ static LoopArgs<SP, C12> plain_loop_args(const CgLoopCall& c) {
   a.y.limit = c.wait_limit;
   a.y.err = c.err;
   return a;
+}
+
+// The paper's loop: D^dag reads p into s, D reads s into q.
+template <int SP, bool C12>
+static LoopArgs<SP, C12> paper_loop_args(const CgLoopCall& c) {
+  LoopArgs<SP, C12> a = plain_loop_args<SP, C12>(c);
+  a.ds.in = make_ref<SP>(c.p, c.g.V);
+  a.ds.out = make_ref<SP>(c.s, c.g.V);
+  a.dq.in = make_ref<SP>(c.s, c.g.V);
+  a.dq.out = make_ref<SP>(c.q, c.g.V);
+  return a;
+}
+
+template <int SP, bool C12, bool DT = false>
+static cudaError_t paper_loop_launch_t(const CgLoopCall* cs, int n, cudaStream_t st) {
+  return loop_launch(cg_paper_loop_kernel<SP, C12, DT>, cg_paper_loop_batch_kernel<SP, C12, DT>,
+                     paper_loop_args<SP, C12>, cs, n, cs[0].g.V, st);
 }
 
 template <int SP, bool C12, int LANES, bool DT = false>
@@ -824,6 +992,14 @@ cudaError_t launch_cg_loop_n(const CgLoopCall* cs, int n, cudaStream_t st) {
         (!d.p2.p || !d.r2.p || d.p2.prec != SP64 || d.r2.prec != SP64))
       return cudaErrorInvalidValue;
     if (d.r.prec == SP64 && d.variant == 0 && d.time_basis && !d.tl.p) return cudaErrorInvalidValue;
+  }
+  if (c.cg_form) {  // one thread per site, the paper's CG form
+    if (c.variant != 0) return cudaErrorInvalidValue;
+    if (c.r.prec == SP64 && c.u.prec == SP64)
+      return c.time_basis ? paper_loop_launch_t<P64, false, true>(cs, n, st) : paper_loop_launch_t<P64, false>(cs, n, st);
+    if (c.r.prec == SP32 && c.u.prec == SP32)
+      return c.u.c12 ? paper_loop_launch_t<P32, true>(cs, n, st) : paper_loop_launch_t<P32, false>(cs, n, st);
+    return cudaErrorInvalidValue;
   }
   if (c.r.prec == SP64) {
     if (c.u.prec != SP64) return cudaErrorInvalidValue;

@@ -240,9 +240,37 @@ def test_paper_form_graph_and_host_loop_agree_bitwise():
     wd = require_gpu()
     dims = (4, 4, 4, 8)
     U, eta = fields(dims)
-    a = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, options={wd.WD_OPT_CG_FORM: 1})
+    a = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta,
+               options={wd.WD_OPT_CG_FORM: 1, wd.WD_OPT_USE_GRAPH: 1})
     b = _solve(wd, dims, 0.12, wd.WD_PREC_F64, 1e-10, U=U, eta=eta, graph=False, options={wd.WD_OPT_CG_FORM: 1})
+    assert a[4]["loop_mode"] == 1 and b[4]["loop_mode"] == 0
     assert a[1] == b[1] and np.array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("prec,tol,basis", [("f64", 1e-10, 1), ("f64", 1e-10, 0), ("f32", 1e-6, 0)])
+def test_paper_form_persistent_loop_matches_the_graph_and_the_oracle(prec, tol, basis):
+    """The paper's CG as one persistent launch (three grid barriers per iteration): the same
+    iterations as its graph within one, both solutions within the system's conditioning of each
+    other and of the oracle's paper CG, the tolerance met by the oracle's residual."""
+    wd = require_gpu()
+    dims = (6, 4, 4, 8)
+    U, eta = fields(dims, gseed=61, sseed=62)
+    p = wd.WD_PREC_F64 if prec == "f64" else wd.WD_PREC_F32
+    opts = {wd.WD_OPT_CG_FORM: 1}
+    if prec == "f64":
+        opts[wd.WD_OPT_LOOP_TIME_BASIS] = basis
+    a = _solve(wd, dims, 0.12, p, tol, U=U, eta=eta, options=dict(opts))
+    b = _solve(wd, dims, 0.12, p, tol, U=U, eta=eta, options={**opts, wd.WD_OPT_USE_GRAPH: 1})
+    assert a[3] == wd.WD_OK and b[3] == wd.WD_OK
+    assert a[4]["loop_mode"] == 2 and a[4]["loop_lanes"] == 1 and b[4]["loop_mode"] == 1
+    assert abs(a[1] - b[1]) <= 1
+    margin = 1.05 if prec == "f32" else 1.0 + 1e-6
+    assert ocg.true_residual(U, eta, a[0], 0.12) <= tol * margin
+    assert abs(a[2] - ocg.true_residual(U, eta, a[0], 0.12)) < max(1e-12, 0.05 * tol)
+    assert rel(a[0], b[0]) < 1e3 * tol
+    if prec == "f64":
+        xo, io, _, _ = ocg.cg_paper(U, eta, 0.12, tol, 4000)
+        assert abs(a[1] - io) <= 2 and rel(a[0], xo) < 1e-8
 
 
 def test_paper_form_uses_the_initial_guess_and_is_rejected_where_unsupported():

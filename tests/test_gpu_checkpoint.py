@@ -3,8 +3,8 @@
 A solve stopped at maxit leaves x, r, p, gamma and the iteration count of the CG iteration (Sec. 2)
 in the context; saved to host memory and resumed, it must reach what the uninterrupted solve
 reaches: bit for bit on the same launch shape (the four-phase persistent loop, the loop with 8
-lanes per site, the graph, FP32, even-odd, a fresh context), to rounding in the FP64 loop's
-time-diagonal basis. Every result meets the tolerance by the oracle's residual.
+lanes per site, the graph, FP32, even-odd, the paper's CG form, a fresh context), to rounding in
+the FP64 loop's time-diagonal basis. Every result meets the tolerance by the oracle's residual.
 """
 import numpy as np
 import pytest
@@ -30,6 +30,7 @@ def _case(wd, name):
         "f64_even_odd": (wd.WD_PREC_F64 | wd.WD_EVEN_ODD, {}, 1e-10, True),
         "f32": (wd.WD_PREC_F32, {}, 1e-6, True),
         "f64_time_basis": (wd.WD_PREC_F64, {wd.WD_OPT_DSLASH_VARIANT: 1, wd.WD_OPT_LOOP_TIME_BASIS: 1}, 1e-10, False),
+        "f64_paper_form": (wd.WD_PREC_F64, {wd.WD_OPT_CG_FORM: 1, wd.WD_OPT_LOOP_TIME_BASIS: 0}, 1e-10, True),
     }[name]
 
 
@@ -42,7 +43,7 @@ def _make(wd, U, prec, opts):
 
 
 @pytest.mark.parametrize("name", ["f64_one_thread_chiral", "f64_eight_lanes", "f64_graph", "f64_host_loop",
-                                  "f64_even_odd", "f32", "f64_time_basis"])
+                                  "f64_even_odd", "f32", "f64_time_basis", "f64_paper_form"])
 def test_resumed_solve_equals_the_uninterrupted_one(name):
     wd = require_gpu()
     prec, opts, tol, bitwise = _case(wd, name)
